@@ -1,0 +1,193 @@
+/*
+ * ptim.h — C ABI of the GB300 library for the hot path of finite-temperature
+ * PT-IM real-time TDDFT with a hybrid functional (arXiv 2501.03061).
+ *
+ * The library applies the occupation-weighted screened Fock exchange operator
+ * to a block of orbitals, builds and applies its adaptively compressed (ACE)
+ * form, applies the Hamiltonian, and takes one PT-IM(-ACE) time step.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Grid: nx*ny*nz points (each dimension 2..64 and 2,3,5-smooth) on an
+ *    orthorhombic cell Lx*Ly*Lz (bohr).  Ng = nx*ny*nz, dV = Lx*Ly*Lz/Ng.
+ *  - Orbital blocks are complex, interleaved (re, im), ORBITAL-MAJOR: orbital
+ *    j, point (x,y,z) sits at element j*Ng + (z*ny + y)*nx + x.  The element
+ *    type is double2 (complex128) for PT_FP64 and float2 (complex64) for the
+ *    FP32 precisions.  Buffers start on a 16-byte boundary.
+ *  - N x N matrices (sigma, Q, ...) are complex128, row-major: a[i*N + j].
+ *  - Inner product <a|b> = dV * sum_r conj(a(r)) b(r).
+ *  - All pointers passed in are DEVICE pointers unless stated otherwise.  The
+ *    caller owns every buffer it passes; the library never frees caller memory
+ *    and never keeps a caller pointer past the call.
+ *  - Every call is asynchronous on `stream` (a cudaStream_t; NULL = the legacy
+ *    default stream) unless its comment says it synchronises.  Errors are
+ *    returned as pt_status; nothing is thrown across the ABI.  After an error,
+ *    pt_last_error(ctx) gives a one-line description.
+ *  - A pt_ctx is not thread-safe: use one context per host thread.
+ */
+#ifndef PTIM_H
+#define PTIM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int pt_status;
+enum {
+  PT_OK = 0,
+  PT_INVALID_ARG = 1,    /* bad size, null pointer, misaligned buffer, unsupported grid */
+  PT_OOM = 2,            /* device allocation failed or the context's HBM budget is exceeded */
+  PT_NOT_PD = 3,         /* Cholesky met a non-positive pivot (ACE: -M not positive definite) */
+  PT_NOT_CONVERGED = 4,  /* PT-IM iteration caps reached before the tolerance */
+  PT_NONFINITE = 5,      /* a NaN/Inf appeared in a residual or a small dense factorisation */
+  PT_TIMEOUT = 6,        /* a bounded device-side wait ran out */
+  PT_CUDA = 7,           /* a CUDA runtime error; see pt_last_error */
+  PT_UNSUPPORTED = 8     /* valid request that this build does not implement */
+};
+
+/* Orthorhombic periodic cell sampled on an nx*ny*nz grid. */
+typedef struct {
+  int nx, ny, nz;
+  double L[3];
+} pt_grid;
+
+/* Fourier-space interaction K(G) of V_x(r,r') = -P(r,r') K(r,r') (Sec. II-B, Eq. 1).
+ *   type 0: Coulomb 4*pi/|G|^2, with K(0) = g0 (use 0).
+ *   type 1: erfc-screened Coulomb 4*pi/|G|^2 * (1 - exp(-|G|^2/(4 mu^2))),
+ *           K(0) = g0 if g0 is finite, else the analytic limit pi/mu^2 (pass NaN).
+ * G = 2*pi*m/L with m wrapped to [-n/2, n/2). */
+typedef struct {
+  int type;
+  double mu;
+  double g0;
+} pt_kernel;
+
+typedef enum {
+  PT_FP64 = 0,          /* every step in FP64 (the plain FP64 form) */
+  PT_FP32 = 1,          /* pair products, FFTs and Ng-long contractions in FP32;
+                           N x N factorisations, residuals and Loewdin in FP64 */
+  PT_FP32_TC_TF32 = 2,  /* as PT_FP32 with the ACE/subspace GEMMs on TF32 tensor cores */
+  PT_FP32_TC_BF16 = 3   /* as PT_FP32 with the ACE/subspace GEMMs on BF16 tensor cores */
+} pt_precision;
+
+typedef struct pt_ctx pt_ctx;
+typedef struct pt_ace pt_ace;
+
+/* ---- context --------------------------------------------------------------------------- */
+
+/* Create a context on CUDA `device`.  hbm_budget caps the bytes of device
+ * workspace the context may hold (0 = 90% of the device's free memory at
+ * creation).  The context owns its workspace, cached FFT/kernel tables and
+ * pair schedules.  Synchronises the device. */
+pt_status pt_create(pt_ctx** ctx, int device, size_t hbm_budget);
+/* Free the context and all workspace it owns (synchronises). */
+void pt_destroy(pt_ctx* ctx);
+/* One-line description of the last error of this context ("" if none). */
+const char* pt_last_error(const pt_ctx* ctx);
+/* Bytes of device workspace currently held by the context. */
+size_t pt_workspace_bytes(const pt_ctx* ctx);
+/* Release cached workspace (synchronises). */
+pt_status pt_trim(pt_ctx* ctx);
+/* Set a tuning option of the context.  Keys:
+ *   "scratch_bytes"  bytes of pair/orbital fields one FFT batch may hold (default 48 MiB, sized
+ *                    to stay resident in L2; smaller values give more, smaller batches). */
+pt_status pt_set_option(pt_ctx* ctx, const char* key, double value);
+
+/* ---- Fock exchange (Sec. IV-A1, Eq. vxdiag; Alg. 2 with sigma diagonalised) ------------ */
+
+/* out_j = (V_x tgt_j)(r) = - sum_i occ_i src_i(r) * IFFT[ K(G) * FFT[ conj(src_i) tgt_j ] ](r)
+ * for j = 0..M-1, i = 0..N-1 (forward FFT unnormalised, inverse divided by Ng).
+ *   src  Ng x N orbitals phit_i in the basis that diagonalises sigma (Eq. diag_sigma)
+ *   occ  N doubles d_i (the eigenvalues of sigma); pairs with occ_i == 0 are skipped
+ *   tgt  Ng x M orbitals, or NULL to use tgt = src (then M must equal N and the
+ *        kernel's symmetry v_ji = conj(v_ij) halves the FFT work)
+ *   out  Ng x M, overwritten; must not alias src or tgt.
+ * The result carries no mixing fraction alpha.  Precisions: PT_FP64 or any FP32 form. */
+pt_status pt_apply_exchange(pt_ctx* ctx, const void* src, const double* occ, int N,
+                            const void* tgt, int M, void* out,
+                            const pt_grid* grid, const pt_kernel* kernel,
+                            pt_precision prec, void* stream);
+
+/* ---- adaptively compressed exchange (Sec. IV-A2, Eq. vx_ace; Lin's construction) -------- */
+
+/* Build the ACE operator of V_x[P] on span(phi), P = sum_i occ_i phi_i phi_i^*:
+ *   W = V_x phi (with src = tgt = phi),  M = <phi|W>,  -M = L L^* (FP64 Cholesky),
+ *   xi = W L^{-*},  so that V_ACE = -xi xi^* (dV inner product) and V_ACE phi = W.
+ *   phi  Ng x N orbitals in the sigma-diagonal basis; occ N doubles (device).
+ * On success *ace holds a library-owned object with xi (Ng x N, precision prec).
+ * Returns PT_NOT_PD if -M is not positive definite (e.g. negative occupations). */
+pt_status pt_build_ace(pt_ctx* ctx, const void* phi, const double* occ, int N,
+                       const pt_grid* grid, const pt_kernel* kernel, pt_precision prec,
+                       pt_ace** ace, void* stream);
+/* Same construction from a given W = V_x phi (for phi not in the sigma-diagonal basis). */
+pt_status pt_build_ace_from(pt_ctx* ctx, const void* W, const void* phi, int N,
+                            const pt_grid* grid, pt_precision prec, pt_ace** ace, void* stream);
+/* out = V_ACE psi = - xi (xi^* psi):  out_j = - sum_k xi_k <xi_k|psi_j>, j = 0..M-1.
+ * psi, out: Ng x M in the ACE's precision; out must not alias psi. */
+pt_status pt_apply_ace(pt_ctx* ctx, const pt_ace* ace, const void* psi, int M, void* out, void* stream);
+/* Copy xi (Ng x N, the ACE's precision) into a caller buffer. */
+pt_status pt_ace_get_xi(const pt_ace* ace, void* xi_out, void* stream);
+void pt_ace_destroy(pt_ace* ace);
+
+/* ---- Hamiltonian (Eq. 1 with frozen V_Hxc + V_ext) -------------------------------------- */
+
+/* out = P_sph[ -1/2 Lap psi + vloc * psi + alpha * V_ACE psi ], the projection
+ * P_sph keeping the plane waves with |G|^2/2 <= ecut.  ace may be NULL (no
+ * exchange term).  vloc: Ng doubles (device).  psi/out Ng x M, out != psi. */
+pt_status pt_apply_H(pt_ctx* ctx, const void* psi, int M, void* out, const double* vloc,
+                     const pt_ace* ace, double alpha, double ecut, const pt_grid* grid,
+                     pt_precision prec, void* stream);
+
+/* ---- occupation matrix (Sec. IV-A1, Eq. diag_sigma) -------------------------------------- */
+
+/* sigma = Q diag(d) Q^* for Hermitian sigma (its Hermitian part is used), FP64
+ * parallel Jacobi on the GPU.  d ascending.  sigma, Q: N x N complex128 row-major;
+ * d: N doubles.  All device pointers.  Synchronises the stream (sweep convergence test). */
+pt_status pt_diag_occupations(pt_ctx* ctx, const void* sigma, int N, void* Q, double* d, void* stream);
+
+/* ---- one PT-IM time step (Alg. 1; Eqs. n+1/2, p_tilde, lisan; Sec. IV-A2 double loop) --- */
+
+typedef struct {
+  double dt;             /* time step (au) */
+  double alpha;          /* exchange mixing fraction (0.25 for HSE-like functionals) */
+  double ecut;           /* plane-wave cutoff (Ha) of the projection P_sph */
+  double tol;            /* relative residual of x = T(x), and of the ACE anchor change */
+  int max_outer;         /* outer (ACE rebuild) iterations */
+  int max_inner;         /* inner Anderson iterations per outer iteration */
+  int anderson_depth;    /* mixing history (<= 20) */
+  double anderson_beta;  /* mixing parameter */
+  int use_ace;           /* 1: PT-IM-ACE double loop; 0: V_x applied exactly every iteration */
+  double spin;           /* spin factor of the reported energies (2 = closed shell) */
+} pt_ptim_params;
+
+typedef struct {
+  int outer, inner;         /* iterations taken */
+  double residual;          /* last relative residual of the inner loop */
+  double exch_energy;       /* spin*(alpha/2) Tr[P V_x[P]] at the last ACE anchor (Ha) */
+  double orth_error;        /* max |Phi^*Phi - Phi_n^*Phi_n| before the final orthonormalisation */
+  int converged;            /* 1 when both loops met tol */
+  long long pair_ffts;      /* pair FFTs executed (counting a symmetric pair once) */
+} pt_ptim_stats;
+
+/* One PT-IM(-ACE) step from (phi, sigma) = (Phi_n, sigma_n) to (Phi_{n+1}, sigma_{n+1}),
+ * both updated in place.  phi: Ng x N (precision prec); sigma: N x N complex128;
+ * vloc: Ng doubles.  Returns PT_NOT_CONVERGED (with the last iterate stored) when the
+ * caps are reached.  Synchronises the stream once per inner iteration (residual test). */
+pt_status pt_ptim_step(pt_ctx* ctx, void* phi, void* sigma, int N, const double* vloc,
+                       const pt_grid* grid, const pt_kernel* kernel, const pt_ptim_params* params,
+                       pt_precision prec, pt_ptim_stats* stats, void* stream);
+
+/* ---- small helpers used by the binding and tests ------------------------------------------ */
+
+/* Library version string and the GPU architecture it was compiled for. */
+const char* pt_version(void);
+/* Number of this library's kernel launches issued so far by the calling process. */
+long long pt_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PTIM_H */

@@ -1,0 +1,214 @@
+"""Thin PyTorch-facing binding of the C ABI: checks tensors, passes raw device pointers.
+
+Every computation runs in libptim.so; this module only marshals arguments.  The
+names follow the C entry points (pt_apply_exchange -> Context.apply_exchange ...).
+Orbital blocks are torch tensors of shape (N, nz, ny, nx), complex128 for
+precision "fp64" and complex64 for the FP32 forms, on the context's device.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+
+import torch
+
+from . import _lib as L
+
+_CDTYPE = {"fp64": torch.complex128, "fp32": torch.complex64, "tf32": torch.complex64, "bf16": torch.complex64}
+
+
+class PtimError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{L.STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _grid(cell) -> L.pt_grid:
+    n, Ls = cell.n, cell.L
+    g = L.pt_grid()
+    g.nx, g.ny, g.nz = int(n[0]), int(n[1]), int(n[2])
+    g.L[0], g.L[1], g.L[2] = float(Ls[0]), float(Ls[1]), float(Ls[2])
+    return g
+
+
+def _kernel(kernel) -> L.pt_kernel:
+    k = L.pt_kernel()
+    kernel = kernel or {"type": 1, "mu": 0.106}
+    k.type = int(kernel.get("type", 1))
+    k.mu = float(kernel.get("mu", 0.106))
+    k.g0 = float(kernel.get("g0", math.nan))
+    return k
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: torch.Tensor):
+    return C.c_void_p(t.data_ptr())
+
+
+class Ace:
+    """Library-owned ACE operator (xi vectors live in device memory until close())."""
+
+    def __init__(self, ctx, handle, N, cell, precision):
+        self.ctx, self.handle, self.N, self.cell, self.precision = ctx, handle, N, cell, precision
+
+    def xi(self, stream=None):
+        out = torch.empty((self.N, self.cell.n[2], self.cell.n[1], self.cell.n[0]), dtype=_CDTYPE[self.precision],
+                          device=self.ctx.device)
+        st = L.load().pt_ace_get_xi(self.handle, _ptr(out), _stream(stream))
+        if st != L.PT_OK:
+            raise PtimError(st, "pt_ace_get_xi failed")
+        return out
+
+    def close(self):
+        if self.handle:
+            L.load().pt_ace_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Context:
+    """A pt_ctx on one CUDA device (owns workspace and cached tables)."""
+
+    def __init__(self, device: int = 0, hbm_budget: int = 0):
+        if not torch.cuda.is_available():
+            raise RuntimeError("the PT-IM library needs a CUDA GPU; no CPU fallback exists")
+        self.lib = L.load()
+        self.device = torch.device("cuda", device)
+        h = C.c_void_p()
+        st = self.lib.pt_create(C.byref(h), device, hbm_budget)
+        if st != L.PT_OK:
+            raise PtimError(st, "pt_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.pt_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what):
+        if st != L.PT_OK:
+            raise PtimError(st, f"{what}: {self.lib.pt_last_error(self.h).decode()}")
+
+    def _orb(self, t, precision, what):
+        if t.device != self.device or not t.is_contiguous() or t.dtype != _CDTYPE[precision] or t.dim() != 4:
+            raise ValueError(f"{what} must be a contiguous {_CDTYPE[precision]} (N, nz, ny, nx) tensor on {self.device}")
+        return t
+
+    def workspace_bytes(self) -> int:
+        return int(self.lib.pt_workspace_bytes(self.h))
+
+    def set_option(self, key: str, value: float):
+        self._check(self.lib.pt_set_option(self.h, key.encode(), float(value)), "pt_set_option")
+
+    def trim(self):
+        self._check(self.lib.pt_trim(self.h), "pt_trim")
+
+    # ---- exchange --------------------------------------------------------------------------
+    def apply_exchange(self, src, occ, tgt=None, out=None, *, cell, kernel=None, precision="fp64", stream=None):
+        """out_j = V_x tgt_j = -sum_i occ_i src_i IFFT[K FFT[conj(src_i) tgt_j]] (tgt None: tgt = src)."""
+        self._orb(src, precision, "src")
+        if tgt is not None:
+            self._orb(tgt, precision, "tgt")
+        occ = occ.to(device=self.device, dtype=torch.float64).contiguous()
+        ref = src if tgt is None else tgt
+        if out is None:
+            out = torch.empty_like(ref)
+        g, k = _grid(cell), _kernel(kernel)
+        st = self.lib.pt_apply_exchange(self.h, _ptr(src), _ptr(occ), src.shape[0],
+                                        None if tgt is None else _ptr(tgt), ref.shape[0], _ptr(out),
+                                        C.byref(g), C.byref(k), L.PRECISIONS[precision], _stream(stream))
+        self._check(st, "pt_apply_exchange")
+        return out
+
+    # ---- ACE --------------------------------------------------------------------------------
+    def build_ace(self, phi, occ, *, cell, kernel=None, precision="fp64", stream=None) -> Ace:
+        self._orb(phi, precision, "phi")
+        occ = occ.to(device=self.device, dtype=torch.float64).contiguous()
+        g, k = _grid(cell), _kernel(kernel)
+        h = C.c_void_p()
+        st = self.lib.pt_build_ace(self.h, _ptr(phi), _ptr(occ), phi.shape[0], C.byref(g), C.byref(k),
+                                   L.PRECISIONS[precision], C.byref(h), _stream(stream))
+        self._check(st, "pt_build_ace")
+        return Ace(self, h, phi.shape[0], cell, precision)
+
+    def build_ace_from(self, W, phi, *, cell, precision="fp64", stream=None) -> Ace:
+        self._orb(W, precision, "W")
+        self._orb(phi, precision, "phi")
+        g = _grid(cell)
+        h = C.c_void_p()
+        st = self.lib.pt_build_ace_from(self.h, _ptr(W), _ptr(phi), phi.shape[0], C.byref(g),
+                                        L.PRECISIONS[precision], C.byref(h), _stream(stream))
+        self._check(st, "pt_build_ace_from")
+        return Ace(self, h, phi.shape[0], cell, precision)
+
+    def apply_ace(self, ace: Ace, psi, out=None, stream=None):
+        self._orb(psi, ace.precision, "psi")
+        if out is None:
+            out = torch.empty_like(psi)
+        st = self.lib.pt_apply_ace(self.h, ace.handle, _ptr(psi), psi.shape[0], _ptr(out), _stream(stream))
+        self._check(st, "pt_apply_ace")
+        return out
+
+    # ---- Hamiltonian ------------------------------------------------------------------------
+    def apply_H(self, psi, vloc, ace: Ace | None = None, alpha=0.25, ecut=10.0, *, cell, precision="fp64",
+                out=None, stream=None):
+        self._orb(psi, precision, "psi")
+        vloc = vloc.to(device=self.device, dtype=torch.float64).contiguous()
+        if out is None:
+            out = torch.empty_like(psi)
+        g = _grid(cell)
+        st = self.lib.pt_apply_H(self.h, _ptr(psi), psi.shape[0], _ptr(out), _ptr(vloc),
+                                 None if ace is None else ace.handle, float(alpha), float(ecut), C.byref(g),
+                                 L.PRECISIONS[precision], _stream(stream))
+        self._check(st, "pt_apply_H")
+        return out
+
+    # ---- occupations ----------------------------------------------------------------------
+    def diag_occupations(self, sigma, stream=None):
+        sigma = sigma.to(device=self.device, dtype=torch.complex128).contiguous()
+        N = sigma.shape[0]
+        Q = torch.empty_like(sigma)
+        d = torch.empty(N, dtype=torch.float64, device=self.device)
+        st = self.lib.pt_diag_occupations(self.h, _ptr(sigma), N, _ptr(Q), _ptr(d), _stream(stream))
+        self._check(st, "pt_diag_occupations")
+        return Q, d
+
+    # ---- PT-IM step -------------------------------------------------------------------------
+    def ptim_step(self, phi, sigma, vloc, *, cell, kernel=None, precision="fp64", dt=0.5, alpha=0.25, ecut=10.0,
+                  tol=1e-6, max_outer=30, max_inner=200, anderson_depth=20, anderson_beta=1.0, use_ace=True,
+                  spin=2.0, stream=None, allow_unconverged=False):
+        """Advance (phi, sigma) by one PT-IM(-ACE) step in place; returns the step statistics."""
+        self._orb(phi, precision, "phi")
+        if sigma.dtype != torch.complex128 or not sigma.is_contiguous() or sigma.device != self.device:
+            raise ValueError("sigma must be a contiguous complex128 tensor on the device")
+        vloc = vloc.to(device=self.device, dtype=torch.float64).contiguous()
+        p = L.pt_ptim_params(dt, alpha, ecut, tol, max_outer, max_inner, anderson_depth, anderson_beta,
+                             int(bool(use_ace)), spin)
+        s = L.pt_ptim_stats()
+        g, k = _grid(cell), _kernel(kernel)
+        st = self.lib.pt_ptim_step(self.h, _ptr(phi), _ptr(sigma), phi.shape[0], _ptr(vloc), C.byref(g), C.byref(k),
+                                   C.byref(p), L.PRECISIONS[precision], C.byref(s), _stream(stream))
+        if not (st == L.PT_OK or (allow_unconverged and st == L.PT_NOT_CONVERGED)):
+            self._check(st, "pt_ptim_step")
+        return {"status": L.STATUS_NAMES[st], "outer": s.outer, "inner": s.inner, "residual": s.residual,
+                "exch_energy": s.exch_energy, "orth_error": s.orth_error, "converged": bool(s.converged),
+                "pair_ffts": int(s.pair_ffts)}
+
+
+def kernel_launches() -> int:
+    return int(L.load().pt_kernel_launches())

@@ -1,0 +1,374 @@
+// Complex contractions over the grid (CUDA-core form) and streaming vector kernels.
+//
+//   gram:    C[i][j] = scale * sum_r conj(A_i(r)) B_j(r)      (A: Ng x N1, B: Ng x N2, orbital-major;
+//            C: N1 x N2 complex128 row-major).  Split over r, FP64 reduction of the splits.
+//   rotate:  Out_j(r) = alpha * sum_k A_k(r) Bm[k][j] + sum_e c_e E_e,j(r)
+//            (Bm: N1 x N2 complex128 row-major, converted to the orbital precision).
+//   lincomb, multi_dot, norms: streaming kernels over orbital blocks.
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace pt {
+
+namespace {
+
+// Summation in the orbital precision: FP64 adds directly; FP32 carries a Kahan
+// compensation so long sums keep ~FP32-ulp accuracy without FP64 arithmetic in the
+// inner loop (FP64 throughput is a small fraction of FP32 on this part).
+template <class T>
+struct Acc {
+  T s = T(0), c = T(0);
+  __device__ __forceinline__ void add(T x) {
+    if constexpr (sizeof(T) == 8) {
+      s += x;
+    } else {
+      const T y = x - c;
+      const T t = s + y;
+      c = (t - s) - y;
+      s = t;
+    }
+  }
+  __device__ __forceinline__ double value() const { return double(s) - double(c); }
+};
+
+// ---------------------------------------------------------------- gram (A^H B) ----
+constexpr int GT = 32;      // output tile (i and j)
+constexpr int GK = 32;      // grid points per smem stage
+constexpr int GTHREADS = 256;
+
+template <class T>
+__global__ void __launch_bounds__(GTHREADS) k_gram(const cx<T>* __restrict__ A, const cx<T>* __restrict__ B,
+                                                    int N1, int N2, size_t ng, size_t chunk,
+                                                    c128* __restrict__ part) {
+  __shared__ cx<T> As[GK][GT + 1];
+  __shared__ cx<T> Bs[GK][GT + 1];
+  const int i0 = blockIdx.x * GT, j0 = blockIdx.y * GT;
+  const size_t r_begin = size_t(blockIdx.z) * chunk;
+  const size_t r_end = std::min(ng, r_begin + chunk);
+  const int tid = threadIdx.x;
+  const int ti = tid % 16, tj = tid / 16;
+  Acc<T> acc_re[2][2], acc_im[2][2];
+  for (size_t r0 = r_begin; r0 < r_end; r0 += GK) {
+    cx<T> acc[2][2];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 2; ++b) acc[a][b] = czero<T>();
+    // load 32 orbitals x 32 points of A and B (points fastest: coalesced)
+#pragma unroll
+    for (int pass = 0; pass < (GT * GK) / GTHREADS; ++pass) {
+      const int e = tid + pass * GTHREADS;
+      const int k = e % GK, o = e / GK;
+      const size_t r = r0 + k;
+      cx<T> va = czero<T>(), vb = czero<T>();
+      if (r < r_end) {
+        if (i0 + o < N1) va = A[size_t(i0 + o) * ng + r];
+        if (j0 + o < N2) vb = B[size_t(j0 + o) * ng + r];
+      }
+      As[k][o] = va;
+      Bs[k][o] = vb;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < GK; ++k) {
+      const cx<T> a0 = As[k][ti], a1 = As[k][ti + 16];
+      const cx<T> b0 = Bs[k][tj], b1 = Bs[k][tj + 16];
+      cfma(acc[0][0], conjc(a0), b0);
+      cfma(acc[0][1], conjc(a0), b1);
+      cfma(acc[1][0], conjc(a1), b0);
+      cfma(acc[1][1], conjc(a1), b1);
+    }
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        acc_re[a][b].add(acc[a][b].re);
+        acc_im[a][b].add(acc[a][b].im);
+      }
+    __syncthreads();
+  }
+  c128* P = part + size_t(blockIdx.z) * N1 * N2;
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const int i = i0 + ti + 16 * a, j = j0 + tj + 16 * b;
+      if (i < N1 && j < N2) P[size_t(i) * N2 + j] = c128{acc_re[a][b].value(), acc_im[a][b].value()};
+    }
+}
+
+__global__ void k_reduce_parts(const c128* __restrict__ part, int nsplit, size_t n, double scale,
+                               c128* __restrict__ C) {
+  const size_t e = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  double re = 0, im = 0;
+  for (int s = 0; s < nsplit; ++s) {
+    re += part[size_t(s) * n + e].re;
+    im += part[size_t(s) * n + e].im;
+  }
+  C[e] = c128{re * scale, im * scale};
+}
+
+// ---------------------------------------------------------------- rotate (A Bm + E) ----
+constexpr int RT = 128;   // grid points per CTA
+constexpr int JT = 32;    // output orbitals per CTA
+constexpr int KC = 16;    // k per smem stage
+constexpr int RTHREADS = 256;
+
+template <class T>
+struct Epi {
+  const cx<T>* e[3];
+  cx<T> c[3];
+};
+
+template <class T>
+__global__ void __launch_bounds__(RTHREADS) k_rotate(const cx<T>* __restrict__ A, const c128* __restrict__ Bm,
+                                                      int ldb, int N1, int N2, size_t ng, cx<T> alpha, Epi<T> epi,
+                                                      cx<T>* __restrict__ out) {
+  __shared__ cx<T> As[KC][RT];
+  __shared__ cx<T> Bs[KC][JT];
+  const size_t r0 = size_t(blockIdx.x) * RT;
+  const int j0 = blockIdx.y * JT;
+  const int tid = threadIdx.x;
+  const int tr = tid % 32, tj = tid / 32;  // 32 x 8
+  cx<T> acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = czero<T>();
+  for (int k0 = 0; k0 < N1; k0 += KC) {
+#pragma unroll
+    for (int pass = 0; pass < (KC * RT) / RTHREADS; ++pass) {
+      const int e = tid + pass * RTHREADS;
+      const int r = e % RT, kk = e / RT;
+      const size_t rr = r0 + r;
+      cx<T> v = czero<T>();
+      if (k0 + kk < N1 && rr < ng) v = A[size_t(k0 + kk) * ng + rr];
+      As[kk][r] = v;
+    }
+    for (int e = tid; e < KC * JT; e += RTHREADS) {
+      const int j = e % JT, kk = e / JT;
+      cx<T> v = czero<T>();
+      if (k0 + kk < N1 && j0 + j < N2) v = to_cx<T>(Bm[size_t(k0 + kk) * ldb + j0 + j]);
+      Bs[kk][j] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < KC; ++kk) {
+      cx<T> av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = As[kk][tr + 32 * a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][tj + 8 * b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) cfma(acc[a][b], av[a], bv[b]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    const int j = j0 + tj + 8 * b;
+    if (j >= N2) continue;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const size_t r = r0 + tr + 32 * a;
+      if (r >= ng) continue;
+      const size_t idx = size_t(j) * ng + r;
+      cx<T> v = cmul(alpha, acc[a][b]);
+#pragma unroll
+      for (int t = 0; t < 3; ++t)
+        if (epi.e[t]) v = v + cmul(epi.c[t], epi.e[t][idx]);
+      out[idx] = v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- streaming kernels ----
+template <class T>
+__global__ void k_lincomb(cx<T>* __restrict__ out, size_t n, Epi<T> t, const cx<T>* __restrict__ x3, cx<T> c3) {
+  for (size_t e = size_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n; e += size_t(gridDim.x) * blockDim.x) {
+    cx<T> v = czero<T>();
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      if (t.e[k]) v = v + cmul(t.c[k], t.e[k][e]);
+    if (x3) v = v + cmul(c3, x3[e]);
+    out[e] = v;
+  }
+}
+
+// out_j(r) = v(r) psi_j(r) + a * X_j(r)   (v real, FP64 on input)
+template <class T>
+__global__ void k_potential_apply(cx<T>* __restrict__ out, const cx<T>* __restrict__ psi,
+                                  const double* __restrict__ v, size_t ng, size_t n, const cx<T>* __restrict__ X,
+                                  T a) {
+  for (size_t e = size_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n; e += size_t(gridDim.x) * blockDim.x) {
+    const T vv = T(v[e % ng]);
+    cx<T> o = psi[e] * vv;
+    if (X) o = o + X[e] * a;
+    out[e] = o;
+  }
+}
+
+// Re sum conj(u_a) v over an orbital segment (weight w1, precision T) and a complex128 segment
+// (weight w2); one partial per block and vector, reduced by k_reduce_dots.
+constexpr int DOT_MAX = 24;
+struct DotArgs {
+  const void* u1[DOT_MAX];
+  const c128* u2[DOT_MAX];
+};
+
+template <class T>
+__global__ void k_multi_dot(DotArgs args, int m, const cx<T>* __restrict__ v1, size_t n1, const c128* __restrict__ v2,
+                            size_t n2, double w1, double w2, double* __restrict__ part) {
+  __shared__ double red[DOT_MAX][8];
+  Acc<T> s1[DOT_MAX];
+  double s[DOT_MAX];
+  const size_t stride = size_t(gridDim.x) * blockDim.x;
+  for (size_t e = size_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n1; e += stride) {
+    const cx<T> vv = v1[e];
+    // fixed trip count keeps the accumulators in registers; the guard skips absent vectors
+#pragma unroll
+    for (int a = 0; a < DOT_MAX; ++a) {
+      if (a < m) {
+        const cx<T> uu = static_cast<const cx<T>*>(args.u1[a])[e];
+        s1[a].add(fma(uu.re, vv.re, uu.im * vv.im));
+      }
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < DOT_MAX; ++a) s[a] = w1 * s1[a].value();
+  for (size_t e = size_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n2; e += stride) {
+    const c128 vv = v2[e];
+#pragma unroll
+    for (int a = 0; a < DOT_MAX; ++a) {
+      if (a < m) {
+        const c128 uu = args.u2[a][e];
+        s[a] += w2 * (uu.re * vv.re + uu.im * vv.im);
+      }
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int a = 0; a < DOT_MAX; ++a) {
+    double x = s[a];
+    for (int off = 16; off; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+    if (lane == 0) red[a][warp] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < m) {
+    double x = 0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) x += red[threadIdx.x][w];
+    part[size_t(threadIdx.x) * gridDim.x + blockIdx.x] = x;
+  }
+}
+
+__global__ void k_reduce_dots(const double* __restrict__ part, int nblk, int m, double* __restrict__ out) {
+  const int a = blockIdx.x;
+  double x = 0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) x += part[size_t(a) * nblk + b];
+  __shared__ double red[32];
+  for (int off = 16; off; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) t += red[w];
+    out[a] = t;
+  }
+}
+
+int stream_blocks(pt_ctx* ctx, size_t n, int threads) {
+  const size_t want = (n + threads - 1) / threads;
+  return int(std::max<size_t>(1, std::min<size_t>(want, size_t(ctx->num_sms) * 8)));
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+template <class T>
+void gram(pt_ctx* ctx, const cx<T>* A, const cx<T>* B, int N1, int N2, size_t ng, double scale, c128* C,
+          cudaStream_t st) {
+  const int ti = (N1 + GT - 1) / GT, tj = (N2 + GT - 1) / GT;
+  const int tiles = ti * tj;
+  // enough splits along r to fill the GPU about four times; chunks are multiples of GK
+  int splits = std::max(1, (ctx->num_sms * 4 + tiles - 1) / tiles);
+  size_t chunk = (ng + splits - 1) / splits;
+  chunk = (chunk + GK - 1) / GK * GK;
+  splits = int((ng + chunk - 1) / chunk);
+  c128* part = static_cast<c128*>(ctx->get("gram_parts", size_t(splits) * N1 * N2 * sizeof(c128)));
+  PT_LAUNCH(k_gram<T>, dim3(ti, tj, splits), GTHREADS, 0, st, A, B, N1, N2, ng, chunk, part);
+  const size_t n = size_t(N1) * N2;
+  PT_LAUNCH(k_reduce_parts, dim3(unsigned((n + 255) / 256)), 256, 0, st, part, splits, n, scale, C);
+}
+
+template <class T>
+void rotate(pt_ctx* ctx, const cx<T>* A, const c128* Bm, int ldb, int N1, int N2, size_t ng, c128 alpha,
+            const Term* terms, int nterms, cx<T>* out, cudaStream_t st) {
+  (void)ctx;
+  Epi<T> epi{};
+  for (int t = 0; t < 3; ++t) {
+    epi.e[t] = (t < nterms) ? static_cast<const cx<T>*>(terms[t].x) : nullptr;
+    epi.c[t] = (t < nterms) ? to_cx<T>(terms[t].c) : czero<T>();
+  }
+  dim3 grid(unsigned((ng + RT - 1) / RT), unsigned((N2 + JT - 1) / JT));
+  PT_LAUNCH(k_rotate<T>, grid, RTHREADS, 0, st, A, Bm, ldb, N1, N2, ng, to_cx<T>(alpha), epi, out);
+}
+
+template <class T>
+void lincomb(pt_ctx* ctx, cx<T>* out, size_t n, const Term* terms, int nterms, cudaStream_t st) {
+  Epi<T> t{};
+  for (int k = 0; k < 3; ++k) {
+    t.e[k] = (k < nterms) ? static_cast<const cx<T>*>(terms[k].x) : nullptr;
+    t.c[k] = (k < nterms) ? to_cx<T>(terms[k].c) : czero<T>();
+  }
+  const cx<T>* x3 = nterms > 3 ? static_cast<const cx<T>*>(terms[3].x) : nullptr;
+  const cx<T> c3 = nterms > 3 ? to_cx<T>(terms[3].c) : czero<T>();
+  PT_LAUNCH(k_lincomb<T>, stream_blocks(ctx, n, 256), 256, 0, st, out, n, t, x3, c3);
+}
+
+template <class T>
+void potential_apply(pt_ctx* ctx, cx<T>* out, const cx<T>* psi, const double* v, size_t ng, int M,
+                     const cx<T>* X, double a, cudaStream_t st) {
+  const size_t n = ng * size_t(M);
+  PT_LAUNCH(k_potential_apply<T>, stream_blocks(ctx, n, 256), 256, 0, st, out, psi, v, ng, n, X, T(a));
+}
+
+template <class T>
+void multi_dot(pt_ctx* ctx, const void* const* u1, const c128* const* u2, int m, const cx<T>* v1, size_t n1,
+               const c128* v2, size_t n2, double w1, double w2, double* out, cudaStream_t st) {
+  if (m > DOT_MAX) fail(PT_INVALID_ARG, "too many vectors in multi_dot");
+  if (m == 0) return;
+  DotArgs args{};
+  for (int a = 0; a < m; ++a) {
+    args.u1[a] = u1 ? u1[a] : nullptr;
+    args.u2[a] = u2 ? u2[a] : nullptr;
+  }
+  const int threads = 256;
+  const int nblk = std::max(1, std::min(ctx->num_sms * 4, int((n1 + threads - 1) / threads)));
+  double* part = static_cast<double*>(ctx->get("dot_parts", size_t(DOT_MAX) * nblk * sizeof(double)));
+  PT_LAUNCH(k_multi_dot<T>, nblk, threads, 0, st, args, m, v1, n1, v2, n2, w1, w2, part);
+  PT_LAUNCH(k_reduce_dots, m, 256, 0, st, part, nblk, m, out);
+}
+
+template void gram<float>(pt_ctx*, const c64*, const c64*, int, int, size_t, double, c128*, cudaStream_t);
+template void gram<double>(pt_ctx*, const c128*, const c128*, int, int, size_t, double, c128*, cudaStream_t);
+template void rotate<float>(pt_ctx*, const c64*, const c128*, int, int, int, size_t, c128, const Term*, int, c64*,
+                            cudaStream_t);
+template void rotate<double>(pt_ctx*, const c128*, const c128*, int, int, int, size_t, c128, const Term*, int,
+                             c128*, cudaStream_t);
+template void lincomb<float>(pt_ctx*, c64*, size_t, const Term*, int, cudaStream_t);
+template void lincomb<double>(pt_ctx*, c128*, size_t, const Term*, int, cudaStream_t);
+template void potential_apply<float>(pt_ctx*, c64*, const c64*, const double*, size_t, int, const c64*, double,
+                                     cudaStream_t);
+template void potential_apply<double>(pt_ctx*, c128*, const c128*, const double*, size_t, int, const c128*, double,
+                                      cudaStream_t);
+template void multi_dot<float>(pt_ctx*, const void* const*, const c128* const*, int, const c64*, size_t,
+                               const c128*, size_t, double, double, double*, cudaStream_t);
+template void multi_dot<double>(pt_ctx*, const void* const*, const c128* const*, int, const c128*, size_t,
+                                const c128*, size_t, double, double, double*, cudaStream_t);
+
+}  // namespace pt

@@ -1,0 +1,310 @@
+// The exported C ABI (include/ptim.h): argument checks, context, error conversion.
+#include <cstring>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace pt {
+
+std::atomic<long long> g_launches{0};
+
+void fail(pt_status code, const std::string& msg) { throw Error{code, msg}; }
+
+void check_cuda(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return;
+  if (e == cudaErrorMemoryAllocation) fail(PT_OOM, std::string(what) + ": " + cudaGetErrorString(e));
+  fail(PT_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void require_aligned(const void* p, const char* what) {
+  if (!p) fail(PT_INVALID_ARG, std::string(what) + " is NULL");
+  if (reinterpret_cast<uintptr_t>(p) % 16 != 0) fail(PT_INVALID_ARG, std::string(what) + " is not 16-byte aligned");
+}
+
+}  // namespace pt
+
+void* pt_ctx::get(const std::string& name, size_t bytes) {
+  auto it = bufs.find(name);
+  if (it != bufs.end() && it->second.bytes >= bytes) return it->second.ptr;
+  if (it != bufs.end()) {
+    pt::check_cuda(cudaDeviceSynchronize(), "workspace resize");
+    cudaFree(it->second.ptr);
+    held -= it->second.bytes;
+    bufs.erase(it);
+  }
+  bytes = std::max<size_t>(bytes, 256);
+  if (budget && held + bytes > budget)
+    pt::fail(PT_OOM, "workspace '" + name + "' of " + std::to_string(bytes) + " bytes exceeds the HBM budget");
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    pt::fail(PT_OOM, "cudaMalloc of workspace '" + name + "' (" + std::to_string(bytes) + " bytes) failed");
+  }
+  bufs[name] = pt::DevBuf{p, bytes};
+  held += bytes;
+  return p;
+}
+
+void pt_ctx::release_all() {
+  cudaDeviceSynchronize();
+  for (auto& kv : bufs) cudaFree(kv.second.ptr);
+  bufs.clear();
+  held = 0;
+}
+
+namespace {
+
+template <class F>
+pt_status guarded(pt_ctx* ctx, F&& f) {
+  try {
+    pt_status s = f();
+    if (ctx && s == PT_OK) ctx->err.clear();
+    return s;
+  } catch (const pt::Error& e) {
+    if (ctx) ctx->err = e.msg;
+    return e.code;
+  } catch (const std::exception& e) {
+    if (ctx) ctx->err = e.what();
+    return PT_CUDA;
+  }
+}
+
+void set_device(pt_ctx* ctx) { pt::check_cuda(cudaSetDevice(ctx->device), "cudaSetDevice"); }
+
+void check_common(pt_ctx* ctx, const pt_grid* grid, pt_precision prec) {
+  if (!ctx) pt::fail(PT_INVALID_ARG, "context is NULL");
+  pt::validate_grid(grid);
+  if (prec < PT_FP64 || prec > PT_FP32_TC_BF16) pt::fail(PT_INVALID_ARG, "unknown precision");
+}
+
+void check_kernel(const pt_kernel* k) {
+  if (!k) pt::fail(PT_INVALID_ARG, "kernel is NULL");
+  if (k->type != 0 && k->type != 1) pt::fail(PT_INVALID_ARG, "kernel type must be 0 or 1");
+  if (k->type == 1 && !(k->mu > 0)) pt::fail(PT_INVALID_ARG, "screened kernel needs mu > 0");
+}
+
+}  // namespace
+
+extern "C" {
+
+pt_status pt_create(pt_ctx** out, int device, size_t hbm_budget) {
+  if (!out) return PT_INVALID_ARG;
+  *out = nullptr;
+  auto* ctx = new pt_ctx();
+  pt_status s = guarded(ctx, [&]() -> pt_status {
+    int n = 0;
+    pt::check_cuda(cudaGetDeviceCount(&n), "cudaGetDeviceCount");
+    if (device < 0 || device >= n) pt::fail(PT_INVALID_ARG, "no such CUDA device");
+    ctx->device = device;
+    set_device(ctx);
+    cudaDeviceProp prop;
+    pt::check_cuda(cudaGetDeviceProperties(&prop, device), "cudaGetDeviceProperties");
+    ctx->num_sms = prop.multiProcessorCount;
+    ctx->max_smem_optin = prop.sharedMemPerBlockOptin;
+    size_t free_b = 0, total_b = 0;
+    pt::check_cuda(cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo");
+    ctx->budget = hbm_budget ? hbm_budget : size_t(0.9 * double(free_b));
+    pt::check_cuda(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    return PT_OK;
+  });
+  if (s != PT_OK) {
+    delete ctx;
+    return s;
+  }
+  *out = ctx;
+  return PT_OK;
+}
+
+void pt_destroy(pt_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  ctx->release_all();
+  ctx->caches.clear();
+  delete ctx;
+}
+
+const char* pt_last_error(const pt_ctx* ctx) { return ctx ? ctx->err.c_str() : "context is NULL"; }
+
+size_t pt_workspace_bytes(const pt_ctx* ctx) { return ctx ? ctx->held : 0; }
+
+pt_status pt_trim(pt_ctx* ctx) {
+  return guarded(ctx, [&]() -> pt_status {
+    if (!ctx) pt::fail(PT_INVALID_ARG, "context is NULL");
+    set_device(ctx);
+    ctx->release_all();
+    return PT_OK;
+  });
+}
+
+pt_status pt_set_option(pt_ctx* ctx, const char* key, double value) {
+  return guarded(ctx, [&]() -> pt_status {
+    if (!ctx || !key) pt::fail(PT_INVALID_ARG, "context or key is NULL");
+    if (std::string(key) == "scratch_bytes") {
+      if (!(value >= 1.0)) pt::fail(PT_INVALID_ARG, "scratch_bytes must be >= 1");
+      ctx->scratch_budget = size_t(value);
+      return PT_OK;
+    }
+    pt::fail(PT_INVALID_ARG, std::string("unknown option ") + key);
+  });
+}
+
+pt_status pt_apply_exchange(pt_ctx* ctx, const void* src, const double* occ, int N, const void* tgt, int M,
+                            void* out, const pt_grid* grid, const pt_kernel* kernel, pt_precision prec,
+                            void* stream) {
+  return guarded(ctx, [&]() -> pt_status {
+    check_common(ctx, grid, prec);
+    check_kernel(kernel);
+    if (N <= 0) pt::fail(PT_INVALID_ARG, "N must be positive");
+    if (tgt == nullptr) M = N;
+    if (M <= 0) pt::fail(PT_INVALID_ARG, "M must be positive");
+    pt::require_aligned(src, "src");
+    pt::require_aligned(out, "out");
+    if (!occ) pt::fail(PT_INVALID_ARG, "occ is NULL");
+    if (tgt) pt::require_aligned(tgt, "tgt");
+    if (out == src || (tgt && out == tgt)) pt::fail(PT_INVALID_ARG, "out must not alias src or tgt");
+    set_device(ctx);
+    pt::exchange(ctx, src, occ, N, tgt, M, out, *grid, *kernel, prec, static_cast<cudaStream_t>(stream));
+    return PT_OK;
+  });
+}
+
+pt_status pt_build_ace_from(pt_ctx* ctx, const void* W, const void* phi, int N, const pt_grid* grid,
+                            pt_precision prec, pt_ace** ace, void* stream) {
+  return guarded(ctx, [&]() -> pt_status {
+    check_common(ctx, grid, prec);
+    if (!ace) pt::fail(PT_INVALID_ARG, "ace is NULL");
+    *ace = nullptr;
+    if (N <= 0) pt::fail(PT_INVALID_ARG, "N must be positive");
+    pt::require_aligned(W, "W");
+    pt::require_aligned(phi, "phi");
+    set_device(ctx);
+    auto* a = new pt_ace();
+    a->ctx = ctx;
+    a->N = N;
+    a->grid = *grid;
+    a->prec = prec;
+    a->bytes = pt::ng_of(*grid) * N * pt::elem_bytes(prec);
+    cudaError_t e = cudaMalloc(&a->xi, a->bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      delete a;
+      pt::fail(PT_OOM, "cannot allocate the ACE vectors");
+    }
+    try {
+      pt::ace_from_w(ctx, W, phi, N, *grid, prec, a->xi, static_cast<cudaStream_t>(stream));
+    } catch (...) {
+      cudaFree(a->xi);
+      delete a;
+      throw;
+    }
+    *ace = a;
+    return PT_OK;
+  });
+}
+
+pt_status pt_build_ace(pt_ctx* ctx, const void* phi, const double* occ, int N, const pt_grid* grid,
+                       const pt_kernel* kernel, pt_precision prec, pt_ace** ace, void* stream) {
+  return guarded(ctx, [&]() -> pt_status {
+    check_common(ctx, grid, prec);
+    check_kernel(kernel);
+    if (!ace) pt::fail(PT_INVALID_ARG, "ace is NULL");
+    if (N <= 0) pt::fail(PT_INVALID_ARG, "N must be positive");
+    pt::require_aligned(phi, "phi");
+    if (!occ) pt::fail(PT_INVALID_ARG, "occ is NULL");
+    set_device(ctx);
+    const size_t bytes = pt::ng_of(*grid) * N * pt::elem_bytes(prec);
+    void* W = ctx->get("build_ace_W", bytes);
+    pt::exchange(ctx, phi, occ, N, nullptr, N, W, *grid, *kernel, prec, static_cast<cudaStream_t>(stream));
+    pt_status s = pt_build_ace_from(ctx, W, phi, N, grid, prec, ace, stream);
+    if (s != PT_OK) pt::fail(s, ctx->err);
+    return PT_OK;
+  });
+}
+
+pt_status pt_apply_ace(pt_ctx* ctx, const pt_ace* ace, const void* psi, int M, void* out, void* stream) {
+  return guarded(ctx, [&]() -> pt_status {
+    if (!ctx || !ace) pt::fail(PT_INVALID_ARG, "context or ACE is NULL");
+    if (M <= 0) pt::fail(PT_INVALID_ARG, "M must be positive");
+    pt::require_aligned(psi, "psi");
+    pt::require_aligned(out, "out");
+    if (out == psi) pt::fail(PT_INVALID_ARG, "out must not alias psi");
+    set_device(ctx);
+    pt::ace_apply(ctx, ace->xi, ace->N, psi, M, out, ace->grid, ace->prec, static_cast<cudaStream_t>(stream));
+    return PT_OK;
+  });
+}
+
+pt_status pt_ace_get_xi(const pt_ace* ace, void* xi_out, void* stream) {
+  if (!ace || !xi_out) return PT_INVALID_ARG;
+  cudaError_t e = cudaMemcpyAsync(xi_out, ace->xi, ace->bytes, cudaMemcpyDeviceToDevice,
+                                  static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? PT_OK : PT_CUDA;
+}
+
+void pt_ace_destroy(pt_ace* ace) {
+  if (!ace) return;
+  cudaFree(ace->xi);
+  delete ace;
+}
+
+pt_status pt_apply_H(pt_ctx* ctx, const void* psi, int M, void* out, const double* vloc, const pt_ace* ace,
+                     double alpha, double ecut, const pt_grid* grid, pt_precision prec, void* stream) {
+  return guarded(ctx, [&]() -> pt_status {
+    check_common(ctx, grid, prec);
+    if (M <= 0) pt::fail(PT_INVALID_ARG, "M must be positive");
+    pt::require_aligned(psi, "psi");
+    pt::require_aligned(out, "out");
+    if (!vloc) pt::fail(PT_INVALID_ARG, "vloc is NULL");
+    if (out == psi) pt::fail(PT_INVALID_ARG, "out must not alias psi");
+    if (ace && (ace->prec != prec || ace->grid.nx != grid->nx || ace->grid.ny != grid->ny || ace->grid.nz != grid->nz))
+      pt::fail(PT_INVALID_ARG, "ACE operator does not match the grid or precision");
+    set_device(ctx);
+    auto st = static_cast<cudaStream_t>(stream);
+    const void* X = nullptr;
+    if (ace) {
+      void* buf = ctx->get("apply_H_X", pt::ng_of(*grid) * M * pt::elem_bytes(prec));
+      pt::ace_apply(ctx, ace->xi, ace->N, psi, M, buf, *grid, prec, st);
+      X = buf;
+    }
+    pt::apply_h(ctx, psi, M, out, vloc, X, alpha, ecut, *grid, prec, st);
+    return PT_OK;
+  });
+}
+
+pt_status pt_diag_occupations(pt_ctx* ctx, const void* sigma, int N, void* Q, double* d, void* stream) {
+  return guarded(ctx, [&]() -> pt_status {
+    if (!ctx) pt::fail(PT_INVALID_ARG, "context is NULL");
+    if (N <= 0) pt::fail(PT_INVALID_ARG, "N must be positive");
+    if (!sigma || !Q || !d) pt::fail(PT_INVALID_ARG, "NULL buffer");
+    set_device(ctx);
+    pt::heev(ctx, static_cast<const c128*>(sigma), N, static_cast<c128*>(Q), d, static_cast<cudaStream_t>(stream));
+    return PT_OK;
+  });
+}
+
+pt_status pt_ptim_step(pt_ctx* ctx, void* phi, void* sigma, int N, const double* vloc, const pt_grid* grid,
+                       const pt_kernel* kernel, const pt_ptim_params* params, pt_precision prec,
+                       pt_ptim_stats* stats, void* stream) {
+  return guarded(ctx, [&]() -> pt_status {
+    check_common(ctx, grid, prec);
+    check_kernel(kernel);
+    if (!params) pt::fail(PT_INVALID_ARG, "params is NULL");
+    if (N <= 0) pt::fail(PT_INVALID_ARG, "N must be positive");
+    pt::require_aligned(phi, "phi");
+    pt::require_aligned(sigma, "sigma");
+    if (!vloc) pt::fail(PT_INVALID_ARG, "vloc is NULL");
+    const pt_ptim_params& P = *params;
+    if (!(P.dt > 0) || !(P.tol > 0) || P.max_inner <= 0 || P.max_outer <= 0 || P.anderson_depth <= 0 ||
+        P.anderson_depth > 20)
+      pt::fail(PT_INVALID_ARG, "invalid PT-IM parameters");
+    set_device(ctx);
+    return pt::ptim_step(ctx, phi, sigma, N, vloc, *grid, *kernel, P, prec, stats, static_cast<cudaStream_t>(stream));
+  });
+}
+
+const char* pt_version(void) { return "ptim-gb300 0.1 (sm_103a)"; }
+
+long long pt_kernel_launches(void) { return pt::g_launches.load(); }
+
+}  // extern "C"

@@ -1,0 +1,131 @@
+// Shared internals of the PT-IM library: complex arithmetic, the context with
+// its workspace arena, error handling and launch accounting.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/ptim.h"
+
+// ------------------------------------------------------------------------------------------
+// complex numbers (interleaved re, im; 8- or 16-byte aligned for vector loads)
+// ------------------------------------------------------------------------------------------
+template <class T>
+struct alignas(2 * sizeof(T)) cx {
+  T re, im;
+};
+
+template <class T> __host__ __device__ __forceinline__ cx<T> mk(T a, T b) { return cx<T>{a, b}; }
+template <class T> __host__ __device__ __forceinline__ cx<T> operator+(cx<T> a, cx<T> b) { return {a.re + b.re, a.im + b.im}; }
+template <class T> __host__ __device__ __forceinline__ cx<T> operator-(cx<T> a, cx<T> b) { return {a.re - b.re, a.im - b.im}; }
+template <class T> __host__ __device__ __forceinline__ cx<T> operator*(cx<T> a, T s) { return {a.re * s, a.im * s}; }
+template <class T> __host__ __device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+// conj(a) * b
+template <class T> __host__ __device__ __forceinline__ cx<T> cmulc(cx<T> a, cx<T> b) {
+  return {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re};
+}
+template <class T> __host__ __device__ __forceinline__ cx<T> conjc(cx<T> a) { return {a.re, -a.im}; }
+// acc += a * b
+template <class T> __host__ __device__ __forceinline__ void cfma(cx<T>& acc, cx<T> a, cx<T> b) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(-a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(a.im, b.re, acc.im);
+}
+// multiply by -i (forward) or +i (inverse)
+template <bool INV, class T> __host__ __device__ __forceinline__ cx<T> rot90(cx<T> a) {
+  return INV ? cx<T>{-a.im, a.re} : cx<T>{a.im, -a.re};
+}
+template <class T> __host__ __device__ __forceinline__ cx<T> czero() { return {T(0), T(0)}; }
+
+using c64 = cx<float>;
+using c128 = cx<double>;
+
+template <class T> __host__ __device__ __forceinline__ cx<T> to_cx(c128 a) { return {T(a.re), T(a.im)}; }
+
+// ------------------------------------------------------------------------------------------
+// errors, launches
+// ------------------------------------------------------------------------------------------
+namespace pt {
+
+extern std::atomic<long long> g_launches;
+
+struct Error {
+  pt_status code;
+  std::string msg;
+};
+
+// Throw inside the library; the C ABI entry points catch and convert to pt_status.
+[[noreturn]] void fail(pt_status code, const std::string& msg);
+void check_cuda(cudaError_t e, const char* what);
+
+#define PT_CUDA_CHECK(expr) ::pt::check_cuda((expr), #expr)
+// Launch a kernel, count it, and surface launch-configuration errors immediately.
+#define PT_LAUNCH(kernel, grid, block, smem, stream, ...)                          \
+  do {                                                                            \
+    kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);                   \
+    ::pt::g_launches.fetch_add(1, std::memory_order_relaxed);                     \
+    ::pt::check_cuda(cudaGetLastError(), #kernel);                                \
+  } while (0)
+
+// ------------------------------------------------------------------------------------------
+// context and workspace
+// ------------------------------------------------------------------------------------------
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+struct FftTables;  // per (grid, precision): twiddles, axis tables
+struct KernelTable;
+struct Schedule;
+
+}  // namespace pt
+
+struct pt_ctx {
+  int device = 0;
+  size_t budget = 0;
+  size_t held = 0;
+  int num_sms = 0;
+  size_t max_smem_optin = 0;
+  size_t scratch_budget = size_t(48) << 20;  // bytes of pair fields per exchange batch (L2-resident)
+  std::string err;
+  std::map<std::string, pt::DevBuf> bufs;
+  std::map<std::string, std::shared_ptr<void>> caches;  // keyed host-side caches of device tables
+
+  // Grow-only named workspace.  The returned pointer stays valid until the next
+  // get() of the same name with a larger size, or pt_trim.
+  void* get(const std::string& name, size_t bytes);
+  void release_all();
+};
+
+struct pt_ace {
+  pt_ctx* ctx = nullptr;
+  int N = 0;
+  pt_grid grid{};
+  pt_precision prec = PT_FP64;
+  void* xi = nullptr;  // Ng x N, precision prec
+  size_t bytes = 0;
+};
+
+namespace pt {
+
+inline size_t elem_bytes(pt_precision p) { return p == PT_FP64 ? sizeof(c128) : sizeof(c64); }
+inline bool is_fp32(pt_precision p) { return p != PT_FP64; }
+inline size_t ng_of(const pt_grid& g) { return size_t(g.nx) * g.ny * g.nz; }
+inline double dv_of(const pt_grid& g) { return g.L[0] * g.L[1] * g.L[2] / double(ng_of(g)); }
+
+void validate_grid(const pt_grid* g);
+void require_aligned(const void* p, const char* what);
+
+}  // namespace pt

@@ -1,0 +1,367 @@
+// FP64 dense linear algebra on N x N complex matrices (N up to a few hundred), on the GPU.
+//
+//   zgemm        C = alpha op(A) op(B) + beta C, op in {N, C (conjugate transpose), T}
+//   heev         Hermitian eigen-decomposition by parallel two-sided cyclic Jacobi
+//                (round-robin pairing; one launch per round; every 2x2 block of the
+//                matrix is updated by J_k^H X J_l in the same launch)
+//   cholesky     lower Cholesky, one rank-1 update launch per column, error flag on a
+//                non-positive or non-finite pivot
+//   tri_inv      L^{-1} of a lower-triangular matrix, one CTA per column
+//   small_solve  m x m (m <= 24) Gaussian elimination with partial pivoting, one thread
+// All matrices are row-major complex128: a[i*ld + j].
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace pt {
+
+namespace {
+
+__device__ __forceinline__ c128 opval(const c128* A, int lda, char op, int i, int k) {
+  // element (i, k) of op(A)
+  if (op == 'N') return A[size_t(i) * lda + k];
+  c128 v = A[size_t(k) * lda + i];
+  if (op == 'C') v.im = -v.im;
+  return v;
+}
+
+constexpr int ZT = 16;
+
+__global__ void __launch_bounds__(ZT* ZT) k_zgemm(char opA, char opB, int m, int n, int k, c128 alpha,
+                                                  const c128* __restrict__ A, int lda, const c128* __restrict__ B,
+                                                  int ldb, c128 beta, c128* __restrict__ C, int ldc) {
+  __shared__ c128 As[ZT][ZT + 1];
+  __shared__ c128 Bs[ZT][ZT + 1];
+  const int tx = threadIdx.x % ZT, ty = threadIdx.x / ZT;
+  const int i = blockIdx.y * ZT + ty, j = blockIdx.x * ZT + tx;
+  c128 acc = czero<double>();
+  for (int k0 = 0; k0 < k; k0 += ZT) {
+    const int ka = k0 + tx, kb = k0 + ty;
+    As[ty][tx] = (i < m && ka < k) ? opval(A, lda, opA, i, ka) : czero<double>();
+    Bs[ty][tx] = (kb < k && j < n) ? opval(B, ldb, opB, kb, j) : czero<double>();
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < ZT; ++kk) cfma(acc, As[ty][kk], Bs[kk][tx]);
+    __syncthreads();
+  }
+  if (i < m && j < n) {
+    c128 v = cmul(alpha, acc);
+    if (beta.re != 0.0 || beta.im != 0.0) v = v + cmul(beta, C[size_t(i) * ldc + j]);
+    C[size_t(i) * ldc + j] = v;
+  }
+}
+
+// ---------------------------------------------------------------- Jacobi ----
+// pair partner of position k in round r of the circle method on Np (even) players
+__device__ __forceinline__ void jacobi_pair(int k, int r, int Np, int* p, int* q) {
+  auto idx = [&](int i) { return i == 0 ? 0 : ((i - 1 + r) % (Np - 1)) + 1; };
+  const int a = idx(k), b = idx(Np - 1 - k);
+  *p = min(a, b);
+  *q = max(a, b);
+}
+
+struct Rot {
+  double c, s;
+  c128 u;  // J = [[c, s u], [-s conj(u), c]]
+};
+
+__device__ __forceinline__ Rot jacobi_rot(const c128* A, int N, int p, int q) {
+  Rot r{1.0, 0.0, c128{1.0, 0.0}};
+  if (q >= N) return r;  // padding player
+  const double app = A[size_t(p) * N + p].re, aqq = A[size_t(q) * N + q].re;
+  const c128 apq = A[size_t(p) * N + q];
+  const double b = hypot(apq.re, apq.im);
+  if (b == 0.0) return r;
+  const double zeta = (aqq - app) / (2.0 * b);
+  const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+  r.c = 1.0 / sqrt(1.0 + t * t);
+  r.s = t * r.c;
+  r.u = c128{apq.re / b, apq.im / b};
+  return r;
+}
+
+constexpr int JB = 16;  // pairs per CTA side (32 x 32 elements)
+
+__global__ void __launch_bounds__(JB* JB) k_jacobi_round(const c128* __restrict__ Ain, c128* __restrict__ Aout,
+                                                         c128* __restrict__ V, int N, int Np, int r) {
+  __shared__ Rot rk[JB], rl[JB];
+  __shared__ int pk[JB], qk[JB], pl[JB], ql[JB];
+  const int kb = blockIdx.y * JB, lb = blockIdx.x * JB;
+  const int half = Np / 2;
+  const int t = threadIdx.x;
+  if (t < JB) {
+    const int k = kb + t;
+    if (k < half) {
+      jacobi_pair(k, r, Np, &pk[t], &qk[t]);
+      rk[t] = jacobi_rot(Ain, N, pk[t], qk[t]);
+    }
+  } else if (t < 2 * JB) {
+    const int l = lb + t - JB;
+    if (l < half) {
+      jacobi_pair(l, r, Np, &pl[t - JB], &ql[t - JB]);
+      rl[t - JB] = jacobi_rot(Ain, N, pl[t - JB], ql[t - JB]);
+    }
+  }
+  __syncthreads();
+  const int tk = t / JB, tl = t % JB;
+  const int k = kb + tk, l = lb + tl;
+  if (k < half && l < half) {
+    const int p1 = pk[tk], q1 = qk[tk], p2 = pl[tl], q2 = ql[tl];
+    const Rot a = rk[tk], b = rl[tl];
+    auto get = [&](int i, int j) -> c128 {
+      return (i < N && j < N) ? Ain[size_t(i) * N + j] : czero<double>();
+    };
+    const c128 x00 = get(p1, p2), x01 = get(p1, q2), x10 = get(q1, p2), x11 = get(q1, q2);
+    // Y = J_a^H X:  J^H = [[c, -s u], [s conj(u), c]]
+    const c128 su = a.u * a.s, suc = conjc(a.u) * a.s;
+    const c128 y00 = x00 * a.c - cmul(su, x10), y01 = x01 * a.c - cmul(su, x11);
+    const c128 y10 = cmul(suc, x00) + x10 * a.c, y11 = cmul(suc, x01) + x11 * a.c;
+    // Z = Y J_b:  J = [[c, s u], [-s conj(u), c]]
+    const c128 tu = b.u * b.s, tuc = conjc(b.u) * b.s;
+    c128 z00 = y00 * b.c - cmul(y01, tuc), z01 = cmul(y00, tu) + y01 * b.c;
+    c128 z10 = y10 * b.c - cmul(y11, tuc), z11 = cmul(y10, tu) + y11 * b.c;
+    if (k == l) {  // the 2x2 block this rotation diagonalises
+      z01 = czero<double>();
+      z10 = czero<double>();
+      z00.im = 0.0;
+      z11.im = 0.0;
+    }
+    auto put = [&](int i, int j, c128 v) {
+      if (i < N && j < N) Aout[size_t(i) * N + j] = v;
+    };
+    put(p1, p2, z00);
+    put(p1, q2, z01);
+    put(q1, p2, z10);
+    put(q1, q2, z11);
+  }
+  // V <- V J for the column pairs of this CTA's l-range, rows split across the k-range CTAs
+  if (blockIdx.y == 0) {
+    for (int e = t; e < N * JB; e += JB * JB) {
+      const int row = e / JB, tl2 = e % JB;
+      const int l2 = lb + tl2;
+      if (l2 >= half) continue;
+      const int p2 = pl[tl2], q2 = ql[tl2];
+      if (q2 >= N) continue;
+      const Rot b = rl[tl2];
+      const c128 vp = V[size_t(row) * N + p2], vq = V[size_t(row) * N + q2];
+      const c128 tu = b.u * b.s, tuc = conjc(b.u) * b.s;
+      V[size_t(row) * N + p2] = vp * b.c - cmul(vq, tuc);
+      V[size_t(row) * N + q2] = cmul(vp, tu) + vq * b.c;
+    }
+  }
+}
+
+__global__ void k_herm_part_and_identity(const c128* __restrict__ S, c128* __restrict__ A, c128* __restrict__ V,
+                                         int N) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= N * N) return;
+  const int i = e / N, j = e % N;
+  const c128 a = S[size_t(i) * N + j], b = S[size_t(j) * N + i];
+  A[e] = c128{0.5 * (a.re + b.re), 0.5 * (a.im - b.im)};
+  V[e] = c128{i == j ? 1.0 : 0.0, 0.0};
+}
+
+// sums of |offdiag|^2 and |all|^2 (one block)
+__global__ void k_offnorm(const c128* __restrict__ A, int N, double* __restrict__ out) {
+  double off = 0, all = 0;
+  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+    const double v = A[e].re * A[e].re + A[e].im * A[e].im;
+    all += v;
+    if (e / N != e % N) off += v;
+  }
+  __shared__ double so[32], sa[32];
+  for (int o = 16; o; o >>= 1) {
+    off += __shfl_down_sync(0xffffffffu, off, o);
+    all += __shfl_down_sync(0xffffffffu, all, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    so[threadIdx.x >> 5] = off;
+    sa[threadIdx.x >> 5] = all;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, b = 0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) {
+      a += so[w];
+      b += sa[w];
+    }
+    out[0] = a;
+    out[1] = b;
+  }
+}
+
+// ascending sort of the diagonal with the matching columns of V (one block, rank sort)
+__global__ void k_sort_eig(const c128* __restrict__ A, const c128* __restrict__ V, int N, c128* __restrict__ Q,
+                           double* __restrict__ d) {
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const double di = A[size_t(i) * N + i].re;
+    int rank = 0;
+    for (int j = 0; j < N; ++j) {
+      const double dj = A[size_t(j) * N + j].re;
+      rank += (dj < di) || (dj == di && j < i);
+    }
+    d[rank] = di;
+    for (int row = 0; row < N; ++row) Q[size_t(row) * N + rank] = V[size_t(row) * N + i];
+  }
+}
+
+// ---------------------------------------------------------------- Cholesky ----
+__global__ void k_chol_step(c128* __restrict__ A, int N, int k, int* __restrict__ info) {
+  if (*info) return;
+  const double piv = A[size_t(k) * N + k].re;
+  if (!(piv > 0.0) || !isfinite(piv)) {
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *info = k + 1;
+    return;
+  }
+  const int i = k + 1 + blockIdx.y * 16 + threadIdx.x / 16;
+  const int j = k + 1 + blockIdx.x * 16 + threadIdx.x % 16;
+  if (i >= N || j > i) return;
+  const c128 aik = A[size_t(i) * N + k], ajk = A[size_t(j) * N + k];
+  const c128 upd = cmulc(ajk, aik);  // A[i][k] conj(A[j][k])
+  A[size_t(i) * N + j] = A[size_t(i) * N + j] - upd * (1.0 / piv);
+}
+
+__global__ void k_chol_finish(const c128* __restrict__ A, int N, c128* __restrict__ L, const int* __restrict__ info) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= N * N || *info) return;
+  const int i = e / N, j = e % N;
+  if (j > i) {
+    L[e] = czero<double>();
+    return;
+  }
+  const double dj = sqrt(A[size_t(j) * N + j].re);
+  L[e] = (i == j) ? c128{dj, 0.0} : A[e] * (1.0 / dj);
+}
+
+// X = L^{-1}, column c per CTA (forward substitution, column-oriented)
+__global__ void k_tri_inv_lower(const c128* __restrict__ L, int N, c128* __restrict__ X) {
+  extern __shared__ c128 b[];
+  const int c = blockIdx.x;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) b[i] = c128{i == c ? 1.0 : 0.0, 0.0};
+  __syncthreads();
+  for (int k = c; k < N; ++k) {
+    const c128 lkk = L[size_t(k) * N + k];
+    const double den = lkk.re * lkk.re + lkk.im * lkk.im;
+    const c128 xk = cmul(b[k], c128{lkk.re / den, -lkk.im / den});
+    __syncthreads();
+    if (threadIdx.x == 0) b[k] = xk;
+    for (int i = k + 1 + threadIdx.x; i < N; i += blockDim.x) b[i] = b[i] - cmul(L[size_t(i) * N + k], xk);
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < N; i += blockDim.x) X[size_t(i) * N + c] = (i < c) ? czero<double>() : b[i];
+}
+
+// out = U diag(f(lam)) (scale columns), f = lam^power
+__global__ void k_scale_cols_pow(const c128* __restrict__ U, const double* __restrict__ lam, int N, double power,
+                                 c128* __restrict__ out, int* __restrict__ info) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= N * N) return;
+  const int j = e % N;
+  const double l = lam[j];
+  if (!(l > 0.0)) {
+    *info = 1;
+    out[e] = czero<double>();
+    return;
+  }
+  out[e] = U[e] * pow(l, power);
+}
+
+__global__ void k_small_solve(const double* __restrict__ G, const double* __restrict__ rhs, int m, double reg,
+                              double* __restrict__ x) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double a[24][25];
+  double tr = 0;
+  for (int i = 0; i < m; ++i) tr += G[i * m + i];
+  const double shift = reg * (tr > 0 ? tr / m : 1.0);
+  for (int i = 0; i < m; ++i) {
+    for (int j = 0; j < m; ++j) a[i][j] = G[i * m + j] + (i == j ? shift : 0.0);
+    a[i][m] = rhs[i];
+  }
+  for (int c = 0; c < m; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < m; ++r)
+      if (fabs(a[r][c]) > fabs(a[piv][c])) piv = r;
+    if (piv != c)
+      for (int j = c; j <= m; ++j) {
+        const double t = a[c][j];
+        a[c][j] = a[piv][j];
+        a[piv][j] = t;
+      }
+    const double d = a[c][c];
+    if (d == 0.0) continue;
+    for (int r = c + 1; r < m; ++r) {
+      const double f = a[r][c] / d;
+      for (int j = c; j <= m; ++j) a[r][j] -= f * a[c][j];
+    }
+  }
+  for (int c = m - 1; c >= 0; --c) {
+    double s = a[c][m];
+    for (int j = c + 1; j < m; ++j) s -= a[c][j] * x[j];
+    x[c] = (a[c][c] != 0.0) ? s / a[c][c] : 0.0;
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+void zgemm(char opA, char opB, int m, int n, int k, c128 alpha, const c128* A, int lda, const c128* B, int ldb,
+           c128 beta, c128* C, int ldc, cudaStream_t st) {
+  dim3 grid((n + ZT - 1) / ZT, (m + ZT - 1) / ZT);
+  PT_LAUNCH(k_zgemm, grid, ZT * ZT, 0, st, opA, opB, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+}
+
+void heev(pt_ctx* ctx, const c128* S, int N, c128* Q, double* d, cudaStream_t st, int max_sweeps) {
+  const int Np = N + (N & 1);
+  c128* A0 = static_cast<c128*>(ctx->get("heev_A0", size_t(N) * N * sizeof(c128)));
+  c128* A1 = static_cast<c128*>(ctx->get("heev_A1", size_t(N) * N * sizeof(c128)));
+  c128* V = static_cast<c128*>(ctx->get("heev_V", size_t(N) * N * sizeof(c128)));
+  double* nrm = static_cast<double*>(ctx->get("heev_norm", 2 * sizeof(double)));
+  PT_LAUNCH(k_herm_part_and_identity, (N * N + 255) / 256, 256, 0, st, S, A0, V, N);
+  const int half = Np / 2;
+  dim3 grid((half + JB - 1) / JB, (half + JB - 1) / JB);
+  double h[2] = {0, 0};
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    PT_LAUNCH(k_offnorm, 1, 1024, 0, st, A0, N, nrm);
+    PT_CUDA_CHECK(cudaMemcpyAsync(h, nrm, sizeof(h), cudaMemcpyDeviceToHost, st));
+    PT_CUDA_CHECK(cudaStreamSynchronize(st));
+    if (!std::isfinite(h[1])) fail(PT_NONFINITE, "non-finite entry in the matrix to diagonalise");
+    if (h[0] <= 1e-30 * h[1] || h[0] == 0.0) break;
+    for (int r = 0; r < Np - 1; ++r) {
+      PT_LAUNCH(k_jacobi_round, grid, JB * JB, 0, st, A0, A1, V, N, Np, r);
+      std::swap(A0, A1);
+    }
+  }
+  PT_LAUNCH(k_sort_eig, 1, 256, 0, st, A0, V, N, Q, d);
+}
+
+void cholesky(pt_ctx* ctx, c128* A, int N, c128* L, int* info, cudaStream_t st) {
+  (void)ctx;
+  PT_CUDA_CHECK(cudaMemsetAsync(info, 0, sizeof(int), st));
+  for (int k = 0; k < N; ++k) {
+    const int rem = N - k - 1;
+    if (rem <= 0) {
+      // the last pivot is still checked by finish through the diagonal
+      PT_LAUNCH(k_chol_step, dim3(1, 1), 256, 0, st, A, N, k, info);
+      break;
+    }
+    dim3 grid((rem + 15) / 16, (rem + 15) / 16);
+    PT_LAUNCH(k_chol_step, grid, 256, 0, st, A, N, k, info);
+  }
+  PT_LAUNCH(k_chol_finish, (N * N + 255) / 256, 256, 0, st, A, N, L, info);
+}
+
+void tri_inv_lower(const c128* L, int N, c128* X, cudaStream_t st) {
+  PT_LAUNCH(k_tri_inv_lower, N, 128, size_t(N) * sizeof(c128), st, L, N, X);
+}
+
+void scale_cols_pow(const c128* U, const double* lam, int N, double power, c128* out, int* info, cudaStream_t st) {
+  PT_LAUNCH(k_scale_cols_pow, (N * N + 255) / 256, 256, 0, st, U, lam, N, power, out, info);
+}
+
+void small_solve(const double* G, const double* rhs, int m, double reg, double* x, cudaStream_t st) {
+  if (m > 24) fail(PT_INVALID_ARG, "small_solve supports m <= 24");
+  PT_LAUNCH(k_small_solve, 1, 32, 0, st, G, rhs, m, reg, x);
+}
+
+}  // namespace pt

@@ -1,0 +1,336 @@
+// Occupation-weighted screened Fock exchange  W_j = V_x tgt_j  (Sec. IV-A1, Eq. vxdiag).
+//
+// For every pair (i, j):  rho = conj(src_i) tgt_j -> FFT -> * K(G)/Ng -> IFFT -> v_ij,
+// then W_j -= d_i src_i v_ij.  Pairs are processed in batches whose pair fields
+// (one Ng-point scratch field per pair) stay resident in L2 between the three
+// passes of the 3-D FFT:
+//   pass 1 (plane):   pair product and the x, y transforms of one z-plane;
+//   pass 2 (column):  forward z transform, kernel multiply, inverse z transform;
+//   pass 3 (plane):   inverse y, x transforms and the d_i-weighted accumulate of
+//                     every pair of the batch that contributes to one target plane.
+// With tgt == src the kernel symmetry v_ji = conj(v_ij) (K real and even) lets
+// one pair FFT serve both W_j (with d_i src_i) and W_i (with d_j src_j conj v).
+// Pairs whose every contribution has d = 0 are skipped on the device.
+#include <algorithm>
+#include <cstring>
+
+#include "fft.cuh"
+#include "internal.h"
+
+namespace pt {
+
+namespace {
+
+constexpr int NT = 512;          // threads per CTA of the tile kernels
+constexpr int MAXE = kMaxDim * kMaxDim;  // tile elements (64 x 64)
+constexpr int EPT = (MAXE + NT - 1) / NT;
+
+struct PairDesc {
+  int i, j;    // source index, target index
+  int o1, o2;  // occupation indices of its contributions (o2 < 0: a single one)
+};
+struct TargetDesc {
+  int t, cbeg, cend, first;
+};
+struct Contrib {
+  int slot, partner, occ, conj;
+};
+
+__device__ __forceinline__ bool pair_skipped(const PairDesc& pd, const double* occ) {
+  return occ[pd.o1] == 0.0 && (pd.o2 < 0 || occ[pd.o2] == 0.0);
+}
+
+template <class T>
+__device__ __forceinline__ void load_twiddles(cx<T>* tw, const cx<T>* twg, int n) {
+  for (int t = threadIdx.x; t < n; t += blockDim.x) tw[t] = twg[t];
+}
+
+// pass 1: rho = conj(src_i) tgt_j on plane z, then FFT along x and y
+template <class T>
+__global__ void __launch_bounds__(NT) k_pair_fwd_plane(GridPlan gp, const cx<T>* __restrict__ src,
+                                                       const cx<T>* __restrict__ tgt,
+                                                       const double* __restrict__ occ,
+                                                       const PairDesc* __restrict__ pairs,
+                                                       cx<T>* __restrict__ scratch,
+                                                       const cx<T>* __restrict__ twg) {
+  extern __shared__ unsigned char smem_raw[];
+  cx<T>* tw = reinterpret_cast<cx<T>*>(smem_raw);
+  cx<T>* buf = tw + 3 * kMaxDim;
+  const int z = blockIdx.x, p = blockIdx.y;
+  const PairDesc pd = pairs[p];
+  if (pair_skipped(pd, occ)) return;
+  const int nx = gp.nx, ny = gp.ny, pitch = gp.pitch_x;
+  const int plane = nx * ny;
+  const size_t ng = size_t(plane) * gp.nz;
+  load_twiddles(tw, twg, nx + ny + gp.nz);
+  const cx<T>* a = src + size_t(pd.i) * ng + size_t(z) * plane;
+  const cx<T>* b = tgt + size_t(pd.j) * ng + size_t(z) * plane;
+  for (int e = threadIdx.x; e < plane; e += NT) {
+    const int y = e / nx, x = e - y * nx;
+    buf[y * pitch + x] = cmulc(a[e], b[e]);
+  }
+  __syncthreads();
+  fft_lines<false, NT, MAXE>(buf, gp.ax[0], ny, pitch, 1, tw);       // x
+  fft_lines<false, NT, MAXE>(buf, gp.ax[1], nx, 1, pitch, tw + nx);  // y
+  cx<T>* o = scratch + size_t(p) * ng + size_t(z) * plane;
+  for (int e = threadIdx.x; e < plane; e += NT) {
+    const int y = e / nx, x = e - y * nx;
+    o[e] = buf[y * pitch + x];
+  }
+}
+
+// pass 2: on the (z, x) slab of row y: FFT along z, multiply by K/Ng, inverse FFT along z
+template <class T>
+__global__ void __launch_bounds__(NT) k_pair_column(GridPlan gp, cx<T>* __restrict__ scratch,
+                                                    const T* __restrict__ ktab,
+                                                    const double* __restrict__ occ,
+                                                    const PairDesc* __restrict__ pairs,
+                                                    const cx<T>* __restrict__ twg) {
+  extern __shared__ unsigned char smem_raw[];
+  cx<T>* tw = reinterpret_cast<cx<T>*>(smem_raw);
+  cx<T>* buf = tw + 3 * kMaxDim;
+  const int y = blockIdx.x, p = blockIdx.y;
+  const PairDesc pd = pairs[p];
+  if (pair_skipped(pd, occ)) return;
+  const int nx = gp.nx, ny = gp.ny, nz = gp.nz, pitch = gp.pitch_x;
+  const size_t ng = size_t(nx) * ny * nz;
+  load_twiddles(tw, twg, nx + ny + nz);
+  cx<T>* f = scratch + size_t(p) * ng;
+  const int slab = nz * nx;
+  for (int e = threadIdx.x; e < slab; e += NT) {
+    const int z = e / nx, x = e - z * nx;
+    buf[z * pitch + x] = f[(size_t(z) * ny + y) * nx + x];
+  }
+  __syncthreads();
+  fft_lines<false, NT, MAXE>(buf, gp.ax[2], nx, 1, pitch, tw + nx + ny);
+  for (int e = threadIdx.x; e < slab; e += NT) {
+    const int z = e / nx, x = e - z * nx;
+    buf[z * pitch + x] = buf[z * pitch + x] * ktab[(size_t(z) * ny + y) * nx + x];
+  }
+  __syncthreads();
+  fft_lines<true, NT, MAXE>(buf, gp.ax[2], nx, 1, pitch, tw + nx + ny);
+  for (int e = threadIdx.x; e < slab; e += NT) {
+    const int z = e / nx, x = e - z * nx;
+    f[(size_t(z) * ny + y) * nx + x] = buf[z * pitch + x];
+  }
+}
+
+// pass 3: for target t and plane z, inverse y/x FFT of each contributing pair and
+// acc += d * partner * v (v conjugated for the mirrored half of a symmetric pair)
+template <class T>
+__global__ void __launch_bounds__(NT) k_pair_inv_acc(GridPlan gp, const cx<T>* __restrict__ scratch,
+                                                     const cx<T>* __restrict__ src,
+                                                     const double* __restrict__ occ,
+                                                     const TargetDesc* __restrict__ tgts,
+                                                     const Contrib* __restrict__ contribs,
+                                                     cx<T>* __restrict__ out,
+                                                     const cx<T>* __restrict__ twg) {
+  extern __shared__ unsigned char smem_raw[];
+  cx<T>* tw = reinterpret_cast<cx<T>*>(smem_raw);
+  cx<T>* buf = tw + 3 * kMaxDim;
+  const int z = blockIdx.x;
+  const TargetDesc td = tgts[blockIdx.y];
+  const int nx = gp.nx, ny = gp.ny, pitch = gp.pitch_x;
+  const int plane = nx * ny;
+  const size_t ng = size_t(plane) * gp.nz;
+  load_twiddles(tw, twg, nx + ny + gp.nz);
+  cx<T> acc[EPT];
+#pragma unroll
+  for (int u = 0; u < EPT; ++u) acc[u] = czero<T>();
+  for (int c = td.cbeg; c < td.cend; ++c) {
+    const Contrib cb = contribs[c];
+    const T coef = T(occ[cb.occ]);
+    if (coef == T(0)) continue;
+    const cx<T>* f = scratch + size_t(cb.slot) * ng + size_t(z) * plane;
+    for (int e = threadIdx.x; e < plane; e += NT) {
+      const int y = e / nx, x = e - y * nx;
+      buf[y * pitch + x] = f[e];
+    }
+    __syncthreads();
+    fft_lines<true, NT, MAXE>(buf, gp.ax[1], nx, 1, pitch, tw + nx);  // y
+    fft_lines<true, NT, MAXE>(buf, gp.ax[0], ny, pitch, 1, tw);       // x
+    const cx<T>* pp = src + size_t(cb.partner) * ng + size_t(z) * plane;
+#pragma unroll
+    for (int u = 0; u < EPT; ++u) {
+      const int e = threadIdx.x + u * NT;
+      if (e < plane) {
+        const int y = e / nx, x = e - y * nx;
+        cx<T> v = buf[y * pitch + x];
+        if (cb.conj) v.im = -v.im;
+        acc[u] = acc[u] + cmul(pp[e], v) * coef;
+      }
+    }
+    __syncthreads();
+  }
+  cx<T>* o = out + size_t(td.t) * ng + size_t(z) * plane;
+#pragma unroll
+  for (int u = 0; u < EPT; ++u) {
+    const int e = threadIdx.x + u * NT;
+    if (e < plane) o[e] = td.first ? czero<T>() - acc[u] : o[e] - acc[u];
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// host: pair schedule
+// ------------------------------------------------------------------------------------------
+struct ScheduleImpl {
+  int N = 0, M = 0, B = 0;
+  bool sym = false;
+  std::vector<int> pair_off, tgt_off;  // per batch offsets (size nbatch+1)
+  PairDesc* d_pairs = nullptr;
+  TargetDesc* d_tgts = nullptr;
+  Contrib* d_contribs = nullptr;
+  int max_pairs = 0, max_tgts = 0;
+  long long total_pairs = 0;
+  ~ScheduleImpl() {
+    cudaFree(d_pairs);
+    cudaFree(d_tgts);
+    cudaFree(d_contribs);
+  }
+};
+
+std::shared_ptr<ScheduleImpl> build_schedule(int N, int M, bool sym, int B) {
+  auto s = std::make_shared<ScheduleImpl>();
+  s->N = N;
+  s->M = M;
+  s->B = B;
+  s->sym = sym;
+  std::vector<PairDesc> pairs;
+  std::vector<TargetDesc> tgts;
+  std::vector<Contrib> cons;
+  std::vector<char> touched(sym ? N : M, 0);
+  s->pair_off.push_back(0);
+  s->tgt_off.push_back(0);
+  auto finish_batch = [&](std::map<int, std::vector<Contrib>>& per_t) {
+    for (auto& kv : per_t) {
+      TargetDesc td;
+      td.t = kv.first;
+      td.cbeg = int(cons.size());
+      for (auto& c : kv.second) cons.push_back(c);
+      td.cend = int(cons.size());
+      td.first = touched[kv.first] ? 0 : 1;
+      touched[kv.first] = 1;
+      tgts.push_back(td);
+    }
+    s->max_pairs = std::max(s->max_pairs, int(pairs.size()) - s->pair_off.back());
+    s->max_tgts = std::max(s->max_tgts, int(tgts.size()) - s->tgt_off.back());
+    s->pair_off.push_back(int(pairs.size()));
+    s->tgt_off.push_back(int(tgts.size()));
+  };
+  if (sym) {
+    const int nb = (N + B - 1) / B;
+    for (int J = 0; J < nb; ++J) {
+      for (int I = 0; I <= J; ++I) {
+        std::map<int, std::vector<Contrib>> per_t;
+        const int base = int(pairs.size());
+        const int i0 = I * B, i1 = std::min(N, i0 + B), j0 = J * B, j1 = std::min(N, j0 + B);
+        for (int i = i0; i < i1; ++i) {
+          for (int j = (I == J ? i : j0); j < j1; ++j) {
+            const int slot = int(pairs.size()) - base;
+            pairs.push_back({i, j, i, i == j ? -1 : j});
+            per_t[j].push_back({slot, i, i, 0});
+            if (i != j) per_t[i].push_back({slot, j, j, 1});
+          }
+        }
+        finish_batch(per_t);
+      }
+    }
+  } else {
+    const int nbi = (N + B - 1) / B, nbj = (M + B - 1) / B;
+    for (int J = 0; J < nbj; ++J) {
+      for (int I = 0; I < nbi; ++I) {
+        std::map<int, std::vector<Contrib>> per_t;
+        const int base = int(pairs.size());
+        const int i0 = I * B, i1 = std::min(N, i0 + B), j0 = J * B, j1 = std::min(M, j0 + B);
+        for (int j = j0; j < j1; ++j) {
+          for (int i = i0; i < i1; ++i) {
+            const int slot = int(pairs.size()) - base;
+            pairs.push_back({i, j, i, -1});
+            per_t[j].push_back({slot, i, i, 0});
+          }
+        }
+        finish_batch(per_t);
+      }
+    }
+  }
+  s->total_pairs = (long long)pairs.size();
+  PT_CUDA_CHECK(cudaMalloc(&s->d_pairs, pairs.size() * sizeof(PairDesc)));
+  PT_CUDA_CHECK(cudaMalloc(&s->d_tgts, tgts.size() * sizeof(TargetDesc)));
+  PT_CUDA_CHECK(cudaMalloc(&s->d_contribs, cons.size() * sizeof(Contrib)));
+  PT_CUDA_CHECK(cudaMemcpy(s->d_pairs, pairs.data(), pairs.size() * sizeof(PairDesc), cudaMemcpyHostToDevice));
+  PT_CUDA_CHECK(cudaMemcpy(s->d_tgts, tgts.data(), tgts.size() * sizeof(TargetDesc), cudaMemcpyHostToDevice));
+  PT_CUDA_CHECK(cudaMemcpy(s->d_contribs, cons.data(), cons.size() * sizeof(Contrib), cudaMemcpyHostToDevice));
+  return s;
+}
+
+size_t tile_smem_bytes(size_t esize) { return (3 * kMaxDim + size_t(kMaxDim) * (kMaxDim + 1)) * esize; }
+
+template <class T>
+void set_smem_attrs() {
+  static bool done = false;
+  if (done) return;
+  const int bytes = int(tile_smem_bytes(sizeof(cx<T>)));
+  PT_CUDA_CHECK(cudaFuncSetAttribute(k_pair_fwd_plane<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  PT_CUDA_CHECK(cudaFuncSetAttribute(k_pair_column<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  PT_CUDA_CHECK(cudaFuncSetAttribute(k_pair_inv_acc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  done = true;
+}
+
+template <class T>
+long long exchange_t(pt_ctx* ctx, const cx<T>* src, const double* occ, int N, const cx<T>* tgt, int M,
+                     cx<T>* out, const pt_grid& g, const pt_kernel& k, pt_precision prec, cudaStream_t st) {
+  const bool sym = (tgt == nullptr);
+  if (sym) {
+    tgt = src;
+    M = N;
+  }
+  const FftTables& ft = fft_tables(ctx, g, prec);
+  const T* ktab = static_cast<const T*>(kernel_table(ctx, g, k, prec));
+  const size_t ng = ng_of(g);
+  const size_t field = ng * sizeof(cx<T>);
+  // Pair batch: as many pair fields as fit a budget that keeps them L2-resident.
+  const size_t budget = exchange_scratch_budget(ctx);
+  int B = int(std::floor(std::sqrt(double(std::max<size_t>(1, budget / field)))));
+  B = std::max(1, std::min(B, std::max(N, M)));
+  char key[128];
+  snprintf(key, sizeof(key), "sched:%d:%d:%d:%d", N, M, int(sym), B);
+  auto it = ctx->caches.find(key);
+  std::shared_ptr<ScheduleImpl> sch;
+  if (it == ctx->caches.end()) {
+    sch = build_schedule(N, M, sym, B);
+    ctx->caches[key] = sch;
+  } else {
+    sch = std::static_pointer_cast<ScheduleImpl>(it->second);
+  }
+  cx<T>* scratch = static_cast<cx<T>*>(ctx->get("exchange_scratch", size_t(sch->max_pairs) * field));
+  set_smem_attrs<T>();
+  const size_t smem = tile_smem_bytes(sizeof(cx<T>));
+  const cx<T>* twg = static_cast<const cx<T>*>(ft.tw);
+  const int nbatch = int(sch->pair_off.size()) - 1;
+  for (int b = 0; b < nbatch; ++b) {
+    const int p0 = sch->pair_off[b], np = sch->pair_off[b + 1] - p0;
+    const int t0 = sch->tgt_off[b], nt = sch->tgt_off[b + 1] - t0;
+    PT_LAUNCH(k_pair_fwd_plane<T>, dim3(g.nz, np), NT, smem, st, ft.plan, src, tgt, occ, sch->d_pairs + p0,
+              scratch, twg);
+    PT_LAUNCH(k_pair_column<T>, dim3(g.ny, np), NT, smem, st, ft.plan, scratch, ktab, occ, sch->d_pairs + p0,
+              twg);
+    PT_LAUNCH(k_pair_inv_acc<T>, dim3(g.nz, nt), NT, smem, st, ft.plan, scratch, src, occ, sch->d_tgts + t0,
+              sch->d_contribs, out, twg);
+  }
+  return sch->total_pairs;
+}
+
+}  // namespace
+
+size_t exchange_scratch_budget(const pt_ctx* ctx) { return ctx->scratch_budget; }
+
+long long exchange(pt_ctx* ctx, const void* src, const double* occ, int N, const void* tgt, int M, void* out,
+                   const pt_grid& g, const pt_kernel& k, pt_precision prec, cudaStream_t st) {
+  if (prec == PT_FP64)
+    return exchange_t<double>(ctx, static_cast<const c128*>(src), occ, N, static_cast<const c128*>(tgt), M,
+                              static_cast<c128*>(out), g, k, prec, st);
+  return exchange_t<float>(ctx, static_cast<const c64*>(src), occ, N, static_cast<const c64*>(tgt), M,
+                           static_cast<c64*>(out), g, k, prec, st);
+}
+
+}  // namespace pt

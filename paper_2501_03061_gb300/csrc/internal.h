@@ -1,0 +1,67 @@
+// Declarations shared between the translation units of the library (not part of the ABI).
+#pragma once
+
+#include "common.cuh"
+
+namespace pt {
+
+// linear-combination term: coefficient c times the orbital block x (precision of the call)
+struct Term {
+  const void* x;
+  c128 c;
+};
+
+// ---- exchange (exchange.cu) ----
+size_t exchange_scratch_budget(const pt_ctx* ctx);
+// W = V_x tgt (tgt == nullptr: tgt = src, symmetric pairs).  Returns the number of pair FFTs.
+long long exchange(pt_ctx* ctx, const void* src, const double* occ, int N, const void* tgt, int M, void* out,
+                   const pt_grid& g, const pt_kernel& k, pt_precision prec, cudaStream_t st);
+
+// ---- contractions over the grid (blas.cu) ----
+template <class T>
+void gram(pt_ctx* ctx, const cx<T>* A, const cx<T>* B, int N1, int N2, size_t ng, double scale, c128* C,
+          cudaStream_t st);
+template <class T>
+void rotate(pt_ctx* ctx, const cx<T>* A, const c128* Bm, int ldb, int N1, int N2, size_t ng, c128 alpha,
+            const Term* terms, int nterms, cx<T>* out, cudaStream_t st);
+template <class T>
+void lincomb(pt_ctx* ctx, cx<T>* out, size_t n, const Term* terms, int nterms, cudaStream_t st);
+template <class T>
+void potential_apply(pt_ctx* ctx, cx<T>* out, const cx<T>* psi, const double* v, size_t ng, int M, const cx<T>* X,
+                     double a, cudaStream_t st);
+template <class T>
+void multi_dot(pt_ctx* ctx, const void* const* u1, const c128* const* u2, int m, const cx<T>* v1, size_t n1,
+               const c128* v2, size_t n2, double w1, double w2, double* out, cudaStream_t st);
+
+// ---- FP64 N x N (dense.cu) ----
+void zgemm(char opA, char opB, int m, int n, int k, c128 alpha, const c128* A, int lda, const c128* B, int ldb,
+           c128 beta, c128* C, int ldc, cudaStream_t st);
+// S (Hermitian part used) = Q diag(d) Q^*, ascending d.  Synchronises st once per sweep.
+void heev(pt_ctx* ctx, const c128* S, int N, c128* Q, double* d, cudaStream_t st, int max_sweeps = 30);
+// A (overwritten) = L L^* ; L written to a separate buffer; *info = k+1 on a bad pivot k.
+void cholesky(pt_ctx* ctx, c128* A, int N, c128* L, int* info, cudaStream_t st);
+void tri_inv_lower(const c128* L, int N, c128* X, cudaStream_t st);
+void scale_cols_pow(const c128* U, const double* lam, int N, double power, c128* out, int* info, cudaStream_t st);
+void small_solve(const double* G, const double* rhs, int m, double reg, double* x, cudaStream_t st);
+
+// ---- Hamiltonian (hamiltonian.cu) ----
+// out = P_sph[ -1/2 Lap psi + y ],  y = vloc*psi + alpha*X (X may be null)
+void apply_h(pt_ctx* ctx, const void* psi, int M, void* out, const double* vloc, const void* X, double alpha,
+             double ecut, const pt_grid& g, pt_precision prec, cudaStream_t st);
+
+void conj_transpose(const c128* A, int N, c128* B, cudaStream_t st);
+
+// ---- PT-IM step (ptim.cu) ----
+pt_status ptim_step(pt_ctx* ctx, void* phi, void* sigma, int N, const double* vloc, const pt_grid& g,
+                    const pt_kernel& k, const pt_ptim_params& P, pt_precision prec, pt_ptim_stats* stats,
+                    cudaStream_t st);
+
+// ---- ACE (ace.cu) ----
+// xi from (phi, W): M = <phi|W>, -M = L L^*, xi = W L^{-*}.  Synchronises st (pivot check).
+void ace_from_w(pt_ctx* ctx, const void* W, const void* phi, int N, const pt_grid& g, pt_precision prec, void* xi,
+                cudaStream_t st);
+// out = -xi (xi^* psi)  (+ beta*out0 is not supported: out is overwritten)
+void ace_apply(pt_ctx* ctx, const void* xi, int N, const void* psi, int M, void* out, const pt_grid& g,
+               pt_precision prec, cudaStream_t st);
+
+}  // namespace pt

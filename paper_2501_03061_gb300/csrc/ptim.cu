@@ -1,0 +1,403 @@
+// One PT-IM(-ACE) time step (Alg. 1; Eqs. n+1/2, p_tilde, lisan, x=tx; the double SCF loop of Sec. IV-A2).
+//
+// Unknowns x = (Phi_{n+1}, sigma_{n+1}), initial guess (Phi_n, sigma_n).  Fixed-point map, with
+// midpoints Phi_h = (Phi + Phi_n)/2 and sigma_h = (sigma + sigma_n)/2:
+//     T_Phi   = Phi_n   - i dt (H Phi_h - Phi_h S^{-1} A),   S = <Phi_h|Phi_h>,  A = <Phi_h|H Phi_h>
+//     T_sigma = sigma_n - i dt (A sigma_h - sigma_h A)
+// Outer loop: diagonalise sigma_h (FP64 Jacobi), phit = Phi_h Q, W = (V_x phit) Q^*, ACE from
+// (Phi_h, W).  Inner loop: Anderson mixing (type II, real coefficients, depth <= 20, history on
+// the device) on x = T(x) with the ACE frozen; the relative residual is reduced in FP64 and read
+// by the host each iteration.  The outer loop stops when the midpoint the ACE was built on moved
+// by less than tol.  Finally Loewdin: Phi <- Phi S^{-1/2}, sigma <- S^{1/2} sigma S^{1/2}, then
+// sigma <- (sigma + sigma^*)/2.
+#include <algorithm>
+#include <cstring>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace pt {
+
+namespace {
+
+constexpr int kMaxDepth = 20;
+
+__global__ void k_maxabs_diff(const c128* __restrict__ A, const c128* __restrict__ B, int n, double* __restrict__ out) {
+  double m = 0;
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    const double dr = A[e].re - B[e].re, di = A[e].im - B[e].im;
+    m = fmax(m, sqrt(dr * dr + di * di));
+  }
+  for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+  __shared__ double s[32];
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) r = fmax(r, s[w]);
+    out[0] = r;
+  }
+}
+
+// sum_i d_i Re <phit_i|V phit_i> * dV   (one block per orbital, FP64 block reduction)
+template <class T>
+__global__ void k_weighted_diag(const cx<T>* __restrict__ a, const cx<T>* __restrict__ b, const double* __restrict__ d,
+                                size_t ng, double dV, double* __restrict__ out) {
+  const int i = blockIdx.x;
+  const cx<T>* x = a + size_t(i) * ng;
+  const cx<T>* y = b + size_t(i) * ng;
+  double s = 0;
+  for (size_t e = threadIdx.x; e < ng; e += blockDim.x) {
+    const cx<T> u = x[e], v = y[e];
+    s += double(u.re * v.re + u.im * v.im);
+  }
+  for (int o = 16; o; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  __shared__ double sh[32];
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) r += sh[w];
+    out[i] = r * dV * d[i];
+  }
+}
+
+// history Gram matrix: G[slot][a] = G[a][slot] = col[a]; rhs kept separately
+__global__ void k_gram_insert(double* __restrict__ G, int ld, const double* __restrict__ col, int slot, int m) {
+  const int a = threadIdx.x;
+  if (a < m) {
+    G[slot * ld + a] = col[a];
+    G[a * ld + slot] = col[a];
+  }
+}
+
+// pack the active m x m block (slots listed in order) into a dense matrix for the solver
+__global__ void k_gram_pack(const double* __restrict__ G, int ld, const int* __restrict__ slots, int m,
+                            double* __restrict__ P) {
+  const int e = threadIdx.x;
+  if (e < m * m) P[e] = G[slots[e / m] * ld + slots[e % m]];
+}
+
+// x <- x + beta r - sum_a gamma_a (dX_a + beta dR_a), over an orbital segment
+template <class T>
+__global__ void k_anderson_update(cx<T>* __restrict__ x, const cx<T>* __restrict__ r,
+                                  const cx<T>* const* __restrict__ dX, const cx<T>* const* __restrict__ dR,
+                                  const double* __restrict__ gamma, int m, double beta, size_t n) {
+  __shared__ T g[kMaxDepth];
+  if (threadIdx.x < m) g[threadIdx.x] = T(gamma[threadIdx.x]);
+  __syncthreads();
+  const T b = T(beta);
+  for (size_t e = size_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n; e += size_t(gridDim.x) * blockDim.x) {
+    cx<T> v = x[e] + r[e] * b;
+    for (int a = 0; a < m; ++a) v = v - (dX[a][e] + dR[a][e] * b) * g[a];
+    x[e] = v;
+  }
+}
+
+template <class T>
+__global__ void k_diff(cx<T>* out, const cx<T>* a, const cx<T>* b, size_t n) {
+  for (size_t e = size_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n; e += size_t(gridDim.x) * blockDim.x)
+    out[e] = a[e] - b[e];
+}
+
+template <class T>
+struct Seg {
+  cx<T>* phi;
+  c128* sig;
+};
+
+template <class T>
+struct Step {
+  pt_ctx* ctx;
+  int N;
+  size_t ng, n1, n2;
+  double dV;
+  pt_grid g;
+  pt_kernel k;
+  pt_precision prec;
+  pt_ptim_params p;
+  cudaStream_t st;
+  int blocks;
+
+  void* buf(const char* name, size_t bytes) { return ctx->get(name, bytes); }
+
+  // ||a||^2 of a two-segment vector with weight dV on the orbital segment (FP64 result on host)
+  double norm2(const cx<T>* phi, const c128* sig) {
+    double* dev = static_cast<double*>(buf("ptim_norm", 2 * sizeof(double)));
+    const void* u1[1] = {phi};
+    const c128* u2[1] = {sig};
+    multi_dot<T>(ctx, u1, u2, 1, phi, n1, sig, n2, dV, 1.0, dev, st);
+    double h = 0;
+    PT_CUDA_CHECK(cudaMemcpyAsync(&h, dev, sizeof(double), cudaMemcpyDeviceToHost, st));
+    PT_CUDA_CHECK(cudaStreamSynchronize(st));
+    return h;
+  }
+
+  void midpoint(cx<T>* phih, c128* sigh, const cx<T>* phi, const cx<T>* phin, const c128* sig, const c128* sign) {
+    Term t[2] = {{phi, c128{0.5, 0}}, {phin, c128{0.5, 0}}};
+    lincomb<T>(ctx, phih, n1, t, 2, st);
+    Term s[2] = {{sig, c128{0.5, 0}}, {sign, c128{0.5, 0}}};
+    lincomb<double>(ctx, sigh, n2, s, 2, st);
+  }
+};
+
+template <class T>
+pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* vloc, const pt_grid& g,
+                      const pt_kernel& kern, const pt_ptim_params& P, pt_precision prec, pt_ptim_stats* stats,
+                      cudaStream_t st) {
+  Step<T> S{ctx, N, ng_of(g), ng_of(g) * N, size_t(N) * N, dv_of(g), g, kern, prec, P, st, 0};
+  const size_t fb = S.n1 * sizeof(cx<T>);
+  const size_t mb = S.n2 * sizeof(c128);
+  const int depth = std::max(1, std::min(P.anderson_depth, kMaxDepth));
+  auto F = [&](const char* n) { return static_cast<cx<T>*>(S.buf(n, fb)); };
+  auto Mx = [&](const char* n) { return static_cast<c128*>(S.buf(n, mb)); };
+  cx<T>* phin = F("ptim_phin");
+  cx<T>* phih = F("ptim_phih");
+  cx<T>* phit = F("ptim_phit");
+  cx<T>* vphit = F("ptim_vphit");
+  cx<T>* W = F("ptim_W");
+  cx<T>* xi = F("ptim_xi");
+  cx<T>* X = F("ptim_X");
+  cx<T>* Hphi = F("ptim_Hphi");
+  cx<T>* rphi = F("ptim_rphi");
+  cx<T>* aphi = F("ptim_anchor_phi");
+  cx<T>* xprev = F("ptim_xprev_phi");
+  cx<T>* rprev = F("ptim_rprev_phi");
+  c128* sign = Mx("ptim_sign");
+  c128* sigh = Mx("ptim_sigh");
+  c128* asig = Mx("ptim_anchor_sig");
+  c128* Q = Mx("ptim_Q");
+  c128* QH = Mx("ptim_QH");
+  c128* A = Mx("ptim_A");
+  c128* Sm = Mx("ptim_S");
+  c128* Sn = Mx("ptim_Sn");
+  c128* Lc = Mx("ptim_L");
+  c128* Li = Mx("ptim_Linv");
+  c128* T1 = Mx("ptim_T1");
+  c128* SinvA = Mx("ptim_SinvA");
+  c128* rsig = Mx("ptim_rsig");
+  c128* sprev = Mx("ptim_xprev_sig");
+  c128* rsprev = Mx("ptim_rprev_sig");
+  double* d = static_cast<double*>(S.buf("ptim_d", N * sizeof(double)));
+  double* dsc = static_cast<double*>(S.buf("ptim_dscratch", (2 * N + 64) * sizeof(double)));
+  int* info = static_cast<int*>(S.buf("ptim_info", sizeof(int)));
+  // Anderson history rings
+  std::vector<cx<T>*> dXp(depth), dRp(depth);
+  std::vector<c128*> dXs(depth), dRs(depth);
+  for (int a = 0; a < depth; ++a) {
+    char nm[64];
+    snprintf(nm, sizeof(nm), "ptim_dX_phi_%d", a);
+    dXp[a] = F(nm);
+    snprintf(nm, sizeof(nm), "ptim_dR_phi_%d", a);
+    dRp[a] = F(nm);
+    snprintf(nm, sizeof(nm), "ptim_dX_sig_%d", a);
+    dXs[a] = Mx(nm);
+    snprintf(nm, sizeof(nm), "ptim_dR_sig_%d", a);
+    dRs[a] = Mx(nm);
+  }
+  double* Gd = static_cast<double*>(S.buf("ptim_G", kMaxDepth * kMaxDepth * sizeof(double)));
+  double* Gp = static_cast<double*>(S.buf("ptim_Gpacked", kMaxDepth * kMaxDepth * sizeof(double)));
+  double* col = static_cast<double*>(S.buf("ptim_col", 2 * kMaxDepth * sizeof(double)));
+  double* gamma = static_cast<double*>(S.buf("ptim_gamma", kMaxDepth * sizeof(double)));
+  int* slots_d = static_cast<int*>(S.buf("ptim_slots", kMaxDepth * sizeof(int)));
+  auto** dXp_d = static_cast<const cx<T>**>(S.buf("ptim_dXp_ptrs", kMaxDepth * sizeof(void*)));
+  auto** dRp_d = static_cast<const cx<T>**>(S.buf("ptim_dRp_ptrs", kMaxDepth * sizeof(void*)));
+  auto** dXs_d = static_cast<const c128**>(S.buf("ptim_dXs_ptrs", kMaxDepth * sizeof(void*)));
+  auto** dRs_d = static_cast<const c128**>(S.buf("ptim_dRs_ptrs", kMaxDepth * sizeof(void*)));
+
+  PT_CUDA_CHECK(cudaMemcpyAsync(phin, phi, fb, cudaMemcpyDeviceToDevice, st));
+  PT_CUDA_CHECK(cudaMemcpyAsync(sign, sig, mb, cudaMemcpyDeviceToDevice, st));
+  gram<T>(ctx, phin, phin, N, N, S.ng, S.dV, Sn, st);
+
+  pt_ptim_stats stv;
+  std::memset(&stv, 0, sizeof(stv));
+  stv.residual = NAN;
+  bool converged = false, inner_conv = false, have_anchor = false;
+  const int nthreads = 256;
+  const int sblocks = std::max(1, std::min<int>(ctx->num_sms * 8, int((S.n1 + nthreads - 1) / nthreads)));
+  const int sblocks2 = std::max(1, int((S.n2 + nthreads - 1) / nthreads));
+
+  // V_x[P_h] Phi_h through the sigma_h eigenbasis: (V_x phit) Q^*, phit = Phi_h Q
+  auto exchange_on_midpoint = [&](cx<T>* out, bool energy) {
+    heev(ctx, sigh, N, Q, d, st);
+    rotate<T>(ctx, phih, Q, N, N, N, S.ng, c128{1, 0}, nullptr, 0, phit, st);
+    stv.pair_ffts += exchange(ctx, phit, d, N, nullptr, N, vphit, g, kern, prec, st);
+    if (energy) {
+      PT_LAUNCH(k_weighted_diag<T>, N, 256, 0, st, phit, vphit, d, S.ng, S.dV, dsc);
+      std::vector<double> h(N);
+      PT_CUDA_CHECK(cudaMemcpyAsync(h.data(), dsc, N * sizeof(double), cudaMemcpyDeviceToHost, st));
+      PT_CUDA_CHECK(cudaStreamSynchronize(st));
+      double e = 0;
+      for (double v : h) e += v;
+      stv.exch_energy = P.spin * 0.5 * P.alpha * e;
+    }
+    conj_transpose(Q, N, QH, st);
+    rotate<T>(ctx, vphit, QH, N, N, N, S.ng, c128{1, 0}, nullptr, 0, out, st);
+  };
+
+  const int max_outer = P.use_ace ? P.max_outer : 1;
+  for (int outer = 0; outer < max_outer && !converged; ++outer) {
+    S.midpoint(phih, sigh, phi, phin, sig, sign);
+    if (P.use_ace) {
+      if (have_anchor) {
+        PT_LAUNCH(k_diff<T>, sblocks, nthreads, 0, st, aphi, phih, aphi, S.n1);
+        PT_LAUNCH(k_diff<double>, sblocks2, nthreads, 0, st, asig, sigh, asig, S.n2);
+        const double ch = S.norm2(aphi, asig), nr = S.norm2(phih, sigh);
+        if (std::sqrt(ch / nr) < P.tol && inner_conv) {
+          converged = true;
+          break;
+        }
+      }
+      PT_CUDA_CHECK(cudaMemcpyAsync(aphi, phih, fb, cudaMemcpyDeviceToDevice, st));
+      PT_CUDA_CHECK(cudaMemcpyAsync(asig, sigh, mb, cudaMemcpyDeviceToDevice, st));
+      have_anchor = true;
+      stv.outer = outer + 1;
+      exchange_on_midpoint(W, true);
+      ace_from_w(ctx, W, phih, N, g, prec, xi, st);
+    } else {
+      stv.outer = 1;
+    }
+    // ---- inner Anderson loop ----
+    inner_conv = false;
+    int hist = 0, next_slot = 0;
+    bool have_prev = false;
+    std::vector<int> slot_order;
+    for (int inner = 0; inner < P.max_inner; ++inner) {
+      stv.inner++;
+      S.midpoint(phih, sigh, phi, phin, sig, sign);
+      if (P.use_ace) ace_apply(ctx, xi, N, phih, N, X, g, prec, st);
+      else exchange_on_midpoint(X, inner == 0);
+      apply_h(ctx, phih, N, Hphi, vloc, X, P.alpha, P.ecut, g, prec, st);
+      gram<T>(ctx, phih, Hphi, N, N, S.ng, S.dV, A, st);
+      gram<T>(ctx, phih, phih, N, N, S.ng, S.dV, Sm, st);
+      // S^{-1} A = L^{-*} (L^{-1} A)
+      cholesky(ctx, Sm, N, Lc, info, st);
+      tri_inv_lower(Lc, N, Li, st);
+      zgemm('N', 'N', N, N, N, c128{1, 0}, Li, N, A, N, c128{0, 0}, T1, N, st);
+      zgemm('C', 'N', N, N, N, c128{1, 0}, Li, N, T1, N, c128{0, 0}, SinvA, N, st);
+      // r_Phi = Phi_n - i dt (H Phi_h - Phi_h S^{-1}A) - Phi
+      Term tr[3] = {{Hphi, c128{0, -P.dt}}, {phin, c128{1, 0}}, {phi, c128{-1, 0}}};
+      rotate<T>(ctx, phih, SinvA, N, N, N, S.ng, c128{0, P.dt}, tr, 3, rphi, st);
+      // r_sigma = sigma_n - i dt (A sigma_h - sigma_h A) - sigma
+      zgemm('N', 'N', N, N, N, c128{1, 0}, A, N, sigh, N, c128{0, 0}, T1, N, st);
+      zgemm('N', 'N', N, N, N, c128{-1, 0}, sigh, N, A, N, c128{1, 0}, T1, N, st);
+      Term ts[3] = {{sign, c128{1, 0}}, {T1, c128{0, -P.dt}}, {sig, c128{-1, 0}}};
+      lincomb<double>(ctx, rsig, S.n2, ts, 3, st);
+      int h_info = 0;
+      PT_CUDA_CHECK(cudaMemcpyAsync(&h_info, info, sizeof(int), cudaMemcpyDeviceToHost, st));
+      const double rr = S.norm2(rphi, rsig);  // synchronises st
+      const double xx = S.norm2(phi, sig);
+      if (h_info) fail(PT_NOT_PD, "PT-IM: overlap of the midpoint orbitals is not positive definite");
+      const double res = std::sqrt(rr / xx);
+      stv.residual = res;
+      if (!std::isfinite(res)) fail(PT_NONFINITE, "PT-IM residual is not finite");
+      if (res < P.tol) {
+        inner_conv = true;
+        break;
+      }
+      // ---- Anderson (type II, real coefficients) ----
+      if (have_prev) {
+        const int slot = next_slot;
+        next_slot = (next_slot + 1) % depth;
+        PT_LAUNCH(k_diff<T>, sblocks, nthreads, 0, st, dXp[slot], phi, xprev, S.n1);
+        PT_LAUNCH(k_diff<T>, sblocks, nthreads, 0, st, dRp[slot], rphi, rprev, S.n1);
+        PT_LAUNCH(k_diff<double>, sblocks2, nthreads, 0, st, dXs[slot], sig, sprev, S.n2);
+        PT_LAUNCH(k_diff<double>, sblocks2, nthreads, 0, st, dRs[slot], rsig, rsprev, S.n2);
+        slot_order.erase(std::remove(slot_order.begin(), slot_order.end(), slot), slot_order.end());
+        slot_order.push_back(slot);
+        hist = int(slot_order.size());
+        // new Gram column: <dR_a, dR_slot> for the active slots, in slot_order order
+        std::vector<const void*> u1(hist);
+        std::vector<const c128*> u2(hist);
+        for (int a = 0; a < hist; ++a) {
+          u1[a] = dRp[slot_order[a]];
+          u2[a] = dRs[slot_order[a]];
+        }
+        multi_dot<T>(ctx, u1.data(), u2.data(), hist, dRp[slot], S.n1, dRs[slot], S.n2, S.dV, 1.0, col, st);
+        // scatter into G by slot index
+        std::vector<double> hcol(hist);
+        PT_CUDA_CHECK(cudaMemcpyAsync(hcol.data(), col, hist * sizeof(double), cudaMemcpyDeviceToHost, st));
+        PT_CUDA_CHECK(cudaStreamSynchronize(st));
+        std::vector<double> full(depth, 0.0);
+        for (int a = 0; a < hist; ++a) full[slot_order[a]] = hcol[a];
+        PT_CUDA_CHECK(cudaMemcpyAsync(col + kMaxDepth, full.data(), depth * sizeof(double), cudaMemcpyHostToDevice, st));
+        PT_LAUNCH(k_gram_insert, 1, 32, 0, st, Gd, kMaxDepth, col + kMaxDepth, slot, depth);
+      }
+      PT_CUDA_CHECK(cudaMemcpyAsync(xprev, phi, fb, cudaMemcpyDeviceToDevice, st));
+      PT_CUDA_CHECK(cudaMemcpyAsync(rprev, rphi, fb, cudaMemcpyDeviceToDevice, st));
+      PT_CUDA_CHECK(cudaMemcpyAsync(sprev, sig, mb, cudaMemcpyDeviceToDevice, st));
+      PT_CUDA_CHECK(cudaMemcpyAsync(rsprev, rsig, mb, cudaMemcpyDeviceToDevice, st));
+      have_prev = true;
+      int m = hist;
+      if (m > 0) {
+        std::vector<const void*> u1(m);
+        std::vector<const c128*> u2(m);
+        std::vector<const cx<T>*> px(m), pr(m);
+        std::vector<const c128*> sx(m), sr(m);
+        for (int a = 0; a < m; ++a) {
+          const int s = slot_order[a];
+          u1[a] = dRp[s];
+          u2[a] = dRs[s];
+          px[a] = dXp[s];
+          pr[a] = dRp[s];
+          sx[a] = dXs[s];
+          sr[a] = dRs[s];
+        }
+        // rhs_a = <dR_a, r>
+        multi_dot<T>(ctx, u1.data(), u2.data(), m, rphi, S.n1, rsig, S.n2, S.dV, 1.0, col, st);
+        PT_CUDA_CHECK(cudaMemcpyAsync(slots_d, slot_order.data(), m * sizeof(int), cudaMemcpyHostToDevice, st));
+        PT_LAUNCH(k_gram_pack, 1, kMaxDepth * kMaxDepth, 0, st, Gd, kMaxDepth, slots_d, m, Gp);
+        small_solve(Gp, col, m, 1e-14, gamma, st);
+        PT_CUDA_CHECK(cudaMemcpyAsync(dXp_d, px.data(), m * sizeof(void*), cudaMemcpyHostToDevice, st));
+        PT_CUDA_CHECK(cudaMemcpyAsync(dRp_d, pr.data(), m * sizeof(void*), cudaMemcpyHostToDevice, st));
+        PT_CUDA_CHECK(cudaMemcpyAsync(dXs_d, sx.data(), m * sizeof(void*), cudaMemcpyHostToDevice, st));
+        PT_CUDA_CHECK(cudaMemcpyAsync(dRs_d, sr.data(), m * sizeof(void*), cudaMemcpyHostToDevice, st));
+        // the host vectors above must outlive the async copies
+        PT_CUDA_CHECK(cudaStreamSynchronize(st));
+      }
+      PT_LAUNCH(k_anderson_update<T>, sblocks, nthreads, 0, st, phi, rphi, dXp_d, dRp_d, gamma, m, P.anderson_beta,
+                S.n1);
+      PT_LAUNCH(k_anderson_update<double>, sblocks2, nthreads, 0, st, sig, rsig, dXs_d, dRs_d, gamma, m,
+                P.anderson_beta, S.n2);
+    }
+    if (!P.use_ace && inner_conv) converged = true;
+  }
+  // ---- final orthonormalisation and conjugate symmetrisation ----
+  gram<T>(ctx, phi, phi, N, N, S.ng, S.dV, Sm, st);
+  PT_LAUNCH(k_maxabs_diff, 1, 1024, 0, st, Sm, Sn, int(S.n2), dsc);
+  heev(ctx, Sm, N, Q, d, st);
+  PT_CUDA_CHECK(cudaMemcpyAsync(&stv.orth_error, dsc, sizeof(double), cudaMemcpyDeviceToHost, st));
+  PT_CUDA_CHECK(cudaMemsetAsync(info, 0, sizeof(int), st));
+  scale_cols_pow(Q, d, N, -0.5, T1, info, st);
+  zgemm('N', 'C', N, N, N, c128{1, 0}, T1, N, Q, N, c128{0, 0}, A, N, st);   // S^{-1/2}
+  scale_cols_pow(Q, d, N, 0.5, T1, info, st);
+  zgemm('N', 'C', N, N, N, c128{1, 0}, T1, N, Q, N, c128{0, 0}, Lc, N, st);  // S^{1/2}
+  rotate<T>(ctx, phi, A, N, N, N, S.ng, c128{1, 0}, nullptr, 0, rphi, st);
+  PT_CUDA_CHECK(cudaMemcpyAsync(phi, rphi, fb, cudaMemcpyDeviceToDevice, st));
+  zgemm('N', 'N', N, N, N, c128{1, 0}, Lc, N, sig, N, c128{0, 0}, T1, N, st);
+  zgemm('N', 'N', N, N, N, c128{1, 0}, T1, N, Lc, N, c128{0, 0}, sig, N, st);
+  conj_transpose(sig, N, T1, st);
+  Term th[2] = {{sig, c128{0.5, 0}}, {T1, c128{0.5, 0}}};
+  lincomb<double>(ctx, sig, S.n2, th, 2, st);
+  int h_info = 0;
+  PT_CUDA_CHECK(cudaMemcpyAsync(&h_info, info, sizeof(int), cudaMemcpyDeviceToHost, st));
+  PT_CUDA_CHECK(cudaStreamSynchronize(st));
+  if (h_info) fail(PT_NOT_PD, "PT-IM: final overlap matrix is not positive definite");
+  stv.converged = converged ? 1 : 0;
+  if (stats) *stats = stv;
+  return converged ? PT_OK : PT_NOT_CONVERGED;
+}
+
+}  // namespace
+
+pt_status ptim_step(pt_ctx* ctx, void* phi, void* sigma, int N, const double* vloc, const pt_grid& g,
+                    const pt_kernel& k, const pt_ptim_params& P, pt_precision prec, pt_ptim_stats* stats,
+                    cudaStream_t st) {
+  if (prec == PT_FP64)
+    return ptim_step_t<double>(ctx, static_cast<c128*>(phi), static_cast<c128*>(sigma), N, vloc, g, k, P, prec,
+                               stats, st);
+  return ptim_step_t<float>(ctx, static_cast<c64*>(phi), static_cast<c128*>(sigma), N, vloc, g, k, P, prec, stats,
+                            st);
+}
+
+}  // namespace pt
