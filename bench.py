@@ -1,0 +1,383 @@
+#!/usr/bin/env python
+"""Benchmark of the PT-IM hybrid-functional hot path on GB300.
+
+A step is one PT-IM-ACE time step (every row of the hot path: sigma diagonalisation, basis
+rotation, pair-FFT exchange, ACE Gram/Cholesky/TRSM, ACE application, H.Psi, projection and
+commutator, Anderson mixing with FP64 residual, Loewdin re-orthonormalisation) on the
+128-site silicon-like cell: L = 20.5 bohr, 64^3 grid, N = 320 orbitals, Fermi-Dirac
+occupations at kT = 0.02 Ha, dt = 0.5 au, screened kernel mu = 0.106, tol = 1e-6.
+Steps are chained (a real propagation).  One JSON line is printed by rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+--impl reference times the FP64 numpy oracle on the host cores (bounded sample, scaled to
+steps/s).  Under torchrun each rank propagates an independent replica (no collective on the
+data path); value = all ranks' steps / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Vx·Ψ pair-FFTs/s and PT-IM steps/s vs plain FP64 GPU form; serve p50/p99"
+UNIT = "PT-IM steps/s"
+WORKLOAD = "ptim_ace_step_64^3_N320_128site_L20.5"
+# model iteration counts used to scale a bounded CPU sample to one step: the paper's ~5 outer x ~13 inner
+MODEL_OUTER, MODEL_INNER = 5, 65
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 form comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle sample (the reference arm and the cpu_baseline field)
+# ------------------------------------------------------------------------------------------
+
+def cpu_sample(budget_s: float = 12.0) -> dict:
+    """Time the FP64 oracle on parts of one step and scale to one step of the model counts."""
+    import numpy as np
+
+    from oracle import ptim_oracle as O
+    from paper_2501_03061_gb300 import synth
+
+    w = synth.ptim_cell128()
+    g = O.grid_of(w.cell)
+    K = O.exchange_kernel(g, 1, synth.SCREENED_MU)
+    N = w.N
+    # pair FFTs: conj(phi_i) phi_j -> FFT -> K -> IFFT -> accumulate, as apply_exchange does per pair
+    t0 = time.perf_counter()
+    npair = 0
+    acc = np.zeros(w.phi.shape[1:], dtype=np.complex128)
+    while time.perf_counter() - t0 < budget_s * 0.5 or npair < 4:
+        i, j = npair % N, (7 * npair + 3) % N
+        acc += w.occ[i] * w.phi[i] * O.pair_potential(w.phi[i], w.phi[j], K)
+        npair += 1
+    t_pair = (time.perf_counter() - t0) / npair
+    # H on a few orbitals (kinetic FFT pair + potential + sphere projection)
+    nh = 4
+    t0 = time.perf_counter()
+    O.apply_H(w.phi[:nh], w.vloc, g, 10.0, 0.25, 0 * w.phi[:nh])
+    t_h = (time.perf_counter() - t0) / nh
+    # one Ng x N x N overlap and one rotation at full size
+    t0 = time.perf_counter()
+    S = O.overlap(w.phi, w.phi, g.dV)
+    t_gram = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    O.rotate(w.phi, S)
+    t_rot = time.perf_counter() - t0
+    pairs = MODEL_OUTER * N * (N + 1) // 2
+    # per inner iteration: ACE (gram + rotate), H, A and S grams, projection rotate
+    t_inner = 3 * t_gram + 2 * t_rot + N * t_h
+    # per outer iteration: rotations into and out of the sigma eigenbasis, ACE Gram + xi rotation
+    t_outer = 3 * t_rot + t_gram
+    t_step = pairs * t_pair + MODEL_INNER * t_inner + MODEL_OUTER * t_outer
+    return {
+        "t_step_s": t_step, "t_pair_s": t_pair, "t_h_orbital_s": t_h, "t_gram_s": t_gram, "t_rotate_s": t_rot,
+        "pairs_sampled": npair,
+        "cores": os.cpu_count(),
+        "sample": (f"FP64 numpy oracle on the 64^3/N=320 cell: {npair} pair FFTs (numpy FFT, 1 thread), "
+                   f"H on {nh} orbitals, one full-size overlap and rotation (BLAS threads); scaled to one "
+                   f"PT-IM-ACE step of {MODEL_OUTER} outer / {MODEL_INNER} inner iterations "
+                   f"({pairs} symmetric pair FFTs)"),
+    }
+
+
+def run_cpu_sample_subprocess() -> dict | None:
+    try:
+        r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--cpu-sample"], capture_output=True,
+                           text=True, timeout=600)
+        for line in r.stdout.splitlines()[::-1]:
+            if line.startswith("{"):
+                return json.loads(line)
+    except Exception as e:  # noqa: BLE001
+        return {"error": str(e)}
+    return {"error": r.stderr[-300:]}
+
+
+# ------------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ------------------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:  # noqa: BLE001
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(5)
+        except Exception:  # noqa: BLE001
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------------------------------
+
+def read_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:  # noqa: BLE001
+        return 6800.0, "fallback"
+
+
+def run_gb300(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2501_03061_gb300 import api, synth
+
+    world, rank, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    devc = torch.device("cuda", local)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = run_cpu_sample_subprocess()  # before any GPU work in this process tree
+
+    w = synth.ptim_cell128()
+    ng = w.cell.ng
+    N = w.N
+    cdt = np.complex64 if args.precision == "fp32" else np.complex128
+    phi0 = torch.from_numpy(w.phi.astype(cdt))
+    sig0 = torch.from_numpy(w.sigma)
+    vloc0 = torch.from_numpy(w.vloc)
+    ctx = api.Context(local)
+    phi = phi0.to(devc)
+    sigma = sig0.to(devc)
+    vloc = vloc0.to(devc)
+    kw = dict(cell=w.cell, kernel=w.kernel, precision=args.precision, dt=0.5, alpha=0.25, ecut=10.0,
+              tol=args.tol, max_outer=20, max_inner=100, anderson_depth=20, allow_unconverged=True)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        ctx.ptim_step(phi, sigma, vloc, **kw)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler() if rank == 0 else None
+    barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    l0 = api.kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    stats = []
+    for _ in range(args.steps):
+        stats.append(ctx.ptim_step(phi, sigma, vloc, **kw))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = api.kernel_launches() - l0
+    clocks = sampler.stop() if sampler else None
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device=devc)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * args.steps / (ms / 1e3)
+
+    pair_ffts = sum(s["pair_ffts"] for s in stats)
+    ex_ms = sum(s["exchange_ms"] for s in stats)
+    ex_calls = sum(s["exchange_calls"] for s in stats)
+    # symmetric pair FFT, streaming model: read phit_i, phit_j, read+write W_i and W_j (complex64 fields)
+    esz = 8 if args.precision == "fp32" else 16
+    bytes_per_pair = 6 * ng * esz
+    flops_per_pair = 10 * ng * math.log2(ng) + 16 * ng
+    peak, peak_src = read_peaks()
+    achieved = pair_ffts * bytes_per_pair / (ex_ms / 1e3) / 1e9 if ex_ms > 0 else None
+
+    # ---- end to end: pinned host buffers, H2D inside the timed region, D2H of the result ----
+    e2e = None
+    if not args.no_e2e:
+        hphi = phi0.pin_memory()
+        hsig = sig0.pin_memory()
+        hv = vloc0.pin_memory()
+        ophi = torch.empty_like(hphi).pin_memory()
+        osig = torch.empty_like(hsig).pin_memory()
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            dphi = hphi.to(devc, non_blocking=True)
+            dsig = hsig.to(devc, non_blocking=True)
+            dv = hv.to(devc, non_blocking=True)
+            ctx.ptim_step(dphi, dsig, dv, **kw)
+            ophi.copy_(dphi, non_blocking=True)
+            osig.copy_(dsig, non_blocking=True)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([te], device=devc)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        e2e = {"value": world * args.steps / te, "unit": UNIT,
+               "h2d_bytes_per_step": int(hphi.numel() * hphi.element_size() + hsig.numel() * 16 + hv.numel() * 8),
+               "d2h_bytes_per_step": int(ophi.numel() * ophi.element_size() + osig.numel() * 16)}
+
+    # ---- plain FP64 GPU form: one exchange application (the step's dominant operation) ----
+    fp64 = None
+    if not args.no_fp64 and rank == 0:
+        ctx.trim()
+        pd = torch.from_numpy(w.phi).to(devc)
+        od = torch.from_numpy(w.occ).to(devc)
+        ctx.apply_exchange(pd[:8].contiguous(), od[:8], cell=w.cell, kernel=w.kernel, precision="fp64")
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.apply_exchange(pd, od, cell=w.cell, kernel=w.kernel, precision="fp64")
+        b.record(stream)
+        torch.cuda.synchronize()
+        t64 = a.elapsed_time(b)
+        p32 = torch.from_numpy(w.phi.astype(np.complex64)).to(devc)
+        a.record(stream)
+        ctx.apply_exchange(p32, od, cell=w.cell, kernel=w.kernel, precision="fp32")
+        b.record(stream)
+        torch.cuda.synchronize()
+        t32 = a.elapsed_time(b)
+        npairs = N * (N + 1) // 2
+        fp64 = {"exchange_ms": t64, "pair_ffts_per_s": npairs / (t64 / 1e3),
+                "fp32_exchange_ms": t32, "fp32_pair_ffts_per_s": npairs / (t32 / 1e3),
+                "exchange_speedup_fp32_vs_fp64": t64 / t32}
+        del pd, p32
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64" if args.precision == "fp32" else "c128",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": [64, 64, 64], "N": N, "atoms": 128, "precision": args.precision,
+                       "tol": args.tol, "dt_au": 0.5, "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (phi alone is %d MB)" % (N * ng * esz >> 20)},
+            "pair_ffts_per_s": pair_ffts / (ms / 1e3) if ms > 0 else None,
+            "exchange": {"pair_ffts": pair_ffts, "calls": ex_calls, "ms": ex_ms,
+                         "pair_ffts_per_s": pair_ffts / (ex_ms / 1e3) if ex_ms else None,
+                         "share_of_step": ex_ms / ms if ms else None},
+            "iterations": [{"outer": s["outer"], "inner": s["inner"], "residual": s["residual"],
+                            "converged": s["converged"]} for s in stats],
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": (achieved / peak) if achieved else None, "traffic": None,
+                         "kernel": "pair-FFT exchange (plane/column/plane passes)",
+                         "model": "6 complex fields of Ng per symmetric pair FFT",
+                         "peak_source": peak_src,
+                         "flops_per_s": pair_ffts * flops_per_pair / (ex_ms / 1e3) if ex_ms else None},
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "plain_fp64_form": fp64,
+        }
+        if cpu is not None and "t_step_s" in cpu:
+            out["cpu_baseline"] = {"value": 1.0 / cpu["t_step_s"], "unit": UNIT, "cores": cpu["cores"],
+                                   "kind": "oracle", "sample": cpu["sample"],
+                                   "t_pair_s": cpu["t_pair_s"]}
+        elif cpu is not None:
+            out["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                   "sample": "failed: " + str(cpu.get("error"))[:200]}
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    vals = []
+    last = None
+    for k in range(args.warmup + args.steps):
+        s = cpu_sample(budget_s=4.0)
+        if k >= args.warmup:
+            vals.append(s["t_step_s"])
+        last = s
+    t = sum(vals) / len(vals)
+    out = {"metric": METRIC, "value": 1.0 / t, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": WORKLOAD, "grid": [64, 64, 64], "N": 320, "atoms": 128, "precision": "fp64",
+                      "parallelism": "host"},
+           "cpu_baseline": {"value": 1.0 / t, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
+                            "sample": last["sample"]},
+           "e2e": {"value": 1.0 / t, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.cpu_sample:
+        print(json.dumps(cpu_sample()), flush=True)
+        return
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gb300(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -169,6 +169,8 @@ typedef struct {
   double orth_error;        /* max |Phi^*Phi - Phi_n^*Phi_n| before the final orthonormalisation */
   int converged;            /* 1 when both loops met tol */
   long long pair_ffts;      /* pair FFTs executed (counting a symmetric pair once) */
+  int exchange_calls;       /* V_x applications */
+  double exchange_ms;       /* device time of those applications (CUDA events on the stream) */
 } pt_ptim_stats;
 
 /* One PT-IM(-ACE) step from (phi, sigma) = (Phi_n, sigma_n) to (Phi_{n+1}, sigma_{n+1}),

@@ -207,7 +207,8 @@ class Context:
             self._check(st, "pt_ptim_step")
         return {"status": L.STATUS_NAMES[st], "outer": s.outer, "inner": s.inner, "residual": s.residual,
                 "exch_energy": s.exch_energy, "orth_error": s.orth_error, "converged": bool(s.converged),
-                "pair_ffts": int(s.pair_ffts)}
+                "pair_ffts": int(s.pair_ffts), "exchange_calls": int(s.exchange_calls),
+                "exchange_ms": float(s.exchange_ms)}
 
 
 def kernel_launches() -> int:

@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cstring>
 
+#include "exchange_sched.h"
 #include "fft.cuh"
 #include "internal.h"
 
@@ -24,21 +25,6 @@ namespace {
 constexpr int NT = 512;          // threads per CTA of the tile kernels
 constexpr int MAXE = kMaxDim * kMaxDim;  // tile elements (64 x 64)
 constexpr int EPT = (MAXE + NT - 1) / NT;
-
-struct PairDesc {
-  int i, j;    // source index, target index
-  int o1, o2;  // occupation indices of its contributions (o2 < 0: a single one)
-};
-struct TargetDesc {
-  int t, cbeg, cend, first;
-};
-struct Contrib {
-  int slot, partner, occ, conj;
-};
-
-__device__ __forceinline__ bool pair_skipped(const PairDesc& pd, const double* occ) {
-  return occ[pd.o1] == 0.0 && (pd.o2 < 0 || occ[pd.o2] == 0.0);
-}
 
 template <class T>
 __device__ __forceinline__ void load_twiddles(cx<T>* tw, const cx<T>* twg, int n) {
@@ -173,21 +159,7 @@ __global__ void __launch_bounds__(NT) k_pair_inv_acc(GridPlan gp, const cx<T>* _
 // ------------------------------------------------------------------------------------------
 // host: pair schedule
 // ------------------------------------------------------------------------------------------
-struct ScheduleImpl {
-  int N = 0, M = 0, B = 0;
-  bool sym = false;
-  std::vector<int> pair_off, tgt_off;  // per batch offsets (size nbatch+1)
-  PairDesc* d_pairs = nullptr;
-  TargetDesc* d_tgts = nullptr;
-  Contrib* d_contribs = nullptr;
-  int max_pairs = 0, max_tgts = 0;
-  long long total_pairs = 0;
-  ~ScheduleImpl() {
-    cudaFree(d_pairs);
-    cudaFree(d_tgts);
-    cudaFree(d_contribs);
-  }
-};
+}  // namespace
 
 std::shared_ptr<ScheduleImpl> build_schedule(int N, int M, bool sym, int B) {
   auto s = std::make_shared<ScheduleImpl>();
@@ -254,6 +226,9 @@ std::shared_ptr<ScheduleImpl> build_schedule(int N, int M, bool sym, int B) {
     }
   }
   s->total_pairs = (long long)pairs.size();
+  s->h_pairs = pairs;
+  s->h_tgts = tgts;
+  s->h_contribs = cons;
   PT_CUDA_CHECK(cudaMalloc(&s->d_pairs, pairs.size() * sizeof(PairDesc)));
   PT_CUDA_CHECK(cudaMalloc(&s->d_tgts, tgts.size() * sizeof(TargetDesc)));
   PT_CUDA_CHECK(cudaMalloc(&s->d_contribs, cons.size() * sizeof(Contrib)));
@@ -262,6 +237,8 @@ std::shared_ptr<ScheduleImpl> build_schedule(int N, int M, bool sym, int B) {
   PT_CUDA_CHECK(cudaMemcpy(s->d_contribs, cons.data(), cons.size() * sizeof(Contrib), cudaMemcpyHostToDevice));
   return s;
 }
+
+namespace {
 
 size_t tile_smem_bytes(size_t esize) { return (3 * kMaxDim + size_t(kMaxDim) * (kMaxDim + 1)) * esize; }
 
@@ -292,6 +269,7 @@ long long exchange_t(pt_ctx* ctx, const cx<T>* src, const double* occ, int N, co
   const size_t budget = exchange_scratch_budget(ctx);
   int B = int(std::floor(std::sqrt(double(std::max<size_t>(1, budget / field)))));
   B = std::max(1, std::min(B, std::max(N, M)));
+  if (exchange64_applies(g) && sizeof(T) == 4) B = std::min(B, 6);
   char key[128];
   snprintf(key, sizeof(key), "sched:%d:%d:%d:%d", N, M, int(sym), B);
   auto it = ctx->caches.find(key);
@@ -301,6 +279,15 @@ long long exchange_t(pt_ctx* ctx, const cx<T>* src, const double* occ, int N, co
     ctx->caches[key] = sch;
   } else {
     sch = std::static_pointer_cast<ScheduleImpl>(it->second);
+  }
+  if (exchange64_applies(g)) {
+    if constexpr (sizeof(T) == 4) {
+      exchange64_tma(ctx, *sch, src, occ, tgt, M, out, ktab, static_cast<const cx<T>*>(ft.tw), st);
+      exchange_check(ctx, st);
+    } else {
+      exchange64<T>(ctx, *sch, src, occ, tgt, out, ktab, static_cast<const cx<T>*>(ft.tw), st);
+    }
+    return sch->total_pairs;
   }
   cx<T>* scratch = static_cast<cx<T>*>(ctx->get("exchange_scratch", size_t(sch->max_pairs) * field));
   set_smem_attrs<T>();
@@ -323,6 +310,14 @@ long long exchange_t(pt_ctx* ctx, const cx<T>* src, const double* occ, int N, co
 }  // namespace
 
 size_t exchange_scratch_budget(const pt_ctx* ctx) { return ctx->scratch_budget; }
+
+void exchange_check(pt_ctx* ctx, cudaStream_t st) {
+  int* err = static_cast<int*>(ctx->get("exchange_err", sizeof(int)));
+  int h = 0;
+  PT_CUDA_CHECK(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  PT_CUDA_CHECK(cudaStreamSynchronize(st));
+  if (h) fail(PT_TIMEOUT, "exchange: a TMA wait timed out on the device (code " + std::to_string(h) + ")");
+}
 
 long long exchange(pt_ctx* ctx, const void* src, const double* occ, int N, const void* tgt, int M, void* out,
                    const pt_grid& g, const pt_kernel& k, pt_precision prec, cudaStream_t st) {

@@ -1,0 +1,366 @@
+// FP32 pair-FFT exchange for 64^3 grids with TMA staging (Sec. IV-A1, Eq. vxdiag).
+//
+// Same four pipelined roles as the register/shared-memory kernel (A: pair product + x/y
+// transforms of a plane, B: z transform + K + inverse z of a slab, C: inverse y/x transforms
+// of a plane, D: occupation-weighted accumulate into the target plane), but every strided
+// access to a pair field goes through the tensor-memory accelerator:
+//   * plane and slab tiles are fetched with cp.async.bulk.tensor into 128B-swizzled shared
+//     tiles (four 16-wide sub-tiles of 128-byte rows); the 16-byte chunk c of row r sits at
+//     chunk c ^ (r mod 8), so the column reads of the line transforms (8 lanes on 8 rows of
+//     one column, 4 adjacent columns per warp) hit every bank exactly twice per warp;
+//   * the z-slab results of pass B go back to the scratch field with TMA stores.
+// Row-contiguous traffic (pass A/C results, pass D) stays on plain coalesced loads/stores.
+// Each CTA waits on its mbarrier with a %globaltimer deadline; on expiry it sets an error
+// word that the host checks after the call, and returns.
+#include <algorithm>
+#include <cstring>
+
+#include "exchange_sched.h"
+#include "fft.cuh"
+#include "internal.h"
+#include "tma.cuh"
+
+namespace pt {
+
+namespace {
+
+constexpr int G = 64;
+constexpr int PITCH = 68;
+constexpr int THREADS = 512;
+constexpr int MAXB = 6;                          // tile side of the pair schedule on this path
+constexpr int MAXP = MAXB * MAXB, MAXT = 2 * MAXB, MAXC = 2 * MAXP;
+constexpr uint32_t TILE_BYTES = 32768;           // 64 x 64 complex64
+constexpr uint32_t SUB_BYTES = 8192;             // 16 columns x 64 rows of 128 B
+constexpr uint32_t OFF_A = 0, OFF_B = 32768, OFF_P = 65536;
+constexpr uint32_t OFF_TW = OFF_P + G * PITCH * 8;  // 100352
+constexpr uint32_t OFF_BAR = OFF_TW + G * 8;        // 100864
+constexpr uint32_t SMEM_USED = OFF_BAR + 128;
+constexpr uint32_t SMEM_BYTES = SMEM_USED + 1024;   // slack to align the base to 1024 B
+constexpr uint64_t TIMEOUT_NS = 2000000000ull;      // 2 s
+
+// byte offset of element (column x, row r) inside a 64 x 64 swizzled tile
+__device__ __forceinline__ uint32_t sw_off(int x, int r) {
+  const int xx = x & 15;
+  return uint32_t(x >> 4) * SUB_BYTES + uint32_t(r) * 128u + uint32_t(((xx >> 1) ^ (r & 7)) << 4) +
+         uint32_t((xx & 1) << 3);
+}
+
+// group-transpose tile of group g inside a 32 KB region: element e stored at e ^ (8 (g & 1))
+__device__ __forceinline__ void fft64_tma(c64 (&v)[8], int t, c64* gs, int gpar, const c64* tw, bool inv) {
+  if (inv) dft8<true>(v);
+  else dft8<false>(v);
+  c64 w1 = tw[t];
+  if (inv) w1.im = -w1.im;
+  const c64 w2 = cmul(w1, w1), w4 = cmul(w2, w2);
+  v[1] = cmul(v[1], w1);
+  v[2] = cmul(v[2], w2);
+  v[3] = cmul(v[3], cmul(w1, w2));
+  v[4] = cmul(v[4], w4);
+  v[5] = cmul(v[5], cmul(w1, w4));
+  v[6] = cmul(v[6], cmul(w2, w4));
+  v[7] = cmul(v[7], cmul(cmul(w1, w2), w4));
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < 8; ++k) gs[(k * 8 + (t ^ k)) ^ gpar] = v[k];
+  __syncwarp();
+#pragma unroll
+  for (int s = 0; s < 8; ++s) v[s] = gs[(t * 8 + (s ^ t)) ^ gpar];
+  if (inv) dft8<true>(v);
+  else dft8<false>(v);
+}
+
+// The batch descriptors travel in the kernel parameters (constant bank): no dependent global
+// load stands between a CTA's start and its first TMA request.
+struct Launch {
+  int nA, nB, nC, nD;
+  int slotA, slotB, slotC, slotD;
+  int max_pairs, d_cbeg;
+  PairDesc pa[MAXP], pb[MAXP], pc[MAXP];
+  TargetDesc td[MAXT];
+  Contrib cd[MAXC];
+};
+
+__constant__ c64 c_tw64[G];
+
+__global__ void __launch_bounds__(THREADS, 2)
+    k_exchange64_tma(const __grid_constant__ CUtensorMap tm_src, const __grid_constant__ CUtensorMap tm_tgt,
+                     const __grid_constant__ CUtensorMap tm_plane, const __grid_constant__ CUtensorMap tm_slab,
+                     const __grid_constant__ Launch L, const c64* __restrict__ src, const double* __restrict__ occ,
+                     const float* __restrict__ ktab, c64* __restrict__ scratch, c64* __restrict__ out,
+                     int* __restrict__ err) {
+  extern __shared__ unsigned char smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  unsigned char* sm = smem_raw + (base - raw);
+  c64* P = reinterpret_cast<c64*>(sm + OFF_P);
+  c64* tw = reinterpret_cast<c64*>(sm + OFF_TW);
+  const uint32_t bar = base + OFF_BAR;
+  const int tid = threadIdx.x, grp = tid >> 3, t = tid & 7;
+  const int gpar = (grp & 1) << 3;
+  constexpr size_t ng = size_t(G) * G * G;
+  if (tid < G) tw[tid] = c_tw64[tid];
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  int bid = blockIdx.x;
+
+  if (bid < L.nA) {
+    // ---------------- pass A ----------------
+    const int z = bid % G, p = bid / G;
+    const PairDesc pd = L.pa[p];
+    if (tid == 0) {
+      mbar_arrive_expect_tx(bar, 2 * TILE_BYTES);
+      for (int s = 0; s < 4; ++s) {
+        tma_load_4d(base + OFF_A + s * SUB_BYTES, &tm_src, 16 * s, 0, z, pd.i, bar);
+        tma_load_4d(base + OFF_B + s * SUB_BYTES, &tm_tgt, 16 * s, 0, z, pd.j, bar);
+      }
+    }
+    const bool skip = pair_skipped(pd, occ);
+    if (!mbar_wait(bar, 0, TIMEOUT_NS)) {
+      atomicOr(err, 1);
+      return;
+    }
+    if (skip) return;
+    const int x = grp;
+    c64 v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const uint32_t o = sw_off(x, t + 8 * q);
+      v[q] = cmulc(*reinterpret_cast<const c64*>(sm + OFF_A + o), *reinterpret_cast<const c64*>(sm + OFF_B + o));
+    }
+    __syncthreads();  // tiles consumed: tile A becomes the group-transpose area
+    c64* gs = reinterpret_cast<c64*>(sm + OFF_A) + grp * 64;
+    fft64_tma(v, t, gs, gpar, tw, false);  // along y: lane t holds ky = t + 8k
+#pragma unroll
+    for (int k = 0; k < 8; ++k) P[(t + 8 * k) * PITCH + x] = v[k];
+    __syncthreads();
+    const int ky = grp;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = P[ky * PITCH + t + 8 * q];
+    fft64_tma(v, t, gs, gpar, tw, false);  // along x: lane t holds kx = t + 8k
+    c64* o = scratch + (size_t(L.slotA) * L.max_pairs + p) * ng + size_t(z) * G * G + ky * G;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) o[t + 8 * k] = v[k];
+    return;
+  }
+  bid -= L.nA;
+  if (bid < L.nB) {
+    // ---------------- pass B ----------------
+    const int ky = bid % G, p = bid / G;
+    const int kx = grp;
+    const PairDesc pd = L.pb[p];
+    const int orb = L.slotB * L.max_pairs + p;
+    if (tid == 0) {
+      mbar_arrive_expect_tx(bar, TILE_BYTES);
+      for (int s = 0; s < 4; ++s) tma_load_4d(base + OFF_A + s * SUB_BYTES, &tm_slab, 16 * s, ky, 0, orb, bar);
+    }
+    float kv[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) kv[k] = ktab[(size_t(t + 8 * k) * G + ky) * G + kx];
+    const bool skip = pair_skipped(pd, occ);
+    c64* gs = reinterpret_cast<c64*>(sm + OFF_B) + grp * 64;
+    if (!mbar_wait(bar, 0, TIMEOUT_NS)) {
+      atomicOr(err, 2);
+      return;
+    }
+    if (skip) return;
+    c64 v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = *reinterpret_cast<const c64*>(sm + OFF_A + sw_off(kx, t + 8 * q));
+    fft64_tma(v, t, gs, gpar, tw, false);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = v[k] * kv[k];
+    fft64_tma(v, t, gs, gpar, tw, true);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) *reinterpret_cast<c64*>(sm + OFF_A + sw_off(kx, t + 8 * k)) = v[k];
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      for (int s = 0; s < 4; ++s) tma_store_4d(&tm_slab, 16 * s, ky, 0, orb, base + OFF_A + s * SUB_BYTES);
+      tma_store_commit();
+      tma_store_wait_all();
+    }
+    return;
+  }
+  bid -= L.nB;
+  if (bid < L.nC) {
+    // ---------------- pass C ----------------
+    const int z = bid % G, p = bid / G;
+    const PairDesc pd = L.pc[p];
+    const int orb = L.slotC * L.max_pairs + p;
+    if (tid == 0) {
+      mbar_arrive_expect_tx(bar, TILE_BYTES);
+      for (int s = 0; s < 4; ++s) tma_load_4d(base + OFF_A + s * SUB_BYTES, &tm_plane, 16 * s, 0, z, orb, bar);
+    }
+    const bool skip = pair_skipped(pd, occ);
+    if (!mbar_wait(bar, 0, TIMEOUT_NS)) {
+      atomicOr(err, 4);
+      return;
+    }
+    if (skip) return;
+    const int kx = grp;
+    c64 v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = *reinterpret_cast<const c64*>(sm + OFF_A + sw_off(kx, t + 8 * q));
+    __syncthreads();
+    c64* gs = reinterpret_cast<c64*>(sm + OFF_A) + grp * 64;
+    fft64_tma(v, t, gs, gpar, tw, true);  // inverse along y: lane t holds y = t + 8k
+#pragma unroll
+    for (int k = 0; k < 8; ++k) P[(t + 8 * k) * PITCH + kx] = v[k];
+    __syncthreads();
+    const int y = grp;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = P[y * PITCH + t + 8 * q];
+    fft64_tma(v, t, gs, gpar, tw, true);  // inverse along x: lane t holds x = t + 8k
+    c64* o = scratch + size_t(orb) * ng + size_t(z) * G * G + y * G;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) o[t + 8 * k] = v[k];
+    return;
+  }
+  bid -= L.nC;
+  {
+    // ---------------- pass D (half a plane per CTA) ----------------
+    const int z = (bid >> 1) % G, half = bid & 1;
+    const TargetDesc td = L.td[(bid >> 1) / G];
+    constexpr int EPT = G * G / (2 * THREADS);
+    const int e0 = half * (G * G / 2) + tid;
+    const size_t zoff = size_t(z) * G * G;
+    c64 acc[EPT];
+#pragma unroll
+    for (int u = 0; u < EPT; ++u) acc[u] = czero<float>();
+    for (int c = td.cbeg; c < td.cend; c += 2) {
+      const bool two = c + 1 < td.cend;
+      const Contrib c0 = L.cd[c - L.d_cbeg];
+      const Contrib c1 = L.cd[(two ? c + 1 : c) - L.d_cbeg];
+      const float f0 = float(occ[c0.occ]);
+      const float f1 = two ? float(occ[c1.occ]) : 0.f;
+      const c64* v0 = scratch + (size_t(L.slotD) * L.max_pairs + c0.slot) * ng + zoff + e0;
+      const c64* v1 = scratch + (size_t(L.slotD) * L.max_pairs + c1.slot) * ng + zoff + e0;
+      const c64* q0 = src + size_t(c0.partner) * ng + zoff + e0;
+      const c64* q1 = src + size_t(c1.partner) * ng + zoff + e0;
+      c64 a0[EPT], b0[EPT], a1[EPT], b1[EPT];
+#pragma unroll
+      for (int u = 0; u < EPT; ++u) {
+        a0[u] = v0[u * THREADS];
+        b0[u] = q0[u * THREADS];
+        a1[u] = v1[u * THREADS];
+        b1[u] = q1[u * THREADS];
+      }
+#pragma unroll
+      for (int u = 0; u < EPT; ++u) {
+        if (c0.conj) a0[u].im = -a0[u].im;
+        if (c1.conj) a1[u].im = -a1[u].im;
+        // a skipped pair (d = 0) left its scratch slot unwritten: never multiply stale data by 0
+        if (f0 != 0.f) acc[u] = acc[u] + cmul(b0[u], a0[u]) * f0;
+        if (f1 != 0.f) acc[u] = acc[u] + cmul(b1[u], a1[u]) * f1;
+      }
+    }
+    c64* o = out + size_t(td.t) * ng + zoff + e0;
+#pragma unroll
+    for (int u = 0; u < EPT; ++u) {
+      const int e = u * THREADS;
+      o[e] = td.first ? czero<float>() - acc[u] : o[e] - acc[u];
+    }
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    PT_CUDA_CHECK(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !p) fail(PT_CUDA, "cuTensorMapEncodeTiled entry point not found");
+    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+}  // namespace
+
+void encode_tmap_4d_u64(CUtensorMap* map, const void* base, const uint64_t dims[4], const uint64_t strides_bytes[3],
+                        const uint32_t box[4], CUtensorMapSwizzle swizzle) {
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  cuuint64_t d[4] = {dims[0], dims[1], dims[2], dims[3]};
+  cuuint64_t s[3] = {strides_bytes[0], strides_bytes[1], strides_bytes[2]};
+  cuuint32_t b[4] = {box[0], box[1], box[2], box[3]};
+  CUresult r = encode_fn()(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, const_cast<void*>(base), d, s, b, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) fail(PT_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string(int(r)) + ")");
+}
+
+void exchange64_tma(pt_ctx* ctx, const ScheduleImpl& sch, const c64* src, const double* occ, const c64* tgt, int M,
+                    c64* out, const float* ktab, const c64* tw, cudaStream_t st) {
+  if (sch.B > MAXB) fail(PT_INVALID_ARG, "64^3 exchange schedule tile exceeds the parameter-block capacity");
+  constexpr size_t ng = size_t(G) * G * G;
+  const int maxp = sch.max_pairs;
+  c64* scratch = static_cast<c64*>(ctx->get("exchange64_scratch", 4 * size_t(maxp) * ng * sizeof(c64)));
+  int* err = static_cast<int*>(ctx->get("exchange_err", sizeof(int)));
+  PT_CUDA_CHECK(cudaMemsetAsync(err, 0, sizeof(int), st));
+  static bool init = false;
+  if (!init) {
+    PT_CUDA_CHECK(cudaFuncSetAttribute(k_exchange64_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    c64 h[G];
+    for (int i = 0; i < G; ++i) {
+      const double ang = -2.0 * M_PI * double(i) / double(G);
+      h[i] = c64{float(std::cos(ang)), float(std::sin(ang))};
+    }
+    PT_CUDA_CHECK(cudaMemcpyToSymbol(c_tw64, h, sizeof(h)));
+    init = true;
+  }
+  (void)tw;
+  const uint64_t strides[3] = {G * 8, G * G * 8, ng * 8};
+  const uint32_t plane_box[4] = {16, 64, 1, 1};
+  const uint32_t slab_box[4] = {16, 1, 64, 1};
+  CUtensorMap tm_src, tm_tgt, tm_plane, tm_slab;
+  const uint64_t dsrc[4] = {G, G, G, uint64_t(sch.N)};
+  const uint64_t dtgt[4] = {G, G, G, uint64_t(M)};
+  const uint64_t dscr[4] = {G, G, G, uint64_t(4) * maxp};
+  encode_tmap_4d_u64(&tm_src, src, dsrc, strides, plane_box, CU_TENSOR_MAP_SWIZZLE_128B);
+  encode_tmap_4d_u64(&tm_tgt, tgt, dtgt, strides, plane_box, CU_TENSOR_MAP_SWIZZLE_128B);
+  encode_tmap_4d_u64(&tm_plane, scratch, dscr, strides, plane_box, CU_TENSOR_MAP_SWIZZLE_128B);
+  encode_tmap_4d_u64(&tm_slab, scratch, dscr, strides, slab_box, CU_TENSOR_MAP_SWIZZLE_128B);
+  const int nb = int(sch.pair_off.size()) - 1;
+  auto copy_pairs = [&](PairDesc* dst, int batch) {
+    const int p0 = sch.pair_off[batch], np = sch.pair_off[batch + 1] - p0;
+    std::copy(sch.h_pairs.begin() + p0, sch.h_pairs.begin() + p0 + np, dst);
+    return np;
+  };
+  Launch L;
+  for (int k = 0; k < nb + 3; ++k) {
+    std::memset(&L, 0, sizeof(L));
+    L.max_pairs = maxp;
+    if (k < nb) {
+      L.nA = G * copy_pairs(L.pa, k);
+      L.slotA = k % 4;
+    }
+    const int b = k - 1, c = k - 2, d = k - 3;
+    if (b >= 0 && b < nb) {
+      L.nB = G * copy_pairs(L.pb, b);
+      L.slotB = b % 4;
+    }
+    if (c >= 0 && c < nb) {
+      L.nC = G * copy_pairs(L.pc, c);
+      L.slotC = c % 4;
+    }
+    if (d >= 0) {
+      const int t0 = sch.tgt_off[d], nt = sch.tgt_off[d + 1] - t0;
+      std::copy(sch.h_tgts.begin() + t0, sch.h_tgts.begin() + t0 + nt, L.td);
+      L.d_cbeg = sch.h_tgts[t0].cbeg;
+      const int cend = sch.h_tgts[t0 + nt - 1].cend;
+      if (cend - L.d_cbeg > MAXC || nt > MAXT) fail(PT_INVALID_ARG, "exchange batch exceeds the parameter block");
+      std::copy(sch.h_contribs.begin() + L.d_cbeg, sch.h_contribs.begin() + cend, L.cd);
+      L.nD = 2 * G * nt;
+      L.slotD = d % 4;
+    }
+    const int grid = L.nA + L.nB + L.nC + L.nD;
+    if (grid == 0) continue;
+    PT_LAUNCH(k_exchange64_tma, grid, THREADS, SMEM_BYTES, st, tm_src, tm_tgt, tm_plane, tm_slab, L, src, occ, ktab,
+              scratch, out, err);
+  }
+}
+
+}  // namespace pt

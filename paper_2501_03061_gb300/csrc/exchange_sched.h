@@ -1,0 +1,60 @@
+// Pair schedule of the exchange: batches of pairs (i, j) whose pair fields share one scratch
+// slot, and per batch the list of targets with the contributions (pair, partner orbital,
+// occupation, conjugation) each target accumulates.
+#pragma once
+
+#include <memory>
+#include <vector>
+
+#include "common.cuh"
+
+namespace pt {
+
+struct PairDesc {
+  int i, j;    // source index, target index
+  int o1, o2;  // occupation indices of its contributions (o2 < 0: a single one)
+};
+struct TargetDesc {
+  int t, cbeg, cend, first;
+};
+struct Contrib {
+  int slot, partner, occ, conj;
+};
+
+__device__ __forceinline__ bool pair_skipped(const PairDesc& pd, const double* occ) {
+  return occ[pd.o1] == 0.0 && (pd.o2 < 0 || occ[pd.o2] == 0.0);
+}
+
+struct ScheduleImpl {
+  int N = 0, M = 0, B = 0;
+  bool sym = false;
+  std::vector<int> pair_off, tgt_off;  // per batch offsets (size nbatch+1)
+  PairDesc* d_pairs = nullptr;
+  TargetDesc* d_tgts = nullptr;
+  Contrib* d_contribs = nullptr;
+  std::vector<PairDesc> h_pairs;
+  std::vector<TargetDesc> h_tgts;
+  std::vector<Contrib> h_contribs;
+  int max_pairs = 0, max_tgts = 0;
+  long long total_pairs = 0;
+  ~ScheduleImpl() {
+    cudaFree(d_pairs);
+    cudaFree(d_tgts);
+    cudaFree(d_contribs);
+  }
+};
+
+// tiles of B x B orbitals; symmetric: I <= J tiles with i <= j inside diagonal tiles
+std::shared_ptr<ScheduleImpl> build_schedule(int N, int M, bool sym, int B);
+
+bool exchange64_applies(const pt_grid& g);
+// FP32 64^3 path with TMA staging; sets a device error word on a wait timeout (see exchange_check)
+void exchange64_tma(pt_ctx* ctx, const ScheduleImpl& sch, const c64* src, const double* occ, const c64* tgt, int M,
+                    c64* out, const float* ktab, const c64* tw, cudaStream_t st);
+// synchronise st and fail with PT_TIMEOUT if a bounded device wait expired
+void exchange_check(pt_ctx* ctx, cudaStream_t st);
+template <class T>
+void exchange64(pt_ctx* ctx, const ScheduleImpl& sch, const cx<T>* src, const double* occ, const cx<T>* tgt,
+                cx<T>* out, const T* ktab, const cx<T>* tw, cudaStream_t st);
+
+}  // namespace pt

@@ -217,11 +217,29 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
   const int sblocks = std::max(1, std::min<int>(ctx->num_sms * 8, int((S.n1 + nthreads - 1) / nthreads)));
   const int sblocks2 = std::max(1, int((S.n2 + nthreads - 1) / nthreads));
 
+  // event pairs bracketing each exchange application (read once the step has synchronised)
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+  struct EvGuard {
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& v;
+    ~EvGuard() {
+      for (auto& e : v) {
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+      }
+    }
+  } ev_guard{ev};
   // V_x[P_h] Phi_h through the sigma_h eigenbasis: (V_x phit) Q^*, phit = Phi_h Q
   auto exchange_on_midpoint = [&](cx<T>* out, bool energy) {
     heev(ctx, sigh, N, Q, d, st);
     rotate<T>(ctx, phih, Q, N, N, N, S.ng, c128{1, 0}, nullptr, 0, phit, st);
+    std::pair<cudaEvent_t, cudaEvent_t> e;
+    PT_CUDA_CHECK(cudaEventCreate(&e.first));
+    PT_CUDA_CHECK(cudaEventCreate(&e.second));
+    ev.push_back(e);
+    PT_CUDA_CHECK(cudaEventRecord(e.first, st));
     stv.pair_ffts += exchange(ctx, phit, d, N, nullptr, N, vphit, g, kern, prec, st);
+    PT_CUDA_CHECK(cudaEventRecord(e.second, st));
+    stv.exchange_calls++;
     if (energy) {
       PT_LAUNCH(k_weighted_diag<T>, N, 256, 0, st, phit, vphit, d, S.ng, S.dV, dsc);
       std::vector<double> h(N);
@@ -383,6 +401,11 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
   PT_CUDA_CHECK(cudaMemcpyAsync(&h_info, info, sizeof(int), cudaMemcpyDeviceToHost, st));
   PT_CUDA_CHECK(cudaStreamSynchronize(st));
   if (h_info) fail(PT_NOT_PD, "PT-IM: final overlap matrix is not positive definite");
+  for (auto& e : ev) {
+    float ms = 0.f;
+    PT_CUDA_CHECK(cudaEventElapsedTime(&ms, e.first, e.second));
+    stv.exchange_ms += ms;
+  }
   stv.converged = converged ? 1 : 0;
   if (stats) *stats = stv;
   return converged ? PT_OK : PT_NOT_CONVERGED;

@@ -279,3 +279,24 @@ def test_ptim_step_fp32_matches_oracle(ctx, ptim_ref):
     assert st["converged"]
     assert rel(phi.cpu().numpy().astype(np.complex128), ptim_ref[0]) <= 5e-5
     assert np.abs(sigma.cpu().numpy() - ptim_ref[1]).max() <= 5e-5
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("sym", [True, False])
+def test_exchange_64cubed_specialised_path(ctx, precision, sym):
+    """The 64^3 kernel (pipelined plane/column/plane roles) against the oracle, several batches."""
+    rng = np.random.default_rng(64 + sym)
+    cell = synth.cubic(64, 20.5)
+    src = synth.random_orbitals(rng, cell, 7)
+    tgt = src if sym else synth.random_orbitals(rng, cell, 3)
+    occ = np.array([1.0, 0.0, 0.8, 0.45, 0.2, 0.05, 0.7])
+    g = O.grid_of(cell)
+    ref = O.apply_exchange(src, occ, tgt, O.exchange_kernel(g, 1, synth.SCREENED_MU))
+    dt = np.complex128 if precision == "fp64" else np.complex64
+    ctx.set_option("scratch_bytes", 4 * g.ng * (16 if precision == "fp64" else 8))  # 2x2 pair tiles
+    try:
+        out = ctx.apply_exchange(dev(src.astype(dt)), dev(occ), None if sym else dev(tgt.astype(dt)), cell=cell,
+                                 kernel={"type": 1, "mu": synth.SCREENED_MU}, precision=precision)
+    finally:
+        ctx.set_option("scratch_bytes", 48 << 20)
+    assert rel(out.cpu().numpy().astype(np.complex128), ref) <= (FP64_TOL if precision == "fp64" else FP32_TOL)
