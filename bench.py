@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--N", type=int, default=320, help="orbital count (reduced values only for profiler captures)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 form comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
@@ -195,7 +196,7 @@ def run_gb300(args):
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = run_cpu_sample_subprocess()  # before any GPU work in this process tree
 
-    w = synth.ptim_cell128()
+    w = synth.ptim_cell128(N=args.N)
     ng = w.cell.ng
     N = w.N
     cdt = np.complex64 if args.precision == "fp32" else np.complex128
@@ -206,6 +207,7 @@ def run_gb300(args):
     phi = phi0.to(devc)
     sigma = sig0.to(devc)
     vloc = vloc0.to(devc)
+    workload = WORKLOAD if N == 320 else WORKLOAD.replace("N320", f"N{N}")
     kw = dict(cell=w.cell, kernel=w.kernel, precision=args.precision, dt=0.5, alpha=0.25, ecut=10.0,
               tol=args.tol, max_outer=20, max_inner=100, anderson_depth=20, allow_unconverged=True)
     stream = torch.cuda.current_stream()
@@ -312,7 +314,7 @@ def run_gb300(args):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64" if args.precision == "fp32" else "c128",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": [64, 64, 64], "N": N, "atoms": 128, "precision": args.precision,
+            "config": {"workload": workload, "grid": [64, 64, 64], "N": N, "atoms": 128, "precision": args.precision,
                        "tol": args.tol, "dt_au": 0.5, "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (phi alone is %d MB)" % (N * ng * esz >> 20)},
             "pair_ffts_per_s": pair_ffts / (ms / 1e3) if ms > 0 else None,
@@ -321,6 +323,8 @@ def run_gb300(args):
                          "share_of_step": ex_ms / ms if ms else None},
             "iterations": [{"outer": s["outer"], "inner": s["inner"], "residual": s["residual"],
                             "converged": s["converged"]} for s in stats],
+            "phases_ms_per_step": {k: sum(s["phase_ms"][k] for s in stats) / len(stats)
+                                   for k in stats[0]["phase_ms"]},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": (achieved / peak) if achieved else None, "traffic": None,
                          "kernel": "pair-FFT exchange (plane/column/plane passes)",

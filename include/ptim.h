@@ -171,6 +171,12 @@ typedef struct {
   long long pair_ffts;      /* pair FFTs executed (counting a symmetric pair once) */
   int exchange_calls;       /* V_x applications */
   double exchange_ms;       /* device time of those applications (CUDA events on the stream) */
+  /* device time per phase (CUDA events on the stream):
+     0 exchange, 1 ACE build (Gram, Cholesky, xi), 2 ACE apply, 3 H application,
+     4 subspace contractions (A, S, projection), 5 subspace N x N (Cholesky, inverse, S^{-1}A),
+     6 sigma diagonalisation, 7 rotations into/out of the sigma eigenbasis, 8 sigma commutator,
+     9 Anderson mixing and residual norms, 10 final Loewdin orthonormalisation, 11 spare */
+  double phase_ms[12];
 } pt_ptim_stats;
 
 /* One PT-IM(-ACE) step from (phi, sigma) = (Phi_n, sigma_n) to (Phi_{n+1}, sigma_{n+1}),

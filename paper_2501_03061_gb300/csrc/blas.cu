@@ -99,16 +99,90 @@ __global__ void __launch_bounds__(GTHREADS) k_gram(const cx<T>* __restrict__ A, 
     }
 }
 
-__global__ void k_reduce_parts(const c128* __restrict__ part, int nsplit, size_t n, double scale,
-                               c128* __restrict__ C) {
+// FP32 Gram tile of 64 x 64 outputs, 4 x 4 complex per thread, 16 grid points per stage; the
+// per-stage sums are folded into Kahan-compensated totals.  With herm, only tiles on or above
+// the diagonal run (the reduction mirrors the rest).
+constexpr int G4T = 64, G4K = 16, G4THREADS = 256;
+
+__global__ void __launch_bounds__(G4THREADS, 2) k_gram64(const c64* __restrict__ A, const c64* __restrict__ B,
+                                                         int N1, int N2, size_t ng, size_t chunk, int herm,
+                                                         c128* __restrict__ part) {
+  if (herm && blockIdx.y < blockIdx.x) return;
+  __shared__ c64 As[G4K][G4T + 1];
+  __shared__ c64 Bs[G4K][G4T + 1];
+  const int i0 = blockIdx.x * G4T, j0 = blockIdx.y * G4T;
+  const size_t r_begin = size_t(blockIdx.z) * chunk;
+  const size_t r_end = std::min(ng, r_begin + chunk);
+  const int tid = threadIdx.x;
+  const int ti = tid % 16, tj = tid / 16;
+  Acc<float> sre[4][4], sim[4][4];
+  for (size_t r0 = r_begin; r0 < r_end; r0 += G4K) {
+#pragma unroll
+    for (int pass = 0; pass < (G4T * G4K) / G4THREADS; ++pass) {
+      const int e = tid + pass * G4THREADS;
+      const int k = e % G4K, o = e / G4K;
+      const size_t r = r0 + k;
+      c64 va = czero<float>(), vb = czero<float>();
+      if (r < r_end) {
+        if (i0 + o < N1) va = A[size_t(i0 + o) * ng + r];
+        if (j0 + o < N2) vb = B[size_t(j0 + o) * ng + r];
+      }
+      As[k][o] = va;
+      Bs[k][o] = vb;
+    }
+    __syncthreads();
+    c64 acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = czero<float>();
+#pragma unroll 4
+    for (int k = 0; k < G4K; ++k) {
+      c64 av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = conjc(As[k][ti + 16 * a]);
+#pragma unroll
+      for (int b = 0; b < 4; ++b) bv[b] = Bs[k][tj + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) cfma(acc[a][b], av[a], bv[b]);
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        sre[a][b].add(acc[a][b].re);
+        sim[a][b].add(acc[a][b].im);
+      }
+    __syncthreads();
+  }
+  c128* P = part + size_t(blockIdx.z) * N1 * N2;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int i = i0 + ti + 16 * a, j = j0 + tj + 16 * b;
+      if (i < N1 && j < N2) P[size_t(i) * N2 + j] = c128{sre[a][b].value(), sim[a][b].value()};
+    }
+}
+
+// C = scale * sum of split partials; herm_tile > 0: elements whose tile row is below the tile
+// column were not computed and are taken as the conjugate of the mirrored element
+__global__ void k_reduce_parts(const c128* __restrict__ part, int nsplit, int N1, int N2, double scale,
+                               int herm_tile, c128* __restrict__ C) {
+  const size_t n = size_t(N1) * N2;
   const size_t e = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (e >= n) return;
+  const int i = int(e / N2), j = int(e % N2);
+  const bool mirror = herm_tile > 0 && (i / herm_tile) > (j / herm_tile);
+  const size_t src = mirror ? size_t(j) * N2 + i : e;
   double re = 0, im = 0;
   for (int s = 0; s < nsplit; ++s) {
-    re += part[size_t(s) * n + e].re;
-    im += part[size_t(s) * n + e].im;
+    re += part[size_t(s) * n + src].re;
+    im += part[size_t(s) * n + src].im;
   }
-  C[e] = c128{re * scale, im * scale};
+  C[e] = mirror ? c128{re * scale, -im * scale} : c128{re * scale, im * scale};
 }
 
 // ---------------------------------------------------------------- rotate (A Bm + E) ----
@@ -291,18 +365,28 @@ int stream_blocks(pt_ctx* ctx, size_t n, int threads) {
 // ------------------------------------------------------------------------------------------
 template <class T>
 void gram(pt_ctx* ctx, const cx<T>* A, const cx<T>* B, int N1, int N2, size_t ng, double scale, c128* C,
-          cudaStream_t st) {
-  const int ti = (N1 + GT - 1) / GT, tj = (N2 + GT - 1) / GT;
-  const int tiles = ti * tj;
-  // enough splits along r to fill the GPU about four times; chunks are multiples of GK
+          cudaStream_t st, bool herm) {
+  const bool f32 = sizeof(T) == 4;
+  const int tile = f32 ? G4T : GT;
+  const int kstep = f32 ? G4K : GK;
+  herm = herm && (N1 == N2);
+  const int ti = (N1 + tile - 1) / tile, tj = (N2 + tile - 1) / tile;
+  const int tiles = herm ? ti * (ti + 1) / 2 : ti * tj;
+  // enough splits along r to fill the GPU about four times (two CTAs per SM for the FP32 tile)
   int splits = std::max(1, (ctx->num_sms * 4 + tiles - 1) / tiles);
   size_t chunk = (ng + splits - 1) / splits;
-  chunk = (chunk + GK - 1) / GK * GK;
+  chunk = (chunk + kstep - 1) / kstep * kstep;
   splits = int((ng + chunk - 1) / chunk);
   c128* part = static_cast<c128*>(ctx->get("gram_parts", size_t(splits) * N1 * N2 * sizeof(c128)));
-  PT_LAUNCH(k_gram<T>, dim3(ti, tj, splits), GTHREADS, 0, st, A, B, N1, N2, ng, chunk, part);
+  if constexpr (sizeof(T) == 4) {
+    PT_LAUNCH(k_gram64, dim3(ti, tj, splits), G4THREADS, 0, st, A, B, N1, N2, ng, chunk, int(herm), part);
+  } else {
+    herm = false;
+    PT_LAUNCH(k_gram<T>, dim3(ti, tj, splits), GTHREADS, 0, st, A, B, N1, N2, ng, chunk, part);
+  }
   const size_t n = size_t(N1) * N2;
-  PT_LAUNCH(k_reduce_parts, dim3(unsigned((n + 255) / 256)), 256, 0, st, part, splits, n, scale, C);
+  PT_LAUNCH(k_reduce_parts, dim3(unsigned((n + 255) / 256)), 256, 0, st, part, splits, N1, N2, scale,
+            herm ? tile : 0, C);
 }
 
 template <class T>
@@ -354,8 +438,8 @@ void multi_dot(pt_ctx* ctx, const void* const* u1, const c128* const* u2, int m,
   PT_LAUNCH(k_reduce_dots, m, 256, 0, st, part, nblk, m, out);
 }
 
-template void gram<float>(pt_ctx*, const c64*, const c64*, int, int, size_t, double, c128*, cudaStream_t);
-template void gram<double>(pt_ctx*, const c128*, const c128*, int, int, size_t, double, c128*, cudaStream_t);
+template void gram<float>(pt_ctx*, const c64*, const c64*, int, int, size_t, double, c128*, cudaStream_t, bool);
+template void gram<double>(pt_ctx*, const c128*, const c128*, int, int, size_t, double, c128*, cudaStream_t, bool);
 template void rotate<float>(pt_ctx*, const c64*, const c128*, int, int, int, size_t, c128, const Term*, int, c64*,
                             cudaStream_t);
 template void rotate<double>(pt_ctx*, const c128*, const c128*, int, int, int, size_t, c128, const Term*, int,

@@ -4,8 +4,8 @@
 //   heev         Hermitian eigen-decomposition by parallel two-sided cyclic Jacobi
 //                (round-robin pairing; one launch per round; every 2x2 block of the
 //                matrix is updated by J_k^H X J_l in the same launch)
-//   cholesky     lower Cholesky, one rank-1 update launch per column, error flag on a
-//                non-positive or non-finite pivot
+//   cholesky     blocked lower Cholesky (32-wide panels), error flag on a non-positive or
+//                non-finite pivot
 //   tri_inv      L^{-1} of a lower-triangular matrix, one CTA per column
 //   small_solve  m x m (m <= 24) Gaussian elimination with partial pivoting, one thread
 // All matrices are row-major complex128: a[i*ld + j].
@@ -135,10 +135,13 @@ __global__ void __launch_bounds__(JB* JB) k_jacobi_round(const c128* __restrict_
     put(q1, p2, z10);
     put(q1, q2, z11);
   }
-  // V <- V J for the column pairs of this CTA's l-range, rows split across the k-range CTAs
-  if (blockIdx.y == 0) {
-    for (int e = t; e < N * JB; e += JB * JB) {
-      const int row = e / JB, tl2 = e % JB;
+  // V <- V J for the column pairs of this CTA's l-range; the rows are split over the CTAs of the
+  // same l-range so every CTA of the grid shares the update
+  {
+    const int rows_per = (N + gridDim.y - 1) / gridDim.y;
+    const int r0 = blockIdx.y * rows_per, r1 = min(N, r0 + rows_per);
+    for (int e = t; e < (r1 - r0) * JB; e += JB * JB) {
+      const int row = r0 + e / JB, tl2 = e % JB;
       const int l2 = lb + tl2;
       if (l2 >= half) continue;
       const int p2 = pl[tl2], q2 = ql[tl2];
@@ -207,31 +210,113 @@ __global__ void k_sort_eig(const c128* __restrict__ A, const c128* __restrict__ 
 }
 
 // ---------------------------------------------------------------- Cholesky ----
-__global__ void k_chol_step(c128* __restrict__ A, int N, int k, int* __restrict__ info) {
+// Right-looking blocked Cholesky with CB-wide panels.  Per panel: the diagonal block is
+// factored (and inverted) in one CTA's shared memory, the panel below is solved against the
+// inverse of the diagonal block, and the trailing lower triangle gets a rank-CB update.
+constexpr int CB = 32;
+
+__global__ void __launch_bounds__(256) k_chol_diag(c128* __restrict__ A, int N, int kb, int bs,
+                                                   c128* __restrict__ Winv, int* __restrict__ info) {
+  __shared__ c128 a[CB][CB + 1];
+  __shared__ c128 x[CB][CB + 1];
   if (*info) return;
-  const double piv = A[size_t(k) * N + k].re;
-  if (!(piv > 0.0) || !isfinite(piv)) {
-    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *info = k + 1;
-    return;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < bs * bs; e += blockDim.x) {
+    const int i = e / bs, j = e % bs;
+    a[i][j] = A[size_t(kb + i) * N + kb + j];
   }
-  const int i = k + 1 + blockIdx.y * 16 + threadIdx.x / 16;
-  const int j = k + 1 + blockIdx.x * 16 + threadIdx.x % 16;
-  if (i >= N || j > i) return;
-  const c128 aik = A[size_t(i) * N + k], ajk = A[size_t(j) * N + k];
-  const c128 upd = cmulc(ajk, aik);  // A[i][k] conj(A[j][k])
-  A[size_t(i) * N + j] = A[size_t(i) * N + j] - upd * (1.0 / piv);
+  __syncthreads();
+  for (int k = 0; k < bs; ++k) {
+    const double piv = a[k][k].re;
+    if (!(piv > 0.0) || !isfinite(piv)) {
+      if (tid == 0) *info = kb + k + 1;
+      return;  // uniform: every thread read the same pivot
+    }
+    const double dk = sqrt(piv);
+    __syncthreads();
+    if (tid == 0) a[k][k] = c128{dk, 0.0};
+    for (int i = k + 1 + tid; i < bs; i += blockDim.x) a[i][k] = a[i][k] * (1.0 / dk);
+    __syncthreads();
+    for (int e = tid; e < bs * bs; e += blockDim.x) {
+      const int i = e / bs, j = e % bs;
+      if (j > k && i >= j) a[i][j] = a[i][j] - cmulc(a[j][k], a[i][k]);
+    }
+    __syncthreads();
+  }
+  // inverse of the lower-triangular factor, one column per thread
+  if (tid < bs) {
+    const int j = tid;
+    for (int i = 0; i < bs; ++i) {
+      if (i < j) {
+        x[i][j] = czero<double>();
+        continue;
+      }
+      c128 acc = c128{i == j ? 1.0 : 0.0, 0.0};
+      for (int p = j; p < i; ++p) acc = acc - cmul(a[i][p], x[p][j]);
+      const c128 lii = a[i][i];
+      x[i][j] = acc * (1.0 / lii.re);
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < bs * bs; e += blockDim.x) {
+    const int i = e / bs, j = e % bs;
+    if (j <= i) A[size_t(kb + i) * N + kb + j] = a[i][j];
+    Winv[i * CB + j] = x[i][j];
+  }
+}
+
+// L_ik = A_ik L_kk^{-*} for the rows below the diagonal block (8 rows per CTA)
+__global__ void __launch_bounds__(256) k_chol_panel(c128* __restrict__ A, int N, int kb, int bs,
+                                                    const c128* __restrict__ Winv, const int* __restrict__ info) {
+  __shared__ c128 w[CB][CB + 1];
+  __shared__ c128 r[8][CB + 1];
+  if (*info) return;
+  const int tid = threadIdx.x;
+  const int i0 = kb + bs + blockIdx.x * 8;
+  for (int e = tid; e < bs * bs; e += blockDim.x) w[e / bs][e % bs] = Winv[(e / bs) * CB + (e % bs)];
+  for (int e = tid; e < 8 * bs; e += blockDim.x) {
+    const int ii = e / bs, p = e % bs;
+    r[ii][p] = (i0 + ii < N) ? A[size_t(i0 + ii) * N + kb + p] : czero<double>();
+  }
+  __syncthreads();
+  const int ii = tid / CB, j = tid % CB;
+  if (i0 + ii < N && j < bs) {
+    c128 acc = czero<double>();
+    // (L_kk^{-*})[p][j] = conj(Winv[j][p]), nonzero for p <= j
+    for (int p = 0; p <= j; ++p) acc = acc + cmul(r[ii][p], conjc(w[j][p]));
+    A[size_t(i0 + ii) * N + kb + j] = acc;
+  }
+}
+
+// trailing update A[i][j] -= sum_p L[i][kb+p] conj(L[j][kb+p]) for kb+bs <= j <= i < N
+__global__ void __launch_bounds__(256) k_chol_update(c128* __restrict__ A, int N, int kb, int bs,
+                                                     const int* __restrict__ info) {
+  if (*info) return;
+  const int t0 = kb + bs;
+  const int bi = blockIdx.y, bj = blockIdx.x;
+  if (bj > bi) return;
+  __shared__ c128 li[16][CB + 1], lj[16][CB + 1];
+  const int tid = threadIdx.x;
+  const int ib = t0 + bi * 16, jb = t0 + bj * 16;
+  for (int e = tid; e < 16 * bs; e += blockDim.x) {
+    const int q = e / bs, p = e % bs;
+    li[q][p] = (ib + q < N) ? A[size_t(ib + q) * N + kb + p] : czero<double>();
+    lj[q][p] = (jb + q < N) ? A[size_t(jb + q) * N + kb + p] : czero<double>();
+  }
+  __syncthreads();
+  const int i = ib + tid / 16, j = jb + tid % 16;
+  if (i < N && j < N && j <= i) {
+    c128 acc = czero<double>();
+    for (int p = 0; p < bs; ++p) acc = acc + cmulc(lj[tid % 16][p], li[tid / 16][p]);
+    A[size_t(i) * N + j] = A[size_t(i) * N + j] - acc;
+  }
 }
 
 __global__ void k_chol_finish(const c128* __restrict__ A, int N, c128* __restrict__ L, const int* __restrict__ info) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= N * N || *info) return;
   const int i = e / N, j = e % N;
-  if (j > i) {
-    L[e] = czero<double>();
-    return;
-  }
-  const double dj = sqrt(A[size_t(j) * N + j].re);
-  L[e] = (i == j) ? c128{dj, 0.0} : A[e] * (1.0 / dj);
+  L[e] = (j > i) ? czero<double>() : A[e];
 }
 
 // X = L^{-1}, column c per CTA (forward substitution, column-oriented)
@@ -321,12 +406,19 @@ void heev(pt_ctx* ctx, const c128* S, int N, c128* Q, double* d, cudaStream_t st
   const int half = Np / 2;
   dim3 grid((half + JB - 1) / JB, (half + JB - 1) / JB);
   double h[2] = {0, 0};
+  double prev_off = INFINITY;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     PT_LAUNCH(k_offnorm, 1, 1024, 0, st, A0, N, nrm);
     PT_CUDA_CHECK(cudaMemcpyAsync(h, nrm, sizeof(h), cudaMemcpyDeviceToHost, st));
     PT_CUDA_CHECK(cudaStreamSynchronize(st));
     if (!std::isfinite(h[1])) fail(PT_NONFINITE, "non-finite entry in the matrix to diagonalise");
-    if (h[0] <= 1e-30 * h[1] || h[0] == 0.0) break;
+    // Converged when the off-diagonal norm is at the FP64 rounding floor (eps * sqrt(N) * ||A||),
+    // or when, already small, a sweep no longer reduces it (cyclic Jacobi converges
+    // quadratically, so a stalled sweep means rounding noise).
+    const double floor2 = 1e-32 * double(N) * h[1];
+    if (h[0] <= floor2 || h[0] == 0.0) break;
+    if (h[0] <= 1e-24 * h[1] && h[0] > 0.25 * prev_off) break;
+    prev_off = h[0];
     for (int r = 0; r < Np - 1; ++r) {
       PT_LAUNCH(k_jacobi_round, grid, JB * JB, 0, st, A0, A1, V, N, Np, r);
       std::swap(A0, A1);
@@ -336,17 +428,16 @@ void heev(pt_ctx* ctx, const c128* S, int N, c128* Q, double* d, cudaStream_t st
 }
 
 void cholesky(pt_ctx* ctx, c128* A, int N, c128* L, int* info, cudaStream_t st) {
-  (void)ctx;
+  c128* winv = static_cast<c128*>(ctx->get("chol_winv", size_t(CB) * CB * sizeof(c128)));
   PT_CUDA_CHECK(cudaMemsetAsync(info, 0, sizeof(int), st));
-  for (int k = 0; k < N; ++k) {
-    const int rem = N - k - 1;
-    if (rem <= 0) {
-      // the last pivot is still checked by finish through the diagonal
-      PT_LAUNCH(k_chol_step, dim3(1, 1), 256, 0, st, A, N, k, info);
-      break;
-    }
-    dim3 grid((rem + 15) / 16, (rem + 15) / 16);
-    PT_LAUNCH(k_chol_step, grid, 256, 0, st, A, N, k, info);
+  for (int kb = 0; kb < N; kb += CB) {
+    const int bs = std::min(CB, N - kb);
+    PT_LAUNCH(k_chol_diag, 1, 256, 0, st, A, N, kb, bs, winv, info);
+    const int rest = N - kb - bs;
+    if (rest <= 0) break;
+    PT_LAUNCH(k_chol_panel, (rest + 7) / 8, 256, 0, st, A, N, kb, bs, winv, info);
+    const int nt = (rest + 15) / 16;
+    PT_LAUNCH(k_chol_update, dim3(nt, nt), 256, 0, st, A, N, kb, bs, info);
   }
   PT_LAUNCH(k_chol_finish, (N * N + 255) / 256, 256, 0, st, A, N, L, info);
 }
@@ -357,6 +448,24 @@ void tri_inv_lower(const c128* L, int N, c128* X, cudaStream_t st) {
 
 void scale_cols_pow(const c128* U, const double* lam, int N, double power, c128* out, int* info, cudaStream_t st) {
   PT_LAUNCH(k_scale_cols_pow, (N * N + 255) / 256, 256, 0, st, U, lam, N, power, out, info);
+}
+
+__global__ void k_set_identity(c128* __restrict__ A, int N) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < N * N) A[e] = c128{(e / N == e % N) ? 1.0 : 0.0, 0.0};
+}
+
+__global__ void k_add_diagonal(c128* __restrict__ A, int N, double v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) A[size_t(i) * N + i].re += v;
+}
+
+void set_identity(c128* A, int N, cudaStream_t st) {
+  PT_LAUNCH(k_set_identity, (N * N + 255) / 256, 256, 0, st, A, N);
+}
+
+void add_diagonal(c128* A, int N, double v, cudaStream_t st) {
+  PT_LAUNCH(k_add_diagonal, (N + 255) / 256, 256, 0, st, A, N, v);
 }
 
 void small_solve(const double* G, const double* rhs, int m, double reg, double* x, cudaStream_t st) {

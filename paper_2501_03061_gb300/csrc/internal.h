@@ -20,7 +20,7 @@ long long exchange(pt_ctx* ctx, const void* src, const double* occ, int N, const
 // ---- contractions over the grid (blas.cu) ----
 template <class T>
 void gram(pt_ctx* ctx, const cx<T>* A, const cx<T>* B, int N1, int N2, size_t ng, double scale, c128* C,
-          cudaStream_t st);
+          cudaStream_t st, bool herm = false);
 template <class T>
 void rotate(pt_ctx* ctx, const cx<T>* A, const c128* Bm, int ldb, int N1, int N2, size_t ng, c128 alpha,
             const Term* terms, int nterms, cx<T>* out, cudaStream_t st);
@@ -43,6 +43,31 @@ void cholesky(pt_ctx* ctx, c128* A, int N, c128* L, int* info, cudaStream_t st);
 void tri_inv_lower(const c128* L, int N, c128* X, cudaStream_t st);
 void scale_cols_pow(const c128* U, const double* lam, int N, double power, c128* out, int* info, cudaStream_t st);
 void small_solve(const double* G, const double* rhs, int m, double reg, double* x, cudaStream_t st);
+void set_identity(c128* A, int N, cudaStream_t st);
+void add_diagonal(c128* A, int N, double v, cudaStream_t st);
+
+// ---- Anderson mixing (anderson.cu) ----
+template <class T>
+struct AndersonSeg {
+  const cx<T>* rk;     // current residual
+  const cx<T>* rprev;  // previous residual
+  const cx<T>* dxp;    // x_k - x_{k-1} from the last update
+  cx<T>* dRs;          // new history entry dR_s (written)
+  cx<T>* Zs;           // new history entry Z_s = dX + beta dR_s (written)
+  const cx<T>* dR[20]; // the other entries' dR, in the caller's order
+  size_t n;
+};
+// dots: for each other entry o: <dR_o, dR_s>, <dR_o, r_k>; then <dR_s, dR_s>, <dR_s, r_k>
+// (orbital segment weighted by w_phi, sigma segment by 1)
+template <class T>
+void anderson_prepare(pt_ctx* ctx, const AndersonSeg<T>& phi, const AndersonSeg<double>& sig, int mo, double beta,
+                      double w_phi, double* dots, cudaStream_t st);
+void anderson_gram(double* G, const double* dots, int s, const int* others_d, int mo, const int* order_d, int m,
+                   double* Gp, double* rhs, cudaStream_t st);
+// x += beta r - sum_a gamma_a Z_a;  dxp = that increment
+template <class T>
+void anderson_update(pt_ctx* ctx, cx<T>* x, const cx<T>* r, const cx<T>* const* Z, int m, const double* gamma,
+                     double beta, cx<T>* dxp, size_t n, cudaStream_t st);
 
 // ---- Hamiltonian (hamiltonian.cu) ----
 // out = P_sph[ -1/2 Lap psi + y ],  y = vloc*psi + alpha*X (X may be null)

@@ -22,6 +22,43 @@ namespace {
 
 constexpr int kMaxDepth = 20;
 
+// CUDA events around the phases of a step, summed per phase once the step has synchronised.
+class PhaseTimer {
+ public:
+  explicit PhaseTimer(cudaStream_t st) : st_(st) {}
+  ~PhaseTimer() {
+    for (auto& r : recs_) {
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+  }
+  void begin(int phase) {
+    Rec r{phase, nullptr, nullptr};
+    check_cuda(cudaEventCreate(&r.a), "cudaEventCreate");
+    check_cuda(cudaEventCreate(&r.b), "cudaEventCreate");
+    check_cuda(cudaEventRecord(r.a, st_), "cudaEventRecord");
+    recs_.push_back(r);
+  }
+  void end() { check_cuda(cudaEventRecord(recs_.back().b, st_), "cudaEventRecord"); }
+  // the stream must have been synchronised
+  void sum(double* ms) const {
+    for (const auto& r : recs_) {
+      float t = 0.f;
+      check_cuda(cudaEventElapsedTime(&t, r.a, r.b), "cudaEventElapsedTime");
+      ms[r.phase] += t;
+    }
+  }
+
+ private:
+  struct Rec {
+    int phase;
+    cudaEvent_t a, b;
+  };
+  cudaStream_t st_;
+  std::vector<Rec> recs_;
+};
+enum { PH_EXCH = 0, PH_ACE_BUILD, PH_ACE_APPLY, PH_H, PH_SUB, PH_SUBNN, PH_EIG, PH_ROT, PH_COMM, PH_AND, PH_LOEW };
+
 __global__ void k_maxabs_diff(const c128* __restrict__ A, const c128* __restrict__ B, int n, double* __restrict__ out) {
   double m = 0;
   for (int e = threadIdx.x; e < n; e += blockDim.x) {
@@ -59,38 +96,6 @@ __global__ void k_weighted_diag(const cx<T>* __restrict__ a, const cx<T>* __rest
     double r = 0;
     for (int w = 0; w < int(blockDim.x >> 5); ++w) r += sh[w];
     out[i] = r * dV * d[i];
-  }
-}
-
-// history Gram matrix: G[slot][a] = G[a][slot] = col[a]; rhs kept separately
-__global__ void k_gram_insert(double* __restrict__ G, int ld, const double* __restrict__ col, int slot, int m) {
-  const int a = threadIdx.x;
-  if (a < m) {
-    G[slot * ld + a] = col[a];
-    G[a * ld + slot] = col[a];
-  }
-}
-
-// pack the active m x m block (slots listed in order) into a dense matrix for the solver
-__global__ void k_gram_pack(const double* __restrict__ G, int ld, const int* __restrict__ slots, int m,
-                            double* __restrict__ P) {
-  const int e = threadIdx.x;
-  if (e < m * m) P[e] = G[slots[e / m] * ld + slots[e % m]];
-}
-
-// x <- x + beta r - sum_a gamma_a (dX_a + beta dR_a), over an orbital segment
-template <class T>
-__global__ void k_anderson_update(cx<T>* __restrict__ x, const cx<T>* __restrict__ r,
-                                  const cx<T>* const* __restrict__ dX, const cx<T>* const* __restrict__ dR,
-                                  const double* __restrict__ gamma, int m, double beta, size_t n) {
-  __shared__ T g[kMaxDepth];
-  if (threadIdx.x < m) g[threadIdx.x] = T(gamma[threadIdx.x]);
-  __syncthreads();
-  const T b = T(beta);
-  for (size_t e = size_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n; e += size_t(gridDim.x) * blockDim.x) {
-    cx<T> v = x[e] + r[e] * b;
-    for (int a = 0; a < m; ++a) v = v - (dX[a][e] + dR[a][e] * b) * g[a];
-    x[e] = v;
   }
 }
 
@@ -159,10 +164,9 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
   cx<T>* xi = F("ptim_xi");
   cx<T>* X = F("ptim_X");
   cx<T>* Hphi = F("ptim_Hphi");
-  cx<T>* rphi = F("ptim_rphi");
+  cx<T>* rphi_buf[2] = {F("ptim_rphi0"), F("ptim_rphi1")};  // residuals of consecutive iterations
   cx<T>* aphi = F("ptim_anchor_phi");
-  cx<T>* xprev = F("ptim_xprev_phi");
-  cx<T>* rprev = F("ptim_rprev_phi");
+  cx<T>* dxp_phi = F("ptim_dxpend_phi");
   c128* sign = Mx("ptim_sign");
   c128* sigh = Mx("ptim_sigh");
   c128* asig = Mx("ptim_anchor_sig");
@@ -175,35 +179,31 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
   c128* Li = Mx("ptim_Linv");
   c128* T1 = Mx("ptim_T1");
   c128* SinvA = Mx("ptim_SinvA");
-  c128* rsig = Mx("ptim_rsig");
-  c128* sprev = Mx("ptim_xprev_sig");
-  c128* rsprev = Mx("ptim_rprev_sig");
+  c128* rsig_buf[2] = {Mx("ptim_rsig0"), Mx("ptim_rsig1")};
+  c128* dxp_sig = Mx("ptim_dxpend_sig");
   double* d = static_cast<double*>(S.buf("ptim_d", N * sizeof(double)));
   double* dsc = static_cast<double*>(S.buf("ptim_dscratch", (2 * N + 64) * sizeof(double)));
   int* info = static_cast<int*>(S.buf("ptim_info", sizeof(int)));
-  // Anderson history rings
-  std::vector<cx<T>*> dXp(depth), dRp(depth);
-  std::vector<c128*> dXs(depth), dRs(depth);
+  // Anderson history ring: dR and Z = dX + beta dR per slot, for both segments
+  std::vector<cx<T>*> Zp(depth), dRp(depth);
+  std::vector<c128*> Zs(depth), dRs(depth);
   for (int a = 0; a < depth; ++a) {
     char nm[64];
-    snprintf(nm, sizeof(nm), "ptim_dX_phi_%d", a);
-    dXp[a] = F(nm);
+    snprintf(nm, sizeof(nm), "ptim_Z_phi_%d", a);
+    Zp[a] = F(nm);
     snprintf(nm, sizeof(nm), "ptim_dR_phi_%d", a);
     dRp[a] = F(nm);
-    snprintf(nm, sizeof(nm), "ptim_dX_sig_%d", a);
-    dXs[a] = Mx(nm);
+    snprintf(nm, sizeof(nm), "ptim_Z_sig_%d", a);
+    Zs[a] = Mx(nm);
     snprintf(nm, sizeof(nm), "ptim_dR_sig_%d", a);
     dRs[a] = Mx(nm);
   }
   double* Gd = static_cast<double*>(S.buf("ptim_G", kMaxDepth * kMaxDepth * sizeof(double)));
   double* Gp = static_cast<double*>(S.buf("ptim_Gpacked", kMaxDepth * kMaxDepth * sizeof(double)));
-  double* col = static_cast<double*>(S.buf("ptim_col", 2 * kMaxDepth * sizeof(double)));
+  double* dots = static_cast<double*>(S.buf("ptim_dots", (2 * kMaxDepth + 2) * sizeof(double)));
+  double* rhs = static_cast<double*>(S.buf("ptim_rhs", kMaxDepth * sizeof(double)));
   double* gamma = static_cast<double*>(S.buf("ptim_gamma", kMaxDepth * sizeof(double)));
-  int* slots_d = static_cast<int*>(S.buf("ptim_slots", kMaxDepth * sizeof(int)));
-  auto** dXp_d = static_cast<const cx<T>**>(S.buf("ptim_dXp_ptrs", kMaxDepth * sizeof(void*)));
-  auto** dRp_d = static_cast<const cx<T>**>(S.buf("ptim_dRp_ptrs", kMaxDepth * sizeof(void*)));
-  auto** dXs_d = static_cast<const c128**>(S.buf("ptim_dXs_ptrs", kMaxDepth * sizeof(void*)));
-  auto** dRs_d = static_cast<const c128**>(S.buf("ptim_dRs_ptrs", kMaxDepth * sizeof(void*)));
+  int* idx_d = static_cast<int*>(S.buf("ptim_idx", 2 * kMaxDepth * sizeof(int)));
 
   PT_CUDA_CHECK(cudaMemcpyAsync(phin, phi, fb, cudaMemcpyDeviceToDevice, st));
   PT_CUDA_CHECK(cudaMemcpyAsync(sign, sig, mb, cudaMemcpyDeviceToDevice, st));
@@ -212,6 +212,7 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
   pt_ptim_stats stv;
   std::memset(&stv, 0, sizeof(stv));
   stv.residual = NAN;
+  PhaseTimer tm(st);
   bool converged = false, inner_conv = false, have_anchor = false;
   const int nthreads = 256;
   const int sblocks = std::max(1, std::min<int>(ctx->num_sms * 8, int((S.n1 + nthreads - 1) / nthreads)));
@@ -230,8 +231,13 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
   } ev_guard{ev};
   // V_x[P_h] Phi_h through the sigma_h eigenbasis: (V_x phit) Q^*, phit = Phi_h Q
   auto exchange_on_midpoint = [&](cx<T>* out, bool energy) {
+    tm.begin(PH_EIG);
     heev(ctx, sigh, N, Q, d, st);
+    tm.end();
+    tm.begin(PH_ROT);
     rotate<T>(ctx, phih, Q, N, N, N, S.ng, c128{1, 0}, nullptr, 0, phit, st);
+    tm.end();
+    tm.begin(PH_EXCH);
     std::pair<cudaEvent_t, cudaEvent_t> e;
     PT_CUDA_CHECK(cudaEventCreate(&e.first));
     PT_CUDA_CHECK(cudaEventCreate(&e.second));
@@ -239,6 +245,7 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
     PT_CUDA_CHECK(cudaEventRecord(e.first, st));
     stv.pair_ffts += exchange(ctx, phit, d, N, nullptr, N, vphit, g, kern, prec, st);
     PT_CUDA_CHECK(cudaEventRecord(e.second, st));
+    tm.end();
     stv.exchange_calls++;
     if (energy) {
       PT_LAUNCH(k_weighted_diag<T>, N, 256, 0, st, phit, vphit, d, S.ng, S.dV, dsc);
@@ -249,8 +256,10 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
       for (double v : h) e += v;
       stv.exch_energy = P.spin * 0.5 * P.alpha * e;
     }
+    tm.begin(PH_ROT);
     conj_transpose(Q, N, QH, st);
     rotate<T>(ctx, vphit, QH, N, N, N, S.ng, c128{1, 0}, nullptr, 0, out, st);
+    tm.end();
   };
 
   const int max_outer = P.use_ace ? P.max_outer : 1;
@@ -271,36 +280,56 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
       have_anchor = true;
       stv.outer = outer + 1;
       exchange_on_midpoint(W, true);
+      tm.begin(PH_ACE_BUILD);
       ace_from_w(ctx, W, phih, N, g, prec, xi, st);
+      tm.end();
     } else {
       stv.outer = 1;
     }
     // ---- inner Anderson loop ----
     inner_conv = false;
-    int hist = 0, next_slot = 0;
-    bool have_prev = false;
-    std::vector<int> slot_order;
+    int next_slot = 0;
+    std::vector<int> order;  // active history slots, oldest first
     for (int inner = 0; inner < P.max_inner; ++inner) {
       stv.inner++;
+      cx<T>* rphi = rphi_buf[inner & 1];
+      c128* rsig = rsig_buf[inner & 1];
       S.midpoint(phih, sigh, phi, phin, sig, sign);
-      if (P.use_ace) ace_apply(ctx, xi, N, phih, N, X, g, prec, st);
-      else exchange_on_midpoint(X, inner == 0);
+      if (P.use_ace) {
+        tm.begin(PH_ACE_APPLY);
+        ace_apply(ctx, xi, N, phih, N, X, g, prec, st);
+        tm.end();
+      } else {
+        exchange_on_midpoint(X, inner == 0);
+      }
+      tm.begin(PH_H);
       apply_h(ctx, phih, N, Hphi, vloc, X, P.alpha, P.ecut, g, prec, st);
-      gram<T>(ctx, phih, Hphi, N, N, S.ng, S.dV, A, st);
-      gram<T>(ctx, phih, phih, N, N, S.ng, S.dV, Sm, st);
+      tm.end();
+      tm.begin(PH_SUB);
+      // A = <Phi_h|H Phi_h> and S = <Phi_h|Phi_h> are Hermitian: upper tiles only, mirrored
+      gram<T>(ctx, phih, Hphi, N, N, S.ng, S.dV, A, st, true);
+      gram<T>(ctx, phih, phih, N, N, S.ng, S.dV, Sm, st, true);
+      tm.end();
+      tm.begin(PH_SUBNN);
       // S^{-1} A = L^{-*} (L^{-1} A)
       cholesky(ctx, Sm, N, Lc, info, st);
       tri_inv_lower(Lc, N, Li, st);
       zgemm('N', 'N', N, N, N, c128{1, 0}, Li, N, A, N, c128{0, 0}, T1, N, st);
       zgemm('C', 'N', N, N, N, c128{1, 0}, Li, N, T1, N, c128{0, 0}, SinvA, N, st);
+      tm.end();
+      tm.begin(PH_SUB);
       // r_Phi = Phi_n - i dt (H Phi_h - Phi_h S^{-1}A) - Phi
       Term tr[3] = {{Hphi, c128{0, -P.dt}}, {phin, c128{1, 0}}, {phi, c128{-1, 0}}};
       rotate<T>(ctx, phih, SinvA, N, N, N, S.ng, c128{0, P.dt}, tr, 3, rphi, st);
+      tm.end();
+      tm.begin(PH_COMM);
       // r_sigma = sigma_n - i dt (A sigma_h - sigma_h A) - sigma
       zgemm('N', 'N', N, N, N, c128{1, 0}, A, N, sigh, N, c128{0, 0}, T1, N, st);
       zgemm('N', 'N', N, N, N, c128{-1, 0}, sigh, N, A, N, c128{1, 0}, T1, N, st);
       Term ts[3] = {{sign, c128{1, 0}}, {T1, c128{0, -P.dt}}, {sig, c128{-1, 0}}};
       lincomb<double>(ctx, rsig, S.n2, ts, 3, st);
+      tm.end();
+      tm.begin(PH_AND);
       int h_info = 0;
       PT_CUDA_CHECK(cudaMemcpyAsync(&h_info, info, sizeof(int), cudaMemcpyDeviceToHost, st));
       const double rr = S.norm2(rphi, rsig);  // synchronises st
@@ -310,97 +339,107 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
       stv.residual = res;
       if (!std::isfinite(res)) fail(PT_NONFINITE, "PT-IM residual is not finite");
       if (res < P.tol) {
+        tm.end();
         inner_conv = true;
         break;
       }
       // ---- Anderson (type II, real coefficients) ----
-      if (have_prev) {
+      int m = 0;
+      if (inner > 0) {
         const int slot = next_slot;
         next_slot = (next_slot + 1) % depth;
-        PT_LAUNCH(k_diff<T>, sblocks, nthreads, 0, st, dXp[slot], phi, xprev, S.n1);
-        PT_LAUNCH(k_diff<T>, sblocks, nthreads, 0, st, dRp[slot], rphi, rprev, S.n1);
-        PT_LAUNCH(k_diff<double>, sblocks2, nthreads, 0, st, dXs[slot], sig, sprev, S.n2);
-        PT_LAUNCH(k_diff<double>, sblocks2, nthreads, 0, st, dRs[slot], rsig, rsprev, S.n2);
-        slot_order.erase(std::remove(slot_order.begin(), slot_order.end(), slot), slot_order.end());
-        slot_order.push_back(slot);
-        hist = int(slot_order.size());
-        // new Gram column: <dR_a, dR_slot> for the active slots, in slot_order order
-        std::vector<const void*> u1(hist);
-        std::vector<const c128*> u2(hist);
-        for (int a = 0; a < hist; ++a) {
-          u1[a] = dRp[slot_order[a]];
-          u2[a] = dRs[slot_order[a]];
+        order.erase(std::remove(order.begin(), order.end(), slot), order.end());
+        const std::vector<int> others = order;
+        order.push_back(slot);
+        m = int(order.size());
+        const int mo = int(others.size());
+        AndersonSeg<T> a1{};
+        a1.rk = rphi;
+        a1.rprev = rphi_buf[(inner + 1) & 1];
+        a1.dxp = dxp_phi;
+        a1.dRs = dRp[slot];
+        a1.Zs = Zp[slot];
+        a1.n = S.n1;
+        AndersonSeg<double> a2{};
+        a2.rk = rsig;
+        a2.rprev = rsig_buf[(inner + 1) & 1];
+        a2.dxp = dxp_sig;
+        a2.dRs = dRs[slot];
+        a2.Zs = Zs[slot];
+        a2.n = S.n2;
+        for (int o = 0; o < mo; ++o) {
+          a1.dR[o] = dRp[others[o]];
+          a2.dR[o] = dRs[others[o]];
         }
-        multi_dot<T>(ctx, u1.data(), u2.data(), hist, dRp[slot], S.n1, dRs[slot], S.n2, S.dV, 1.0, col, st);
-        // scatter into G by slot index
-        std::vector<double> hcol(hist);
-        PT_CUDA_CHECK(cudaMemcpyAsync(hcol.data(), col, hist * sizeof(double), cudaMemcpyDeviceToHost, st));
-        PT_CUDA_CHECK(cudaStreamSynchronize(st));
-        std::vector<double> full(depth, 0.0);
-        for (int a = 0; a < hist; ++a) full[slot_order[a]] = hcol[a];
-        PT_CUDA_CHECK(cudaMemcpyAsync(col + kMaxDepth, full.data(), depth * sizeof(double), cudaMemcpyHostToDevice, st));
-        PT_LAUNCH(k_gram_insert, 1, 32, 0, st, Gd, kMaxDepth, col + kMaxDepth, slot, depth);
+        anderson_prepare<T>(ctx, a1, a2, mo, P.anderson_beta, S.dV, dots, st);
+        int hidx[2 * kMaxDepth];
+        for (int o = 0; o < mo; ++o) hidx[o] = others[o];
+        for (int p = 0; p < m; ++p) hidx[kMaxDepth + p] = order[p];
+        PT_CUDA_CHECK(cudaMemcpyAsync(idx_d, hidx, sizeof(hidx), cudaMemcpyHostToDevice, st));
+        anderson_gram(Gd, dots, slot, idx_d, mo, idx_d + kMaxDepth, m, Gp, rhs, st);
+        small_solve(Gp, rhs, m, 1e-14, gamma, st);
       }
-      PT_CUDA_CHECK(cudaMemcpyAsync(xprev, phi, fb, cudaMemcpyDeviceToDevice, st));
-      PT_CUDA_CHECK(cudaMemcpyAsync(rprev, rphi, fb, cudaMemcpyDeviceToDevice, st));
-      PT_CUDA_CHECK(cudaMemcpyAsync(sprev, sig, mb, cudaMemcpyDeviceToDevice, st));
-      PT_CUDA_CHECK(cudaMemcpyAsync(rsprev, rsig, mb, cudaMemcpyDeviceToDevice, st));
-      have_prev = true;
-      int m = hist;
-      if (m > 0) {
-        std::vector<const void*> u1(m);
-        std::vector<const c128*> u2(m);
-        std::vector<const cx<T>*> px(m), pr(m);
-        std::vector<const c128*> sx(m), sr(m);
-        for (int a = 0; a < m; ++a) {
-          const int s = slot_order[a];
-          u1[a] = dRp[s];
-          u2[a] = dRs[s];
-          px[a] = dXp[s];
-          pr[a] = dRp[s];
-          sx[a] = dXs[s];
-          sr[a] = dRs[s];
-        }
-        // rhs_a = <dR_a, r>
-        multi_dot<T>(ctx, u1.data(), u2.data(), m, rphi, S.n1, rsig, S.n2, S.dV, 1.0, col, st);
-        PT_CUDA_CHECK(cudaMemcpyAsync(slots_d, slot_order.data(), m * sizeof(int), cudaMemcpyHostToDevice, st));
-        PT_LAUNCH(k_gram_pack, 1, kMaxDepth * kMaxDepth, 0, st, Gd, kMaxDepth, slots_d, m, Gp);
-        small_solve(Gp, col, m, 1e-14, gamma, st);
-        PT_CUDA_CHECK(cudaMemcpyAsync(dXp_d, px.data(), m * sizeof(void*), cudaMemcpyHostToDevice, st));
-        PT_CUDA_CHECK(cudaMemcpyAsync(dRp_d, pr.data(), m * sizeof(void*), cudaMemcpyHostToDevice, st));
-        PT_CUDA_CHECK(cudaMemcpyAsync(dXs_d, sx.data(), m * sizeof(void*), cudaMemcpyHostToDevice, st));
-        PT_CUDA_CHECK(cudaMemcpyAsync(dRs_d, sr.data(), m * sizeof(void*), cudaMemcpyHostToDevice, st));
-        // the host vectors above must outlive the async copies
-        PT_CUDA_CHECK(cudaStreamSynchronize(st));
+      std::vector<const cx<T>*> zp(m);
+      std::vector<const c128*> zs(m);
+      for (int p = 0; p < m; ++p) {
+        zp[p] = Zp[order[p]];
+        zs[p] = Zs[order[p]];
       }
-      PT_LAUNCH(k_anderson_update<T>, sblocks, nthreads, 0, st, phi, rphi, dXp_d, dRp_d, gamma, m, P.anderson_beta,
-                S.n1);
-      PT_LAUNCH(k_anderson_update<double>, sblocks2, nthreads, 0, st, sig, rsig, dXs_d, dRs_d, gamma, m,
-                P.anderson_beta, S.n2);
+      anderson_update<T>(ctx, phi, rphi, zp.data(), m, gamma, P.anderson_beta, dxp_phi, S.n1, st);
+      anderson_update<double>(ctx, sig, rsig, zs.data(), m, gamma, P.anderson_beta, dxp_sig, S.n2, st);
+      tm.end();
     }
     if (!P.use_ace && inner_conv) converged = true;
   }
   // ---- final orthonormalisation and conjugate symmetrisation ----
+  tm.begin(PH_LOEW);
   gram<T>(ctx, phi, phi, N, N, S.ng, S.dV, Sm, st);
   PT_LAUNCH(k_maxabs_diff, 1, 1024, 0, st, Sm, Sn, int(S.n2), dsc);
-  heev(ctx, Sm, N, Q, d, st);
-  PT_CUDA_CHECK(cudaMemcpyAsync(&stv.orth_error, dsc, sizeof(double), cudaMemcpyDeviceToHost, st));
+  set_identity(T1, N, st);
+  PT_LAUNCH(k_maxabs_diff, 1, 1024, 0, st, Sm, T1, int(S.n2), dsc + 1);
+  double devs[2] = {0, 0};
+  PT_CUDA_CHECK(cudaMemcpyAsync(devs, dsc, sizeof(devs), cudaMemcpyDeviceToHost, st));
+  PT_CUDA_CHECK(cudaStreamSynchronize(st));
+  stv.orth_error = devs[0];
   PT_CUDA_CHECK(cudaMemsetAsync(info, 0, sizeof(int), st));
-  scale_cols_pow(Q, d, N, -0.5, T1, info, st);
-  zgemm('N', 'C', N, N, N, c128{1, 0}, T1, N, Q, N, c128{0, 0}, A, N, st);   // S^{-1/2}
-  scale_cols_pow(Q, d, N, 0.5, T1, info, st);
-  zgemm('N', 'C', N, N, N, c128{1, 0}, T1, N, Q, N, c128{0, 0}, Lc, N, st);  // S^{1/2}
-  rotate<T>(ctx, phi, A, N, N, N, S.ng, c128{1, 0}, nullptr, 0, rphi, st);
-  PT_CUDA_CHECK(cudaMemcpyAsync(phi, rphi, fb, cudaMemcpyDeviceToDevice, st));
+  const double sdev = devs[1];  // max |S - I|
+  if (sdev < 0.05) {
+    // S close to I: coupled Newton-Schulz  T = (3I - Z Y)/2, Y <- Y T, Z <- T Z,  Y -> S^{1/2}, Z -> S^{-1/2}
+    c128* Y = Lc;   // S^{1/2}
+    c128* Z = A;    // S^{-1/2}
+    PT_CUDA_CHECK(cudaMemcpyAsync(Y, Sm, mb, cudaMemcpyDeviceToDevice, st));
+    set_identity(Z, N, st);
+    const int iters = sdev < 1e-6 ? 3 : (sdev < 1e-3 ? 4 : 6);
+    for (int it = 0; it < iters; ++it) {
+      zgemm('N', 'N', N, N, N, c128{-0.5, 0}, Z, N, Y, N, c128{0, 0}, T1, N, st);
+      add_diagonal(T1, N, 1.5, st);  // T = 1.5 I - 0.5 Z Y
+      zgemm('N', 'N', N, N, N, c128{1, 0}, Y, N, T1, N, c128{0, 0}, SinvA, N, st);
+      std::swap(Y, SinvA);
+      zgemm('N', 'N', N, N, N, c128{1, 0}, T1, N, Z, N, c128{0, 0}, SinvA, N, st);
+      std::swap(Z, SinvA);
+    }
+    if (Z != A) PT_CUDA_CHECK(cudaMemcpyAsync(A, Z, mb, cudaMemcpyDeviceToDevice, st));
+    if (Y != Lc) PT_CUDA_CHECK(cudaMemcpyAsync(Lc, Y, mb, cudaMemcpyDeviceToDevice, st));
+  } else {
+    heev(ctx, Sm, N, Q, d, st);
+    scale_cols_pow(Q, d, N, -0.5, T1, info, st);
+    zgemm('N', 'C', N, N, N, c128{1, 0}, T1, N, Q, N, c128{0, 0}, A, N, st);   // S^{-1/2}
+    scale_cols_pow(Q, d, N, 0.5, T1, info, st);
+    zgemm('N', 'C', N, N, N, c128{1, 0}, T1, N, Q, N, c128{0, 0}, Lc, N, st);  // S^{1/2}
+  }
+  rotate<T>(ctx, phi, A, N, N, N, S.ng, c128{1, 0}, nullptr, 0, rphi_buf[0], st);
+  PT_CUDA_CHECK(cudaMemcpyAsync(phi, rphi_buf[0], fb, cudaMemcpyDeviceToDevice, st));
   zgemm('N', 'N', N, N, N, c128{1, 0}, Lc, N, sig, N, c128{0, 0}, T1, N, st);
   zgemm('N', 'N', N, N, N, c128{1, 0}, T1, N, Lc, N, c128{0, 0}, sig, N, st);
   conj_transpose(sig, N, T1, st);
   Term th[2] = {{sig, c128{0.5, 0}}, {T1, c128{0.5, 0}}};
   lincomb<double>(ctx, sig, S.n2, th, 2, st);
+  tm.end();
   int h_info = 0;
   PT_CUDA_CHECK(cudaMemcpyAsync(&h_info, info, sizeof(int), cudaMemcpyDeviceToHost, st));
   PT_CUDA_CHECK(cudaStreamSynchronize(st));
   if (h_info) fail(PT_NOT_PD, "PT-IM: final overlap matrix is not positive definite");
+  tm.sum(stv.phase_ms);
   for (auto& e : ev) {
     float ms = 0.f;
     PT_CUDA_CHECK(cudaEventElapsedTime(&ms, e.first, e.second));

@@ -300,3 +300,19 @@ def test_exchange_64cubed_specialised_path(ctx, precision, sym):
     finally:
         ctx.set_option("scratch_bytes", 48 << 20)
     assert rel(out.cpu().numpy().astype(np.complex128), ref) <= (FP64_TOL if precision == "fp64" else FP32_TOL)
+
+
+def test_ptim_step_fp32_multitile_N66(ctx):
+    """N = 66 spans two 64-wide Gram tiles (Hermitian mirror of A and S) and several exchange batches."""
+    w = synth.small_cell(29, 10, 9.0, 66, kT=0.05, ecut=12.0)
+    g = O.grid_of(w.cell)
+    K = O.exchange_kernel(g, 1, synth.SCREENED_MU)
+    phi1, sig1, st = O.ptim_step(w.phi, w.sigma, w.vloc, g, K, O.PtimParams(tol=1e-9, ecut=12.0))
+    assert st.converged
+    phi = dev(w.phi.astype(np.complex64))
+    sigma = dev(w.sigma)
+    s = ctx.ptim_step(phi, sigma, dev(w.vloc), cell=w.cell, kernel=w.kernel, precision="fp32", dt=0.5,
+                      ecut=12.0, tol=2e-6)
+    assert s["converged"]
+    assert rel(phi.cpu().numpy().astype(np.complex128), phi1) <= 5e-5
+    assert np.abs(sigma.cpu().numpy() - sig1).max() <= 5e-5
