@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 form comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    ap.add_argument("--mode", default="step", choices=["step", "exchange"],
+                    help="step: PT-IM steps (the benchmark); exchange: only V_x applications on the same cell "
+                         "(profiler captures of the exchange kernel)")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -177,6 +180,36 @@ def read_peaks():
         return float(p["hbm_gbs"]), "measured"
     except Exception:  # noqa: BLE001
         return 6800.0, "fallback"
+
+
+def run_exchange_only(args):
+    """V_x applications on the 64^3 cell with N orbitals (symmetric pairs), timed with CUDA events."""
+    import numpy as np
+    import torch
+
+    from paper_2501_03061_gb300 import api, synth
+
+    w = synth.ptim_cell128(N=args.N)
+    cdt = np.complex64 if args.precision == "fp32" else np.complex128
+    ctx = api.Context(0)
+    phi = torch.from_numpy(w.phi.astype(cdt)).cuda()
+    occ = torch.from_numpy(w.occ).cuda()
+    out = torch.empty_like(phi)
+    kw = dict(cell=w.cell, kernel=w.kernel, precision=args.precision)
+    for _ in range(args.warmup):
+        ctx.apply_exchange(phi, occ, out=out, **kw)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        ctx.apply_exchange(phi, occ, out=out, **kw)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / args.steps
+    pairs = args.N * (args.N + 1) // 2
+    print(json.dumps({"mode": "exchange", "N": args.N, "precision": args.precision, "ms_per_application": ms,
+                      "pair_ffts_per_s": pairs / (ms / 1e3)}), flush=True)
+    ctx.close()
 
 
 def run_gb300(args):
@@ -379,6 +412,8 @@ def main():
         return
     if args.impl == "reference":
         run_reference(args)
+    elif args.mode == "exchange":
+        run_exchange_only(args)
     else:
         run_gb300(args)
 
