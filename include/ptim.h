@@ -110,6 +110,21 @@ pt_status pt_apply_exchange(pt_ctx* ctx, const void* src, const double* occ, int
                             const pt_grid* grid, const pt_kernel* kernel,
                             pt_precision prec, void* stream);
 
+/* Allocation-free variant of pt_apply_exchange (no counterpart in the paper: it exists for
+ * callers that cannot allocate device memory while they run — an application whose own pool
+ * allocator owns the whole device memory, or a latency-critical loop that cannot afford the
+ * device synchronisation of cudaMalloc/cudaFree).  Same arguments and result as
+ * pt_apply_exchange, but no context: every buffer beyond the caller's inputs and outputs lives
+ * in static device arrays of this library (32 MiB pair scratch, a 64^3 kernel table, small
+ * schedule tables) that every GPU loading the library holds until the process exits.  Limits:
+ * N, M <= 1024 and grids of at most 64^3 points (the regular grid rules apply); larger requests
+ * return PT_INVALID_ARG.  The first call on a device (with that device current) looks up the
+ * device addresses of those arrays; make it before any stream capture.  All calls share the
+ * arrays: calls that overlap on the GPU (other streams or host threads) race.  Uses the generic
+ * (non-TMA) exchange kernels.  Other status codes as pt_apply_exchange. */
+pt_status pt_apply_exchange_noalloc(const void* src, const double* occ, int N, const void* tgt, int M, void* out,
+                                    const pt_grid* grid, const pt_kernel* kernel, pt_precision prec, void* stream);
+
 /* ---- adaptively compressed exchange (Sec. IV-A2, Eq. vx_ace; Lin's construction) -------- */
 
 /* Build the ACE operator of V_x[P] on span(phi), P = sum_i occ_i phi_i phi_i^*:

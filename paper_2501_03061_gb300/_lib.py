@@ -46,6 +46,7 @@ PROTOTYPES = {
     "pt_trim": (i32, [vp]),
     "pt_set_option": (i32, [vp, C.c_char_p, C.c_double]),
     "pt_apply_exchange": (i32, [vp, vp, vp, i32, vp, i32, vp, C.POINTER(pt_grid), C.POINTER(pt_kernel), i32, vp]),
+    "pt_apply_exchange_noalloc": (i32, [vp, vp, i32, vp, i32, vp, C.POINTER(pt_grid), C.POINTER(pt_kernel), i32, vp]),
     "pt_build_ace": (i32, [vp, vp, vp, i32, C.POINTER(pt_grid), C.POINTER(pt_kernel), i32, C.POINTER(vp), vp]),
     "pt_build_ace_from": (i32, [vp, vp, vp, i32, C.POINTER(pt_grid), i32, C.POINTER(vp), vp]),
     "pt_apply_ace": (i32, [vp, vp, vp, i32, vp, vp]),

@@ -309,6 +309,24 @@ long long exchange_t(pt_ctx* ctx, const cx<T>* src, const double* occ, int N, co
 
 }  // namespace
 
+template <class T>
+void exchange_batch_generic(const GridPlan& gp, const cx<T>* src, const cx<T>* tgt, const double* occ,
+                            const PairDesc* pairs, int np, const TargetDesc* tgts, int nt, const Contrib* contribs,
+                            const T* ktab, const cx<T>* tw, cx<T>* scratch, cx<T>* out, cudaStream_t st) {
+  set_smem_attrs<T>();
+  const size_t smem = tile_smem_bytes(sizeof(cx<T>));
+  PT_LAUNCH(k_pair_fwd_plane<T>, dim3(gp.nz, np), NT, smem, st, gp, src, tgt, occ, pairs, scratch, tw);
+  PT_LAUNCH(k_pair_column<T>, dim3(gp.ny, np), NT, smem, st, gp, scratch, ktab, occ, pairs, tw);
+  PT_LAUNCH(k_pair_inv_acc<T>, dim3(gp.nz, nt), NT, smem, st, gp, scratch, src, occ, tgts, contribs, out, tw);
+}
+
+template void exchange_batch_generic<float>(const GridPlan&, const c64*, const c64*, const double*, const PairDesc*,
+                                            int, const TargetDesc*, int, const Contrib*, const float*, const c64*,
+                                            c64*, c64*, cudaStream_t);
+template void exchange_batch_generic<double>(const GridPlan&, const c128*, const c128*, const double*,
+                                             const PairDesc*, int, const TargetDesc*, int, const Contrib*,
+                                             const double*, const c128*, c128*, c128*, cudaStream_t);
+
 size_t exchange_scratch_budget(const pt_ctx* ctx) { return ctx->scratch_budget; }
 
 void exchange_check(pt_ctx* ctx, cudaStream_t st) {

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "fft.cuh"
 
 namespace pt {
 
@@ -46,6 +47,13 @@ struct ScheduleImpl {
 
 // tiles of B x B orbitals; symmetric: I <= J tiles with i <= j inside diagonal tiles
 std::shared_ptr<ScheduleImpl> build_schedule(int N, int M, bool sym, int B);
+
+// the three generic tile passes for one pair batch on caller-provided device buffers
+template <class T>
+void exchange_batch_generic(const GridPlan& gp, const cx<T>* src, const cx<T>* tgt, const double* occ,
+                            const PairDesc* pairs, int np, const TargetDesc* tgts, int nt, const Contrib* contribs,
+                            const T* ktab, const cx<T>* tw, cx<T>* scratch, cx<T>* out, cudaStream_t st);
+double kernel_value(const pt_kernel& k, double G2);
 
 bool exchange64_applies(const pt_grid& g);
 // FP32 64^3 path with TMA staging; sets a device error word on a wait timeout (see exchange_check)
