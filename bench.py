@@ -48,9 +48,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 form comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
-    ap.add_argument("--mode", default="step", choices=["step", "exchange"],
+    ap.add_argument("--mode", default="step", choices=["step", "exchange", "serve"],
                     help="step: PT-IM steps (the benchmark); exchange: only V_x applications on the same cell "
                          "(profiler captures of the exchange kernel)")
+    ap.add_argument("--serve-window", type=float, default=15.0, help="seconds of arrivals per serving phase")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement in step mode")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -212,6 +214,120 @@ def run_exchange_only(args):
     ctx.close()
 
 
+def serve_measurement(window_s: float, slots: int = 6) -> dict:
+    """Serving form: Poisson stream of PT-IM step requests (N in 32..320, grids 32^3..64^3, FP32).
+
+    Systems are cut from one generated template per grid size (the first N orbitals of an
+    orthonormal set stay orthonormal; occupations are redrawn for N).  Phase 1 measures the
+    saturation throughput with a burst; phase 2 replays the 200 req/s stream for `window_s`
+    seconds of arrivals; phase 3 replays arrivals at 75% of the saturation rate.  Queued
+    requests still waiting when a window closes are counted as backlog, not run.
+    """
+    import numpy as np
+
+    from paper_2501_03061_gb300 import serve, synth
+
+    templates = {}
+    for n in synth.SERVE_GRID_SIZES:
+        w = synth.small_cell(2000 + n, n, 0.32 * n, 320, kT=0.02, natoms=8)
+        templates[n] = w
+
+    def make(spec, precision="fp32"):
+        w = templates[spec["n"]]
+        N = spec["N"]
+        f = synth.fermi_dirac_occupations(N, 0.02)
+        return serve.Request(phi=w.phi[:N], sigma=np.diag(f).astype(np.complex128), occ=None, vloc=w.vloc,
+                             cell=w.cell, kernel=w.kernel, kind="ptim", precision=precision,
+                             params={"tol": 1e-6, "anderson_depth": 20})
+
+    stream = synth.serving_stream()
+    srv = serve.Server(slots=slots)
+    out = {"slots": slots, "budget_gb": srv.budget / 1e9}
+    try:
+        # warm every slot (first-use allocations and tables), then phase 1: saturation from a burst
+        warm = [srv.submit(make({"n": 64, "N": 320})) for _ in range(slots)]
+        for f in warm:
+            f.result()
+        burst = [make(s) for s in stream[:2 * slots]]
+        t0 = time.perf_counter()
+        futs = [srv.submit(r) for r in burst]
+        done = [f.result() for f in futs]
+        t_burst = time.perf_counter() - t0
+        sat = len(done) / t_burst
+        out["saturation_req_per_s"] = sat
+
+        def replay(rate, tag):
+            srv.completed.clear()
+            gaps = np.random.default_rng(1005).exponential(1.0 / rate, size=100000)
+            t_start = time.perf_counter()
+            futs, k, t = [], 0, 0.0
+            while True:
+                t += gaps[k]
+                if t > window_s:
+                    break
+                now = time.perf_counter() - t_start
+                if t > now:
+                    time.sleep(t - now)
+                r = make(stream[(2 * slots + k) % len(stream)])
+                r.t_arrival = t_start + t
+                futs.append(srv.submit(r))
+                k += 1
+            backlog = 0
+            with srv.cv:
+                backlog = len(srv.queue)
+                srv.queue.clear()
+            for f in futs:
+                if f.done():
+                    continue
+            while any(w.busy for w in srv.workers):
+                time.sleep(0.05)
+            fin = [r for r in srv.completed if r.error is None]
+            summ = serve.latency_summary(fin)
+            summ.update({"offered_req_per_s": rate, "arrivals": k, "completed": len(fin), "backlog": backlog,
+                         "throughput_req_per_s": len(fin) / max(1e-9, time.perf_counter() - t_start)})
+            out[tag] = summ
+
+        replay(200.0, "at_200_req_per_s")
+        window_s = max(window_s, 40.0)
+        replay(0.75 * sat, "at_75pct_saturation")
+    finally:
+        srv.close()
+    return out
+
+
+def batched_measurement(slots: int = 8) -> dict:
+    """Batched form: 64 independent V_x applications (N ~ U{16..256}, grids 24^3..64^3, FP32)
+    submitted together and run concurrently over the serving slots; pair-FFTs/s of the batch."""
+    import numpy as np
+
+    from paper_2501_03061_gb300 import serve, synth
+
+    specs = synth.batched_instances()
+    templates = {}
+    for n in sorted({s["n"] for s in specs}):
+        templates[n] = synth.small_cell(3000 + n, n, 0.32 * n, 256, kT=0.02, natoms=8)
+    reqs = []
+    pairs = 0
+    for sp in specs:
+        w = templates[sp["n"]]
+        N = sp["N"]
+        reqs.append(serve.Request(phi=w.phi[:N], sigma=None, occ=synth.fermi_dirac_occupations(N, 0.02), vloc=None,
+                                  cell=w.cell, kernel=w.kernel, kind="exchange", precision="fp32"))
+        pairs += N * (N + 1) // 2
+    srv = serve.Server(slots=slots)
+    try:
+        for f in [srv.submit(r) for r in reqs[:slots]]:  # warm-up pass over the slots
+            f.result()
+        t0 = time.perf_counter()
+        done = [f.result() for f in [srv.submit(r) for r in reqs]]
+        dt = time.perf_counter() - t0
+    finally:
+        srv.close()
+    errs = [r.error for r in done if r.error]
+    return {"instances": len(reqs), "pair_ffts": pairs, "seconds": dt, "pair_ffts_per_s": pairs / dt,
+            "slots": slots, "errors": errs[:3], "note": "wall clock incl. host<->device copies of each instance"}
+
+
 def run_gb300(args):
     import numpy as np
     import torch
@@ -341,6 +457,18 @@ def run_gb300(args):
                 "exchange_speedup_fp32_vs_fp64": t64 / t32}
         del pd, p32
 
+    serve_res = None
+    if rank == 0 and world == 1 and not args.no_serve:
+        try:
+            ctx.trim()
+            serve_res = serve_measurement(args.serve_window)
+        except Exception as e:  # noqa: BLE001
+            serve_res = {"error": str(e)[:300]}
+        try:
+            serve_res["batched"] = batched_measurement()
+        except Exception as e:  # noqa: BLE001
+            serve_res["batched"] = {"error": str(e)[:300]}
+
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -368,6 +496,7 @@ def run_gb300(args):
             "gpu_launches": launches,
             "clocks": clocks,
             "plain_fp64_form": fp64,
+            "serve": serve_res,
         }
         if cpu is not None and "t_step_s" in cpu:
             out["cpu_baseline"] = {"value": 1.0 / cpu["t_step_s"], "unit": UNIT, "cores": cpu["cores"],
@@ -414,6 +543,12 @@ def main():
         run_reference(args)
     elif args.mode == "exchange":
         run_exchange_only(args)
+    elif args.mode == "serve":
+        import torch
+        torch.cuda.set_device(0)
+        res = serve_measurement(args.serve_window)
+        res["batched"] = batched_measurement()
+        print(json.dumps({"mode": "serve", "serve": res}), flush=True)
     else:
         run_gb300(args)
 

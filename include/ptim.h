@@ -202,6 +202,12 @@ pt_status pt_ptim_step(pt_ctx* ctx, void* phi, void* sigma, int N, const double*
                        const pt_grid* grid, const pt_kernel* kernel, const pt_ptim_params* params,
                        pt_precision prec, pt_ptim_stats* stats, void* stream);
 
+/* Upper bound of the device workspace (bytes) that pt_ptim_step with these sizes makes a fresh
+ * context allocate: the orbital blocks of the step, the Anderson ring of `anderson_depth`
+ * entries, FFT/exchange scratch at the context's default batch size, and the N x N matrices.
+ * Used by a serving loop to admit requests by HBM footprint.  Pure host arithmetic. */
+size_t pt_ptim_footprint(int N, const pt_grid* grid, pt_precision prec, int anderson_depth);
+
 /* ---- small helpers used by the binding and tests ------------------------------------------ */
 
 /* Library version string and the GPU architecture it was compiled for. */

@@ -56,6 +56,7 @@ PROTOTYPES = {
     "pt_diag_occupations": (i32, [vp, vp, i32, vp, vp, vp]),
     "pt_ptim_step": (i32, [vp, vp, vp, i32, vp, C.POINTER(pt_grid), C.POINTER(pt_kernel),
                            C.POINTER(pt_ptim_params), i32, C.POINTER(pt_ptim_stats), vp]),
+    "pt_ptim_footprint": (C.c_size_t, [i32, C.POINTER(pt_grid), i32, i32]),
     "pt_version": (C.c_char_p, []),
     "pt_kernel_launches": (C.c_longlong, []),
 }

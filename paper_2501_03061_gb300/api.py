@@ -212,5 +212,11 @@ class Context:
                 "phase_ms": {n: float(s.phase_ms[i]) for i, n in enumerate(L.PHASES)}}
 
 
+def ptim_footprint(N: int, cell, precision: str = "fp32", anderson_depth: int = 20) -> int:
+    """Upper bound of the device bytes one PT-IM step of this size makes a fresh context allocate."""
+    g = _grid(cell)
+    return int(L.load().pt_ptim_footprint(int(N), C.byref(g), L.PRECISIONS[precision], int(anderson_depth)))
+
+
 def kernel_launches() -> int:
     return int(L.load().pt_kernel_launches())

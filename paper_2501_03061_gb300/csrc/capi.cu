@@ -303,6 +303,27 @@ pt_status pt_ptim_step(pt_ctx* ctx, void* phi, void* sigma, int N, const double*
   });
 }
 
+size_t pt_ptim_footprint(int N, const pt_grid* grid, pt_precision prec, int anderson_depth) {
+  if (!grid || N <= 0) return 0;
+  const size_t ng = pt::ng_of(*grid);
+  const size_t es = pt::elem_bytes(prec);
+  const size_t field = ng * es;
+  const size_t block = field * size_t(N);
+  const int depth = anderson_depth < 1 ? 1 : (anderson_depth > 20 ? 20 : anderson_depth);
+  const size_t budget = size_t(48) << 20;  // default scratch_bytes of a context
+  size_t B = size_t(std::floor(std::sqrt(double(std::max<size_t>(1, budget / field)))));
+  B = std::max<size_t>(1, std::min<size_t>(B, size_t(N)));
+  const bool tma64 = grid->nx == 64 && grid->ny == 64 && grid->nz == 64;
+  if (tma64 && prec != PT_FP64) B = std::min<size_t>(B, 6);
+  const size_t exch = (tma64 ? 4 : 1) * B * B * field;
+  const size_t hscr = 2 * std::max<size_t>(1, std::min<size_t>(size_t(N), budget / (2 * field))) * field;
+  const size_t nn = size_t(N) * N * sizeof(double) * 2;
+  const size_t gram_parts = size_t(4 * 160 + 64) * nn;  // split partials, bounded by 4 waves of tiles
+  const size_t blocks = (12 + 2 * size_t(depth)) * block;
+  const size_t small = 40 * nn + (size_t(64) << 20);
+  return blocks + exch + hscr + std::min(gram_parts, size_t(8) * block) + small;
+}
+
 const char* pt_version(void) { return "ptim-gb300 0.1 (sm_103a)"; }
 
 long long pt_kernel_launches(void) { return pt::g_launches.load(); }
