@@ -92,7 +92,12 @@ size_t pt_workspace_bytes(const pt_ctx* ctx);
 pt_status pt_trim(pt_ctx* ctx);
 /* Set a tuning option of the context.  Keys:
  *   "scratch_bytes"  bytes of pair/orbital fields one FFT batch may hold (default 48 MiB, sized
- *                    to stay resident in L2; smaller values give more, smaller batches). */
+ *                    to stay resident in L2; smaller values give more, smaller batches).
+ *   "tc_gram"        1: in the PT_FP32 form, run the Gram contractions (A^H B over the grid) on
+ *                    the tensor cores with a 3-product TF32 split (hi*hi + hi*lo + lo*hi) that
+ *                    keeps FP32-level accuracy; 0 (default): CUDA cores.
+ *   "tc_period"      K stages of 32 floats the tensor-core Gram accumulates in TMEM between
+ *                    readouts into compensated registers (1..64, default 2). */
 pt_status pt_set_option(pt_ctx* ctx, const char* key, double value);
 
 /* ---- Fock exchange (Sec. IV-A1, Eq. vxdiag; Alg. 2 with sigma diagonalised) ------------ */
@@ -145,6 +150,19 @@ pt_status pt_apply_ace(pt_ctx* ctx, const pt_ace* ace, const void* psi, int M, v
 /* Copy xi (Ng x N, the ACE's precision) into a caller buffer. */
 pt_status pt_ace_get_xi(const pt_ace* ace, void* xi_out, void* stream);
 void pt_ace_destroy(pt_ace* ace);
+
+/* ---- overlaps (the Gram contractions of ACE's M = <phi|W> and of PT-IM's S = <phi|phi>) -- */
+
+/* C[i][j] = dV * sum_r conj(A_i(r)) B_j(r), i < N1, j < N2: the dV-weighted inner products
+ * of two orbital blocks, e.g. M = Phi^* W of the ACE construction (Sec. IV-A2) or the overlap
+ * S of the Loewdin orthonormalisation.  A: Ng x N1 and B: Ng x N2 orbitals (device, orbital-
+ * major, precision prec); C: N1 x N2 complex128 (device, row-major).  In PT_FP32 the
+ * contraction runs on CUDA cores with compensated sums unless the "tc_gram" option selects the
+ * 3-product TF32 tensor-core form; PT_FP32_TC_TF32 runs one TF32 product (about 1e-3 relative
+ * error per term, for error studies).  Asynchronous on `stream`, except that the tensor-core
+ * forms synchronise once to read the kernel's error word (PT_TIMEOUT if a bounded wait expired). */
+pt_status pt_overlap(pt_ctx* ctx, const void* A, int N1, const void* B, int N2, const pt_grid* grid,
+                     pt_precision prec, void* C, void* stream);
 
 /* ---- Hamiltonian (Eq. 1 with frozen V_Hxc + V_ext) -------------------------------------- */
 

@@ -164,6 +164,20 @@ class Context:
         self._check(st, "pt_apply_ace")
         return out
 
+    # ---- overlaps ---------------------------------------------------------------------------
+    def overlap(self, A, B=None, *, cell, precision="fp64", out=None, stream=None):
+        """C[i][j] = dV <A_i|B_j> as an (N1, N2) complex128 device tensor (B None: B = A)."""
+        self._orb(A, precision, "A")
+        B = A if B is None else B
+        self._orb(B, precision, "B")
+        if out is None:
+            out = torch.empty((A.shape[0], B.shape[0]), dtype=torch.complex128, device=self.device)
+        g = _grid(cell)
+        st = self.lib.pt_overlap(self.h, _ptr(A), A.shape[0], _ptr(B), B.shape[0], C.byref(g),
+                                 L.PRECISIONS[precision], _ptr(out), _stream(stream))
+        self._check(st, "pt_overlap")
+        return out
+
     # ---- Hamiltonian ------------------------------------------------------------------------
     def apply_H(self, psi, vloc, ace: Ace | None = None, alpha=0.25, ecut=10.0, *, cell, precision="fp64",
                 out=None, stream=None):

@@ -366,6 +366,12 @@ int stream_blocks(pt_ctx* ctx, size_t n, int threads) {
 template <class T>
 void gram(pt_ctx* ctx, const cx<T>* A, const cx<T>* B, int N1, int N2, size_t ng, double scale, c128* C,
           cudaStream_t st, bool herm) {
+  if constexpr (sizeof(T) == 4) {
+    if (ctx->active_tc && gram_tc_applies(A, B, ng)) {
+      gram_tc(ctx, A, B, N1, N2, ng, scale, C, st, herm, ctx->active_tc == 1);
+      return;
+    }
+  }
   const bool f32 = sizeof(T) == 4;
   const int tile = f32 ? G4T : GT;
   const int kstep = f32 ? G4K : GK;

@@ -51,6 +51,7 @@ void pt_ctx::release_all() {
   for (auto& kv : bufs) cudaFree(kv.second.ptr);
   bufs.clear();
   held = 0;
+  tc_err_clean = false;
 }
 
 namespace {
@@ -71,6 +72,12 @@ pt_status guarded(pt_ctx* ctx, F&& f) {
 }
 
 void set_device(pt_ctx* ctx) { pt::check_cuda(cudaSetDevice(ctx->device), "cudaSetDevice"); }
+
+// contraction engine for this call: TF32 form on single-product tensor cores, FP32 form on
+// 3xTF32 tensor cores when the context option asks for it, CUDA cores otherwise
+void set_engine(pt_ctx* ctx, pt_precision prec) {
+  ctx->active_tc = (prec == PT_FP32_TC_TF32) ? 2 : ((prec == PT_FP32 && ctx->tc_gram) ? 1 : 0);
+}
 
 void check_common(pt_ctx* ctx, const pt_grid* grid, pt_precision prec) {
   if (!ctx) pt::fail(PT_INVALID_ARG, "context is NULL");
@@ -140,6 +147,15 @@ pt_status pt_trim(pt_ctx* ctx) {
 pt_status pt_set_option(pt_ctx* ctx, const char* key, double value) {
   return guarded(ctx, [&]() -> pt_status {
     if (!ctx || !key) pt::fail(PT_INVALID_ARG, "context or key is NULL");
+    if (std::string(key) == "tc_period") {
+      if (value < 1 || value > 64) pt::fail(PT_INVALID_ARG, "tc_period must be in [1, 64]");
+      ctx->tc_period = int(value);
+      return PT_OK;
+    }
+    if (std::string(key) == "tc_gram") {
+      ctx->tc_gram = value != 0.0 ? 1 : 0;
+      return PT_OK;
+    }
     if (std::string(key) == "scratch_bytes") {
       if (!(value >= 1.0)) pt::fail(PT_INVALID_ARG, "scratch_bytes must be >= 1");
       ctx->scratch_budget = size_t(value);
@@ -164,6 +180,7 @@ pt_status pt_apply_exchange(pt_ctx* ctx, const void* src, const double* occ, int
     if (tgt) pt::require_aligned(tgt, "tgt");
     if (out == src || (tgt && out == tgt)) pt::fail(PT_INVALID_ARG, "out must not alias src or tgt");
     set_device(ctx);
+    set_engine(ctx, prec);
     pt::exchange(ctx, src, occ, N, tgt, M, out, *grid, *kernel, prec, static_cast<cudaStream_t>(stream));
     return PT_OK;
   });
@@ -179,6 +196,7 @@ pt_status pt_build_ace_from(pt_ctx* ctx, const void* W, const void* phi, int N, 
     pt::require_aligned(W, "W");
     pt::require_aligned(phi, "phi");
     set_device(ctx);
+    set_engine(ctx, prec);
     auto* a = new pt_ace();
     a->ctx = ctx;
     a->N = N;
@@ -193,6 +211,7 @@ pt_status pt_build_ace_from(pt_ctx* ctx, const void* W, const void* phi, int N, 
     }
     try {
       pt::ace_from_w(ctx, W, phi, N, *grid, prec, a->xi, static_cast<cudaStream_t>(stream));
+      if (ctx->active_tc) pt::gram_tc_check(ctx, static_cast<cudaStream_t>(stream));
     } catch (...) {
       cudaFree(a->xi);
       delete a;
@@ -222,6 +241,30 @@ pt_status pt_build_ace(pt_ctx* ctx, const void* phi, const double* occ, int N, c
   });
 }
 
+pt_status pt_overlap(pt_ctx* ctx, const void* A, int N1, const void* B, int N2, const pt_grid* grid,
+                     pt_precision prec, void* C, void* stream) {
+  return guarded(ctx, [&]() -> pt_status {
+    check_common(ctx, grid, prec);
+    if (N1 <= 0 || N2 <= 0) pt::fail(PT_INVALID_ARG, "N1 and N2 must be positive");
+    pt::require_aligned(A, "A");
+    pt::require_aligned(B, "B");
+    pt::require_aligned(C, "C");
+    set_device(ctx);
+    set_engine(ctx, prec);
+    auto st = static_cast<cudaStream_t>(stream);
+    const size_t ng = pt::ng_of(*grid);
+    const double dV = pt::dv_of(*grid);
+    auto* Cm = static_cast<c128*>(C);
+    const bool herm = (A == B && N1 == N2);  // Hermitian result: compute one triangle of tiles
+    if (prec == PT_FP64)
+      pt::gram<double>(ctx, static_cast<const c128*>(A), static_cast<const c128*>(B), N1, N2, ng, dV, Cm, st, herm);
+    else
+      pt::gram<float>(ctx, static_cast<const c64*>(A), static_cast<const c64*>(B), N1, N2, ng, dV, Cm, st, herm);
+    if (ctx->active_tc) pt::gram_tc_check(ctx, st);
+    return PT_OK;
+  });
+}
+
 pt_status pt_apply_ace(pt_ctx* ctx, const pt_ace* ace, const void* psi, int M, void* out, void* stream) {
   return guarded(ctx, [&]() -> pt_status {
     if (!ctx || !ace) pt::fail(PT_INVALID_ARG, "context or ACE is NULL");
@@ -230,7 +273,9 @@ pt_status pt_apply_ace(pt_ctx* ctx, const pt_ace* ace, const void* psi, int M, v
     pt::require_aligned(out, "out");
     if (out == psi) pt::fail(PT_INVALID_ARG, "out must not alias psi");
     set_device(ctx);
+    set_engine(ctx, ace->prec);
     pt::ace_apply(ctx, ace->xi, ace->N, psi, M, out, ace->grid, ace->prec, static_cast<cudaStream_t>(stream));
+    if (ctx->active_tc) pt::gram_tc_check(ctx, static_cast<cudaStream_t>(stream));
     return PT_OK;
   });
 }
@@ -260,6 +305,7 @@ pt_status pt_apply_H(pt_ctx* ctx, const void* psi, int M, void* out, const doubl
     if (ace && (ace->prec != prec || ace->grid.nx != grid->nx || ace->grid.ny != grid->ny || ace->grid.nz != grid->nz))
       pt::fail(PT_INVALID_ARG, "ACE operator does not match the grid or precision");
     set_device(ctx);
+    set_engine(ctx, prec);
     auto st = static_cast<cudaStream_t>(stream);
     const void* X = nullptr;
     if (ace) {
@@ -268,6 +314,7 @@ pt_status pt_apply_H(pt_ctx* ctx, const void* psi, int M, void* out, const doubl
       X = buf;
     }
     pt::apply_h(ctx, psi, M, out, vloc, X, alpha, ecut, *grid, prec, st);
+    if (ctx->active_tc && ace) pt::gram_tc_check(ctx, st);
     return PT_OK;
   });
 }
@@ -299,7 +346,11 @@ pt_status pt_ptim_step(pt_ctx* ctx, void* phi, void* sigma, int N, const double*
         P.anderson_depth > 20)
       pt::fail(PT_INVALID_ARG, "invalid PT-IM parameters");
     set_device(ctx);
-    return pt::ptim_step(ctx, phi, sigma, N, vloc, *grid, *kernel, P, prec, stats, static_cast<cudaStream_t>(stream));
+    set_engine(ctx, prec);
+    pt_status r =
+        pt::ptim_step(ctx, phi, sigma, N, vloc, *grid, *kernel, P, prec, stats, static_cast<cudaStream_t>(stream));
+    if (ctx->active_tc) pt::gram_tc_check(ctx, static_cast<cudaStream_t>(stream));
+    return r;
   });
 }
 

@@ -280,6 +280,22 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 }  // namespace
 
+static void encode_tmap_4d(CUtensorMap* map, CUtensorMapDataType dt, const void* base, const uint64_t dims[4],
+                          const uint64_t strides_bytes[3], const uint32_t box[4], CUtensorMapSwizzle swizzle) {
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  cuuint64_t d[4] = {dims[0], dims[1], dims[2], dims[3]};
+  cuuint64_t s[3] = {strides_bytes[0], strides_bytes[1], strides_bytes[2]};
+  cuuint32_t b[4] = {box[0], box[1], box[2], box[3]};
+  CUresult r = encode_fn()(map, dt, 4, const_cast<void*>(base), d, s, b, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) fail(PT_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string(int(r)) + ")");
+}
+
+void encode_tmap_4d_f32(CUtensorMap* map, const void* base, const uint64_t dims[4], const uint64_t strides_bytes[3],
+                        const uint32_t box[4], CUtensorMapSwizzle swizzle) {
+  encode_tmap_4d(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, base, dims, strides_bytes, box, swizzle);
+}
+
 void encode_tmap_4d_u64(CUtensorMap* map, const void* base, const uint64_t dims[4], const uint64_t strides_bytes[3],
                         const uint32_t box[4], CUtensorMapSwizzle swizzle) {
   const cuuint32_t estr[4] = {1, 1, 1, 1};

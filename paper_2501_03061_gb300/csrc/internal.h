@@ -33,6 +33,12 @@ template <class T>
 void multi_dot(pt_ctx* ctx, const void* const* u1, const c128* const* u2, int m, const cx<T>* v1, size_t n1,
                const c128* v2, size_t n2, double w1, double w2, double* out, cudaStream_t st);
 
+// ---- tensor-core Gram (gram_tc.cu) ----
+void gram_tc(pt_ctx* ctx, const c64* A, const c64* B, int N1, int N2, size_t ng, double scale, c128* C,
+             cudaStream_t st, bool herm, bool split3);
+void gram_tc_check(pt_ctx* ctx, cudaStream_t st);  // raises PT_TIMEOUT if a bounded wait expired
+bool gram_tc_applies(const void* A, const void* B, size_t ng);
+
 // ---- FP64 N x N (dense.cu) ----
 void zgemm(char opA, char opB, int m, int n, int k, c128 alpha, const c128* A, int lda, const c128* B, int ldb,
            c128 beta, c128* C, int ldc, cudaStream_t st);

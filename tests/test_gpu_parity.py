@@ -269,13 +269,19 @@ def test_ptim_step_fp64_matches_oracle(ctx, ptim_ref, use_ace):
     assert st["orth_error"] <= 1e-10
 
 
-def test_ptim_step_fp32_matches_oracle(ctx, ptim_ref):
-    """FP32 orbitals, FP64 N x N algebra: the step agrees with the FP64 oracle to FP32 accuracy."""
+@pytest.mark.parametrize("tc_gram", [0, 1])
+def test_ptim_step_fp32_matches_oracle(ctx, ptim_ref, tc_gram):
+    """FP32 orbitals, FP64 N x N algebra: the step agrees with the FP64 oracle to FP32 accuracy,
+    with the Gram contractions on CUDA cores or on tensor cores (3-product TF32)."""
     w, sig = _ptim_case()
     phi = dev(w.phi.astype(np.complex64))
     sigma = dev(sig)
-    st = ctx.ptim_step(phi, sigma, dev(w.vloc), cell=w.cell, kernel=w.kernel, precision="fp32", dt=0.5,
-                       ecut=6.0, tol=2e-6)
+    ctx.set_option("tc_gram", tc_gram)
+    try:
+        st = ctx.ptim_step(phi, sigma, dev(w.vloc), cell=w.cell, kernel=w.kernel, precision="fp32", dt=0.5,
+                           ecut=6.0, tol=2e-6)
+    finally:
+        ctx.set_option("tc_gram", 0)
     assert st["converged"]
     assert rel(phi.cpu().numpy().astype(np.complex128), ptim_ref[0]) <= 5e-5
     assert np.abs(sigma.cpu().numpy() - ptim_ref[1]).max() <= 5e-5
@@ -302,17 +308,28 @@ def test_exchange_64cubed_specialised_path(ctx, precision, sym):
     assert rel(out.cpu().numpy().astype(np.complex128), ref) <= (FP64_TOL if precision == "fp64" else FP32_TOL)
 
 
-def test_ptim_step_fp32_multitile_N66(ctx):
-    """N = 66 spans two 64-wide Gram tiles (Hermitian mirror of A and S) and several exchange batches."""
+@pytest.fixture(scope="module")
+def ref_N66():
     w = synth.small_cell(29, 10, 9.0, 66, kT=0.05, ecut=12.0)
     g = O.grid_of(w.cell)
     K = O.exchange_kernel(g, 1, synth.SCREENED_MU)
     phi1, sig1, st = O.ptim_step(w.phi, w.sigma, w.vloc, g, K, O.PtimParams(tol=1e-9, ecut=12.0))
     assert st.converged
+    return w, phi1, sig1
+
+
+@pytest.mark.parametrize("tc_gram", [0, 1])
+def test_ptim_step_fp32_multitile_N66(ctx, ref_N66, tc_gram):
+    """N = 66 spans two 64-wide Gram tiles (Hermitian mirror of A and S) and several exchange batches."""
+    w, phi1, sig1 = ref_N66
     phi = dev(w.phi.astype(np.complex64))
     sigma = dev(w.sigma)
-    s = ctx.ptim_step(phi, sigma, dev(w.vloc), cell=w.cell, kernel=w.kernel, precision="fp32", dt=0.5,
-                      ecut=12.0, tol=2e-6)
+    ctx.set_option("tc_gram", tc_gram)
+    try:
+        s = ctx.ptim_step(phi, sigma, dev(w.vloc), cell=w.cell, kernel=w.kernel, precision="fp32", dt=0.5,
+                          ecut=12.0, tol=2e-6)
+    finally:
+        ctx.set_option("tc_gram", 0)
     assert s["converged"]
     assert rel(phi.cpu().numpy().astype(np.complex128), phi1) <= 5e-5
     assert np.abs(sigma.cpu().numpy() - sig1).max() <= 5e-5
