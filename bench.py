@@ -45,8 +45,9 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--N", type=int, default=320, help="orbital count (reduced values only for profiler captures)")
-    ap.add_argument("--tc-gram", type=int, default=0, choices=[0, 1],
-                    help="1: Gram contractions of the FP32 step on tensor cores (3-product TF32)")
+    ap.add_argument("--tc-gram", type=int, default=1, choices=[0, 1],
+                    help="1: Gram and rotation contractions of the FP32 step on tensor cores (3-product "
+                         "TF32); 0: CUDA cores")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 form comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
@@ -480,7 +481,7 @@ def run_gb300(args):
             "data": "synthetic",
             "config": {"workload": workload, "grid": [64, 64, 64], "N": N, "atoms": 128, "precision": args.precision,
                        "tol": args.tol, "dt_au": 0.5, "parallelism": f"replicas{world}",
-                       "gram_engine": "tcgen05 3xTF32" if args.tc_gram else "CUDA cores, compensated FP32",
+                       "contraction_engine": "tcgen05 3xTF32" if args.tc_gram else "CUDA cores",
                        "l2": "inputs larger than L2 (phi alone is %d MB)" % (N * ng * esz >> 20)},
             "pair_ffts_per_s": pair_ffts / (ms / 1e3) if ms > 0 else None,
             "exchange": {"pair_ffts": pair_ffts, "calls": ex_calls, "ms": ex_ms,

@@ -164,6 +164,13 @@ void pt_ace_destroy(pt_ace* ace);
 pt_status pt_overlap(pt_ctx* ctx, const void* A, int N1, const void* B, int N2, const pt_grid* grid,
                      pt_precision prec, void* C, void* stream);
 
+/* out_j = sum_k B[k][j] A_k, j < N2: the rotation of an orbital block by an N1 x N2 matrix, e.g.
+ * phit = Phi Q into the sigma eigenbasis (Eq. vxdiag) or xi = W L^{-*} of the ACE construction.
+ * A: Ng x N1 orbitals, out: Ng x N2 orbitals (device, orbital-major, precision prec; out must
+ * not overlap A); B: N1 x N2 complex128 (device, row-major).  Engines as for pt_overlap. */
+pt_status pt_rotate(pt_ctx* ctx, const void* A, int N1, const void* B, int N2, const pt_grid* grid,
+                    pt_precision prec, void* out, void* stream);
+
 /* ---- Hamiltonian (Eq. 1 with frozen V_Hxc + V_ext) -------------------------------------- */
 
 /* out = P_sph[ -1/2 Lap psi + vloc * psi + alpha * V_ACE psi ], the projection

@@ -53,6 +53,7 @@ PROTOTYPES = {
     "pt_ace_get_xi": (i32, [vp, vp, vp]),
     "pt_ace_destroy": (None, [vp]),
     "pt_overlap": (i32, [vp, vp, i32, vp, i32, C.POINTER(pt_grid), i32, vp, vp]),
+    "pt_rotate": (i32, [vp, vp, i32, vp, i32, C.POINTER(pt_grid), i32, vp, vp]),
     "pt_apply_H": (i32, [vp, vp, i32, vp, vp, vp, C.c_double, C.c_double, C.POINTER(pt_grid), i32, vp]),
     "pt_diag_occupations": (i32, [vp, vp, i32, vp, vp, vp]),
     "pt_ptim_step": (i32, [vp, vp, vp, i32, vp, C.POINTER(pt_grid), C.POINTER(pt_kernel),

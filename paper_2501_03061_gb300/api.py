@@ -178,6 +178,20 @@ class Context:
         self._check(st, "pt_overlap")
         return out
 
+    def rotate(self, A, B, *, cell, precision="fp64", out=None, stream=None):
+        """out_j = sum_k B[k, j] A_k for an (N1, N2) complex128 device matrix B."""
+        self._orb(A, precision, "A")
+        B = B.to(device=self.device, dtype=torch.complex128).contiguous()
+        if B.dim() != 2 or B.shape[0] != A.shape[0]:
+            raise ValueError("B must be (N1, N2) with N1 = A.shape[0]")
+        if out is None:
+            out = torch.empty((B.shape[1],) + tuple(A.shape[1:]), dtype=A.dtype, device=self.device)
+        g = _grid(cell)
+        st = self.lib.pt_rotate(self.h, _ptr(A), A.shape[0], _ptr(B), B.shape[1], C.byref(g),
+                                L.PRECISIONS[precision], _ptr(out), _stream(stream))
+        self._check(st, "pt_rotate")
+        return out
+
     # ---- Hamiltonian ------------------------------------------------------------------------
     def apply_H(self, psi, vloc, ace: Ace | None = None, alpha=0.25, ecut=10.0, *, cell, precision="fp64",
                 out=None, stream=None):

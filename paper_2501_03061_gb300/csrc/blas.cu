@@ -398,7 +398,12 @@ void gram(pt_ctx* ctx, const cx<T>* A, const cx<T>* B, int N1, int N2, size_t ng
 template <class T>
 void rotate(pt_ctx* ctx, const cx<T>* A, const c128* Bm, int ldb, int N1, int N2, size_t ng, c128 alpha,
             const Term* terms, int nterms, cx<T>* out, cudaStream_t st) {
-  (void)ctx;
+  if constexpr (sizeof(T) == 4) {
+    if (ctx->active_tc && nterms <= 3 && rotate_tc_applies(A, ng)) {
+      rotate_tc(ctx, A, Bm, ldb, N1, N2, ng, alpha, terms, nterms, out, st, ctx->active_tc == 1);
+      return;
+    }
+  }
   Epi<T> epi{};
   for (int t = 0; t < 3; ++t) {
     epi.e[t] = (t < nterms) ? static_cast<const cx<T>*>(terms[t].x) : nullptr;

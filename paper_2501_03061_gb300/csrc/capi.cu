@@ -265,6 +265,33 @@ pt_status pt_overlap(pt_ctx* ctx, const void* A, int N1, const void* B, int N2, 
   });
 }
 
+pt_status pt_rotate(pt_ctx* ctx, const void* A, int N1, const void* B, int N2, const pt_grid* grid,
+                    pt_precision prec, void* out, void* stream) {
+  return guarded(ctx, [&]() -> pt_status {
+    check_common(ctx, grid, prec);
+    if (N1 <= 0 || N2 <= 0) pt::fail(PT_INVALID_ARG, "N1 and N2 must be positive");
+    pt::require_aligned(A, "A");
+    pt::require_aligned(B, "B");
+    pt::require_aligned(out, "out");
+    const size_t ng = pt::ng_of(*grid), eb = pt::elem_bytes(prec);
+    const char* a0 = static_cast<const char*>(A);
+    const char* o0 = static_cast<const char*>(out);
+    if (o0 < a0 + ng * N1 * eb && a0 < o0 + ng * N2 * eb) pt::fail(PT_INVALID_ARG, "out overlaps A");
+    set_device(ctx);
+    set_engine(ctx, prec);
+    auto st = static_cast<cudaStream_t>(stream);
+    const auto* Bm = static_cast<const c128*>(B);
+    if (prec == PT_FP64)
+      pt::rotate<double>(ctx, static_cast<const c128*>(A), Bm, N2, N1, N2, ng, c128{1, 0}, nullptr, 0,
+                         static_cast<c128*>(out), st);
+    else
+      pt::rotate<float>(ctx, static_cast<const c64*>(A), Bm, N2, N1, N2, ng, c128{1, 0}, nullptr, 0,
+                        static_cast<c64*>(out), st);
+    if (ctx->active_tc) pt::gram_tc_check(ctx, st);
+    return PT_OK;
+  });
+}
+
 pt_status pt_apply_ace(pt_ctx* ctx, const pt_ace* ace, const void* psi, int M, void* out, void* stream) {
   return guarded(ctx, [&]() -> pt_status {
     if (!ctx || !ace) pt::fail(PT_INVALID_ARG, "context or ACE is NULL");

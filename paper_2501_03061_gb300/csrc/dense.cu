@@ -155,14 +155,15 @@ __global__ void __launch_bounds__(JB* JB) k_jacobi_round(const c128* __restrict_
   }
 }
 
-__global__ void k_herm_part_and_identity(const c128* __restrict__ S, c128* __restrict__ A, c128* __restrict__ V,
-                                         int N) {
+// A = (S + S^*)/2 and V = V0 (identity when V0 is NULL)
+__global__ void k_herm_part_and_basis(const c128* __restrict__ S, c128* __restrict__ A, const c128* __restrict__ V0,
+                                      c128* __restrict__ V, int N) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= N * N) return;
   const int i = e / N, j = e % N;
   const c128 a = S[size_t(i) * N + j], b = S[size_t(j) * N + i];
   A[e] = c128{0.5 * (a.re + b.re), 0.5 * (a.im - b.im)};
-  V[e] = c128{i == j ? 1.0 : 0.0, 0.0};
+  V[e] = V0 ? V0[e] : c128{i == j ? 1.0 : 0.0, 0.0};
 }
 
 // sums of |offdiag|^2 and |all|^2 (one block)
@@ -396,13 +397,22 @@ void zgemm(char opA, char opB, int m, int n, int k, c128 alpha, const c128* A, i
   PT_LAUNCH(k_zgemm, grid, ZT * ZT, 0, st, opA, opB, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
 }
 
-void heev(pt_ctx* ctx, const c128* S, int N, c128* Q, double* d, cudaStream_t st, int max_sweeps) {
+void heev(pt_ctx* ctx, const c128* S, int N, c128* Q, double* d, cudaStream_t st, int max_sweeps, const c128* Q0) {
   const int Np = N + (N & 1);
   c128* A0 = static_cast<c128*>(ctx->get("heev_A0", size_t(N) * N * sizeof(c128)));
   c128* A1 = static_cast<c128*>(ctx->get("heev_A1", size_t(N) * N * sizeof(c128)));
   c128* V = static_cast<c128*>(ctx->get("heev_V", size_t(N) * N * sizeof(c128)));
   double* nrm = static_cast<double*>(ctx->get("heev_norm", 2 * sizeof(double)));
-  PT_LAUNCH(k_herm_part_and_identity, (N * N + 255) / 256, 256, 0, st, S, A0, V, N);
+  if (Q0) {
+    // warm start: rotate into the basis Q0 (Jacobi then starts from a nearly diagonal matrix when
+    // Q0 diagonalises a nearby matrix) and accumulate the rotations onto Q0
+    zgemm('N', 'N', N, N, N, c128{1, 0}, S, N, Q0, N, c128{0, 0}, A1, N, st);
+    zgemm('C', 'N', N, N, N, c128{1, 0}, Q0, N, A1, N, c128{0, 0}, V, N, st);
+    PT_LAUNCH(k_herm_part_and_basis, (N * N + 255) / 256, 256, 0, st, V, A0, Q0, A1, N);
+    std::swap(V, A1);
+  } else {
+    PT_LAUNCH(k_herm_part_and_basis, (N * N + 255) / 256, 256, 0, st, S, A0, nullptr, V, N);
+  }
   const int half = Np / 2;
   dim3 grid((half + JB - 1) / JB, (half + JB - 1) / JB);
   double h[2] = {0, 0};

@@ -39,11 +39,18 @@ void gram_tc(pt_ctx* ctx, const c64* A, const c64* B, int N1, int N2, size_t ng,
 void gram_tc_check(pt_ctx* ctx, cudaStream_t st);  // raises PT_TIMEOUT if a bounded wait expired
 bool gram_tc_applies(const void* A, const void* B, size_t ng);
 
+// ---- tensor-core rotation (rotate_tc.cu): out = alpha A Bm + sum_t c_t x_t (complex64 orbitals) ----
+void rotate_tc(pt_ctx* ctx, const c64* A, const c128* Bm, int ldb, int N1, int N2, size_t ng, c128 alpha,
+               const Term* terms, int nterms, c64* out, cudaStream_t st, bool split3);
+bool rotate_tc_applies(const void* A, size_t ng);
+
 // ---- FP64 N x N (dense.cu) ----
 void zgemm(char opA, char opB, int m, int n, int k, c128 alpha, const c128* A, int lda, const c128* B, int ldb,
            c128 beta, c128* C, int ldc, cudaStream_t st);
 // S (Hermitian part used) = Q diag(d) Q^*, ascending d.  Synchronises st once per sweep.
-void heev(pt_ctx* ctx, const c128* S, int N, c128* Q, double* d, cudaStream_t st, int max_sweeps = 30);
+// Q0 (optional): an orthonormal basis that nearly diagonalises S (warm start); may alias Q
+void heev(pt_ctx* ctx, const c128* S, int N, c128* Q, double* d, cudaStream_t st, int max_sweeps = 30,
+          const c128* Q0 = nullptr);
 // A (overwritten) = L L^* ; L written to a separate buffer; *info = k+1 on a bad pivot k.
 void cholesky(pt_ctx* ctx, c128* A, int N, c128* L, int* info, cudaStream_t st);
 void tri_inv_lower(const c128* L, int N, c128* X, cudaStream_t st);

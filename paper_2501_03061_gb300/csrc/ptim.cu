@@ -230,9 +230,12 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
     }
   } ev_guard{ev};
   // V_x[P_h] Phi_h through the sigma_h eigenbasis: (V_x phit) Q^*, phit = Phi_h Q
+  // sigma_h changes little between outer iterations: later eigensolves start from the last basis
+  bool have_q = false;
   auto exchange_on_midpoint = [&](cx<T>* out, bool energy) {
     tm.begin(PH_EIG);
-    heev(ctx, sigh, N, Q, d, st);
+    heev(ctx, sigh, N, Q, d, st, 30, have_q ? Q : nullptr);
+    have_q = true;
     tm.end();
     tm.begin(PH_ROT);
     rotate<T>(ctx, phih, Q, N, N, N, S.ng, c128{1, 0}, nullptr, 0, phit, st);

@@ -1,4 +1,5 @@
-"""GPU parity of the overlap contraction C = dV A^* B (ACE's M = <phi|W>, PT-IM's S = <phi|phi>).
+"""GPU parity of the two grid contractions: the overlap C = dV A^* B (ACE's M = <phi|W>,
+PT-IM's S = <phi|phi>) and the rotation out_j = sum_k B[k][j] A_k (phit = Phi Q, xi = W L^-*).
 
 The FP32 forms are compared with the FP64 oracle evaluated on the same FP32-rounded inputs, so
 the bound measures the contraction alone: |C_gpu - C_ref| <= tol * dV sum_r |a_i(r)| |b_j(r)|
@@ -128,3 +129,58 @@ def test_overlap_64cubed_N320_tensor_cores_sampled(ctx):
         assert abs(simt[i, j] - ref) <= TOL["fp32"] * scale
     diag = dV * (absn ** 2).sum(axis=1)
     assert np.abs(tc - simt).max() <= 2 * TOL["fp32_tc"] * diag.max()
+
+
+def run_rotate(ctx, mode, A, B, cell):
+    prec = {"fp32_tc": "fp32"}.get(mode, mode)
+    dt = np.complex128 if prec == "fp64" else np.complex64
+    ctx.set_option("tc_gram", 1 if mode == "fp32_tc" else 0)
+    try:
+        return ctx.rotate(dev(A.astype(dt)), dev(B), cell=cell, precision=prec).cpu().numpy()
+    finally:
+        ctx.set_option("tc_gram", 0)
+
+
+def check_rotate(got, A, B, tol):
+    A64 = A.astype(np.complex128)
+    ref = O.rotate(A64, B)
+    scale = (np.abs(B).T @ np.abs(A64).reshape(len(A64), -1)).reshape(ref.shape)
+    err = np.abs(got - ref)
+    assert np.all(err <= tol * scale), float((err / scale).max())
+
+
+ROT_TOL = {"fp32": 1e-5, "fp32_tc": 1e-5, "tf32": 2e-3}
+
+
+@pytest.mark.parametrize("mode", ["fp64", "fp32", "fp32_tc", "tf32"])
+@pytest.mark.parametrize("shape", [(24, 24, 24), (9, 10, 12)])
+def test_rotate_ragged(ctx, mode, shape):
+    """N1 = 70 (partial last K stage of 16 orbitals), N2 = 130 (partial last 64-orbital tile);
+    9 x 10 x 12 = 1080 points leaves a partial 128-point tile."""
+    rng = np.random.default_rng(311)
+    cell = synth.Cell(shape, (6.0, 6.5, 7.0))
+    A = fields(rng, cell, 70)
+    B = rng.standard_normal((70, 130)) + 1j * rng.standard_normal((70, 130))
+    got = run_rotate(ctx, mode, A, B, cell)
+    if mode == "fp64":
+        ref = O.rotate(A.astype(np.complex128), B)
+        assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+    else:
+        check_rotate(got, A, B, ROT_TOL[mode])
+
+
+def test_rotate_64cubed_N320_tensor_cores_sampled(ctx):
+    """Full size of the PT-IM rotations (64^3 grid, N = 320, a unitary B as for phit = Phi Q)."""
+    rng = np.random.default_rng(312)
+    cell = synth.cubic(64, 20.5)
+    A = fields(rng, cell, 320)
+    Q, _ = np.linalg.qr(rng.standard_normal((320, 320)) + 1j * rng.standard_normal((320, 320)))
+    got = run_rotate(ctx, "fp32_tc", A, Q, cell).reshape(320, -1)
+    simt = run_rotate(ctx, "fp32", A, Q, cell).reshape(320, -1)
+    Af = A.reshape(320, -1).astype(np.complex128)
+    for _ in range(64):
+        j, r = int(rng.integers(0, 320)), int(rng.integers(0, Af.shape[1]))
+        ref = np.sum(Q[:, j] * Af[:, r])
+        scale = float(np.sum(np.abs(Q[:, j]) * np.abs(Af[:, r])))
+        assert abs(got[j, r] - ref) <= ROT_TOL["fp32_tc"] * scale
+        assert abs(simt[j, r] - ref) <= ROT_TOL["fp32"] * scale
