@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 form comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
-    ap.add_argument("--mode", default="step", choices=["step", "exchange", "serve"],
+    ap.add_argument("--mode", default="step", choices=["step", "exchange", "serve", "batched"],
                     help="step: PT-IM steps (the benchmark); exchange: only V_x applications on the same cell "
                          "(profiler captures of the exchange kernel)")
     ap.add_argument("--serve-window", type=float, default=15.0, help="seconds of arrivals per serving phase")
@@ -298,37 +298,59 @@ def serve_measurement(window_s: float, slots: int = 6) -> dict:
     return out
 
 
-def batched_measurement(slots: int = 8) -> dict:
-    """Batched form: 64 independent V_x applications (N ~ U{16..256}, grids 24^3..64^3, FP32)
-    submitted together and run concurrently over the serving slots; pair-FFTs/s of the batch."""
+def batched_measurement(reps: int = 3) -> dict:
+    """Batched form: 64 independent V_x applications (N ~ U{16..256}, grids 24^3..64^3, FP32) in
+    one pt_apply_exchange_batched call: autotuned pair tiles, replayed from one captured CUDA graph.
+    Inputs resident on the device; CUDA events around the replays.  The same batch run eagerly
+    (graphs off) is timed beside it."""
     import numpy as np
+    import torch
 
-    from paper_2501_03061_gb300 import serve, synth
+    from paper_2501_03061_gb300 import api, synth
 
     specs = synth.batched_instances()
     templates = {}
     for n in sorted({s["n"] for s in specs}):
         templates[n] = synth.small_cell(3000 + n, n, 0.32 * n, 256, kT=0.02, natoms=8)
-    reqs = []
-    pairs = 0
-    for sp in specs:
-        w = templates[sp["n"]]
-        N = sp["N"]
-        reqs.append(serve.Request(phi=w.phi[:N], sigma=None, occ=synth.fermi_dirac_occupations(N, 0.02), vloc=None,
-                                  cell=w.cell, kernel=w.kernel, kind="exchange", precision="fp32"))
-        pairs += N * (N + 1) // 2
-    srv = serve.Server(slots=slots)
+    ctx = api.Context(0)
     try:
-        for f in [srv.submit(r) for r in reqs[:slots]]:  # warm-up pass over the slots
-            f.result()
+        items, pairs = [], 0
+        for sp in specs:
+            w = templates[sp["n"]]
+            N = sp["N"]
+            src = torch.from_numpy(np.ascontiguousarray(w.phi[:N].astype(np.complex64))).cuda()
+            occ = torch.from_numpy(synth.fermi_dirac_occupations(N, 0.02)).cuda()
+            items.append({"src": src, "occ": occ, "cell": w.cell, "kernel": w.kernel, "out": torch.empty_like(src)})
+            pairs += N * (N + 1) // 2
+        stream = torch.cuda.current_stream()
         t0 = time.perf_counter()
-        done = [f.result() for f in [srv.submit(r) for r in reqs]]
-        dt = time.perf_counter() - t0
+        _, npairs, _ = ctx.apply_exchange_batched(items, precision="fp32")  # tunes, runs eagerly, captures
+        torch.cuda.synchronize()
+        first_s = time.perf_counter() - t0
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = api.kernel_launches()
+        a.record(stream)
+        for _ in range(reps):
+            _, _, nodes = ctx.apply_exchange_batched(items, precision="fp32")
+        b.record(stream)
+        torch.cuda.synchronize()
+        host_launches = api.kernel_launches() - l0
+        t_graph = a.elapsed_time(b) / reps / 1e3
+        ctx.set_option("graphs", 0)
+        a.record(stream)
+        ctx.apply_exchange_batched(items, precision="fp32")
+        b.record(stream)
+        torch.cuda.synchronize()
+        t_eager = a.elapsed_time(b) / 1e3
+        ctx.set_option("graphs", 1)
     finally:
-        srv.close()
-    errs = [r.error for r in done if r.error]
-    return {"instances": len(reqs), "pair_ffts": pairs, "seconds": dt, "pair_ffts_per_s": pairs / dt,
-            "slots": slots, "errors": errs[:3], "note": "wall clock incl. host<->device copies of each instance"}
+        ctx.close()
+    return {"instances": len(items), "pair_ffts": npairs, "seconds": t_graph, "pair_ffts_per_s": npairs / t_graph,
+            "graph_nodes": nodes, "host_kernel_launches_per_replay": host_launches // reps,
+            "eager_seconds": t_eager, "eager_pair_ffts_per_s": npairs / t_eager,
+            "first_call_seconds_incl_autotune_and_capture": first_s,
+            "note": "one pt_apply_exchange_batched call per replay (one graph launch), inputs resident on "
+                    "the device, CUDA events on the launching stream"}
 
 
 def run_gb300(args):
@@ -548,6 +570,10 @@ def main():
         run_reference(args)
     elif args.mode == "exchange":
         run_exchange_only(args)
+    elif args.mode == "batched":
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps({"mode": "batched", "batched": batched_measurement()}), flush=True)
     elif args.mode == "serve":
         import torch
         torch.cuda.set_device(0)

@@ -90,7 +90,8 @@ const char* pt_last_error(const pt_ctx* ctx);
 size_t pt_workspace_bytes(const pt_ctx* ctx);
 /* Release cached workspace (synchronises). */
 pt_status pt_trim(pt_ctx* ctx);
-/* Set a tuning option of the context.  Keys:
+/* Set a tuning option of the context.  Keys (besides "graphs" and "autotune" of the batched
+ * exchange, 0 or 1):
  *   "scratch_bytes"  bytes of pair/orbital fields one FFT batch may hold (default 48 MiB, sized
  *                    to stay resident in L2; smaller values give more, smaller batches).
  *   "tc_gram"        1: in the PT_FP32 form, run the Gram contractions (A^H B over the grid) on
@@ -129,6 +130,32 @@ pt_status pt_apply_exchange(pt_ctx* ctx, const void* src, const double* occ, int
  * (non-TMA) exchange kernels.  Other status codes as pt_apply_exchange. */
 pt_status pt_apply_exchange_noalloc(const void* src, const double* occ, int N, const void* tgt, int M, void* out,
                                     const pt_grid* grid, const pt_kernel* kernel, pt_precision prec, void* stream);
+
+/* One item of a batched exchange call: out = V_x tgt for its own orbitals, grid and kernel
+ * (fields as in pt_apply_exchange; tgt NULL means tgt = src and M = N). */
+typedef struct {
+  const void* src;
+  const double* occ;
+  int N;
+  const void* tgt;
+  int M;
+  void* out;
+  pt_grid grid;
+  pt_kernel kernel;
+} pt_exchange_item;
+
+/* Batched exchange: `count` independent V_x applications (different orbital counts, grids and
+ * kernels) in one call, in the given precision, in item order on `stream`.  The pair-tile size
+ * of each grid is chosen by timing a few candidates the first time the grid is seen (option
+ * "autotune", default 1).  The first call with a given item set (the same buffers and sizes)
+ * runs eagerly and records the batch into a CUDA graph; later calls with the same item set
+ * replay the graph as one launch (option "graphs", default 1).  pt_trim drops the graphs.
+ * Synchronises `stream` once at the end to read the kernels' error word (PT_TIMEOUT if a
+ * bounded wait expired).  *pair_ffts (optional) receives the pair FFTs of the batch and
+ * *graph_nodes (optional) the node count of the graph that ran (0: eager).  No counterpart
+ * in the paper, which treats one system at a time: this is the batched serving form. */
+pt_status pt_apply_exchange_batched(pt_ctx* ctx, const pt_exchange_item* items, int count, pt_precision prec,
+                                    long long* pair_ffts, size_t* graph_nodes, void* stream);
 
 /* ---- adaptively compressed exchange (Sec. IV-A2, Eq. vx_ace; Lin's construction) -------- */
 

@@ -21,6 +21,11 @@ class pt_kernel(C.Structure):
     _fields_ = [("type", C.c_int), ("mu", C.c_double), ("g0", C.c_double)]
 
 
+class pt_exchange_item(C.Structure):
+    _fields_ = [("src", C.c_void_p), ("occ", C.c_void_p), ("N", C.c_int), ("tgt", C.c_void_p), ("M", C.c_int),
+                ("out", C.c_void_p), ("grid", pt_grid), ("kernel", pt_kernel)]
+
+
 class pt_ptim_params(C.Structure):
     _fields_ = [("dt", C.c_double), ("alpha", C.c_double), ("ecut", C.c_double), ("tol", C.c_double),
                 ("max_outer", C.c_int), ("max_inner", C.c_int), ("anderson_depth", C.c_int),
@@ -47,6 +52,8 @@ PROTOTYPES = {
     "pt_set_option": (i32, [vp, C.c_char_p, C.c_double]),
     "pt_apply_exchange": (i32, [vp, vp, vp, i32, vp, i32, vp, C.POINTER(pt_grid), C.POINTER(pt_kernel), i32, vp]),
     "pt_apply_exchange_noalloc": (i32, [vp, vp, i32, vp, i32, vp, C.POINTER(pt_grid), C.POINTER(pt_kernel), i32, vp]),
+    "pt_apply_exchange_batched": (i32, [vp, C.POINTER(pt_exchange_item), i32, i32, C.POINTER(C.c_longlong),
+                                        C.POINTER(C.c_size_t), vp]),
     "pt_build_ace": (i32, [vp, vp, vp, i32, C.POINTER(pt_grid), C.POINTER(pt_kernel), i32, C.POINTER(vp), vp]),
     "pt_build_ace_from": (i32, [vp, vp, vp, i32, C.POINTER(pt_grid), i32, C.POINTER(vp), vp]),
     "pt_apply_ace": (i32, [vp, vp, vp, i32, vp, vp]),

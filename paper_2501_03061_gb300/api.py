@@ -135,6 +135,33 @@ class Context:
         self._check(st, "pt_apply_exchange")
         return out
 
+    def apply_exchange_batched(self, items, *, precision="fp32", stream=None):
+        """Batched V_x applications.  items: list of dicts with keys src, occ, cell and optional
+        tgt, out, kernel (as apply_exchange).  Returns (outs, pair_ffts, graph_nodes)."""
+        arr = (L.pt_exchange_item * len(items))()
+        outs, keep = [], []
+        for k, it in enumerate(items):
+            src = self._orb(it["src"], precision, "src")
+            tgt = it.get("tgt")
+            if tgt is not None:
+                self._orb(tgt, precision, "tgt")
+            occ = it["occ"].to(device=self.device, dtype=torch.float64).contiguous()
+            out = it.get("out")
+            if out is None:
+                out = torch.empty_like(src if tgt is None else tgt)
+            keep.append(occ)
+            outs.append(out)
+            a = arr[k]
+            a.src, a.occ, a.N = src.data_ptr(), occ.data_ptr(), src.shape[0]
+            a.tgt, a.M = (None, 0) if tgt is None else (tgt.data_ptr(), tgt.shape[0])
+            a.out = out.data_ptr()
+            a.grid, a.kernel = _grid(it["cell"]), _kernel(it.get("kernel"))
+        pairs, nodes = C.c_longlong(0), C.c_size_t(0)
+        st = self.lib.pt_apply_exchange_batched(self.h, arr, len(items), L.PRECISIONS[precision], C.byref(pairs),
+                                                C.byref(nodes), _stream(stream))
+        self._check(st, "pt_apply_exchange_batched")
+        return outs, int(pairs.value), int(nodes.value)
+
     # ---- ACE --------------------------------------------------------------------------------
     def build_ace(self, phi, occ, *, cell, kernel=None, precision="fp64", stream=None) -> Ace:
         self._orb(phi, precision, "phi")

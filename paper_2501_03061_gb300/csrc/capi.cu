@@ -52,6 +52,11 @@ void pt_ctx::release_all() {
   bufs.clear();
   held = 0;
   tc_err_clean = false;
+  // captured graphs hold pointers into the freed workspace
+  for (auto it = caches.begin(); it != caches.end();) {
+    if (it->first.rfind("graph:", 0) == 0) it = caches.erase(it);
+    else ++it;
+  }
 }
 
 namespace {
@@ -128,6 +133,7 @@ void pt_destroy(pt_ctx* ctx) {
   cudaSetDevice(ctx->device);
   ctx->release_all();
   ctx->caches.clear();
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   delete ctx;
 }
 
@@ -147,6 +153,10 @@ pt_status pt_trim(pt_ctx* ctx) {
 pt_status pt_set_option(pt_ctx* ctx, const char* key, double value) {
   return guarded(ctx, [&]() -> pt_status {
     if (!ctx || !key) pt::fail(PT_INVALID_ARG, "context or key is NULL");
+    if (std::string(key) == "graphs" || std::string(key) == "autotune") {
+      (std::string(key) == "graphs" ? ctx->use_graphs : ctx->autotune) = value != 0.0 ? 1 : 0;
+      return PT_OK;
+    }
     if (std::string(key) == "tc_period") {
       if (value < 1 || value > 64) pt::fail(PT_INVALID_ARG, "tc_period must be in [1, 64]");
       ctx->tc_period = int(value);
@@ -182,6 +192,36 @@ pt_status pt_apply_exchange(pt_ctx* ctx, const void* src, const double* occ, int
     set_device(ctx);
     set_engine(ctx, prec);
     pt::exchange(ctx, src, occ, N, tgt, M, out, *grid, *kernel, prec, static_cast<cudaStream_t>(stream));
+    return PT_OK;
+  });
+}
+
+pt_status pt_apply_exchange_batched(pt_ctx* ctx, const pt_exchange_item* items, int count, pt_precision prec,
+                                    long long* pair_ffts, size_t* graph_nodes, void* stream) {
+  return guarded(ctx, [&]() -> pt_status {
+    if (!ctx) pt::fail(PT_INVALID_ARG, "context is NULL");
+    if (count <= 0 || !items) pt::fail(PT_INVALID_ARG, "no items");
+    if (prec < PT_FP64 || prec > PT_FP32_TC_BF16) pt::fail(PT_INVALID_ARG, "unknown precision");
+    for (int k = 0; k < count; ++k) {
+      const pt_exchange_item& it = items[k];
+      const std::string w = "item " + std::to_string(k) + ": ";
+      try {
+        pt::validate_grid(&it.grid);
+        check_kernel(&it.kernel);
+      } catch (const pt::Error& e) {
+        pt::fail(e.code, w + e.msg);
+      }
+      if (it.N <= 0 || (it.tgt && it.M <= 0)) pt::fail(PT_INVALID_ARG, w + "N and M must be positive");
+      if (!it.occ) pt::fail(PT_INVALID_ARG, w + "occ is NULL");
+      pt::require_aligned(it.src, "src");
+      pt::require_aligned(it.out, "out");
+      if (it.tgt) pt::require_aligned(it.tgt, "tgt");
+      if (it.out == it.src || (it.tgt && it.out == it.tgt))
+        pt::fail(PT_INVALID_ARG, w + "out must not alias src or tgt");
+    }
+    set_device(ctx);
+    const long long n = pt::exchange_batched(ctx, items, count, prec, static_cast<cudaStream_t>(stream), graph_nodes);
+    if (pair_ffts) *pair_ffts = n;
     return PT_OK;
   });
 }

@@ -103,6 +103,12 @@ struct pt_ctx {
   int active_tc = 0;   // per call: 0 CUDA cores, 1 tensor cores 3xTF32, 2 tensor cores single TF32
   int tc_period = 2;   // option: K stages (32 floats each) accumulated in TMEM between readouts
   bool tc_err_clean = false;  // the tensor-core Gram's device error word exists and has been zeroed
+  // batched exchange (batched.cu)
+  int use_graphs = 1;          // option "graphs": replay repeated batches from captured CUDA graphs
+  int autotune = 1;            // option "autotune": pick the pair-tile budget per grid by measurement
+  size_t budget_override = 0;  // pair-field budget in force for the current batched call (0: scratch_budget)
+  bool defer_checks = false;   // inside a batched call: device error words are checked once at the end
+  cudaStream_t cap_stream = nullptr;  // non-default stream that graph captures are recorded on
   std::string err;
   std::map<std::string, pt::DevBuf> bufs;
   std::map<std::string, std::shared_ptr<void>> caches;  // keyed host-side caches of device tables

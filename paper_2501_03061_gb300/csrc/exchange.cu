@@ -266,7 +266,7 @@ long long exchange_t(pt_ctx* ctx, const cx<T>* src, const double* occ, int N, co
   const size_t ng = ng_of(g);
   const size_t field = ng * sizeof(cx<T>);
   // Pair batch: as many pair fields as fit a budget that keeps them L2-resident.
-  const size_t budget = exchange_scratch_budget(ctx);
+  const size_t budget = ctx->budget_override ? ctx->budget_override : exchange_scratch_budget(ctx);
   int B = int(std::floor(std::sqrt(double(std::max<size_t>(1, budget / field)))));
   B = std::max(1, std::min(B, std::max(N, M)));
   if (exchange64_applies(g) && sizeof(T) == 4) B = std::min(B, 6);
@@ -283,7 +283,7 @@ long long exchange_t(pt_ctx* ctx, const cx<T>* src, const double* occ, int N, co
   if (exchange64_applies(g)) {
     if constexpr (sizeof(T) == 4) {
       exchange64_tma(ctx, *sch, src, occ, tgt, M, out, ktab, static_cast<const cx<T>*>(ft.tw), st);
-      exchange_check(ctx, st);
+      if (!ctx->defer_checks) exchange_check(ctx, st);
     } else {
       exchange64<T>(ctx, *sch, src, occ, tgt, out, ktab, static_cast<const cx<T>*>(ft.tw), st);
     }

@@ -315,7 +315,7 @@ void exchange64_tma(pt_ctx* ctx, const ScheduleImpl& sch, const c64* src, const 
   const int maxp = sch.max_pairs;
   c64* scratch = static_cast<c64*>(ctx->get("exchange64_scratch", 4 * size_t(maxp) * ng * sizeof(c64)));
   int* err = static_cast<int*>(ctx->get("exchange_err", sizeof(int)));
-  PT_CUDA_CHECK(cudaMemsetAsync(err, 0, sizeof(int), st));
+  if (!ctx->defer_checks) PT_CUDA_CHECK(cudaMemsetAsync(err, 0, sizeof(int), st));  // else zeroed once per batch
   static bool init = false;
   if (!init) {
     PT_CUDA_CHECK(cudaFuncSetAttribute(k_exchange64_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));

@@ -17,6 +17,11 @@ size_t exchange_scratch_budget(const pt_ctx* ctx);
 long long exchange(pt_ctx* ctx, const void* src, const double* occ, int N, const void* tgt, int M, void* out,
                    const pt_grid& g, const pt_kernel& k, pt_precision prec, cudaStream_t st);
 
+// ---- batched exchange (batched.cu): autotuned pair tiles, replay from captured CUDA graphs ----
+long long exchange_batched(pt_ctx* ctx, const pt_exchange_item* items, int count, pt_precision prec,
+                           cudaStream_t st, size_t* graph_nodes);
+void exchange_check(pt_ctx* ctx, cudaStream_t st);
+
 // ---- contractions over the grid (blas.cu) ----
 template <class T>
 void gram(pt_ctx* ctx, const cx<T>* A, const cx<T>* B, int N1, int N2, size_t ng, double scale, c128* C,
