@@ -16,6 +16,7 @@
 
 #include "exchange_sched.h"
 #include "fft.cuh"
+#include "fft_fixed.cuh"
 #include "internal.h"
 
 namespace pt {
@@ -290,10 +291,20 @@ long long exchange_t(pt_ctx* ctx, const cx<T>* src, const double* occ, int N, co
     return sch->total_pairs;
   }
   cx<T>* scratch = static_cast<cx<T>*>(ctx->get("exchange_scratch", size_t(sch->max_pairs) * field));
-  set_smem_attrs<T>();
-  const size_t smem = tile_smem_bytes(sizeof(cx<T>));
   const cx<T>* twg = static_cast<const cx<T>*>(ft.tw);
   const int nbatch = int(sch->pair_off.size()) - 1;
+  if (fixed_cubic(g)) {
+    // compile-time FFT kernels for this side; inverse plane transforms once per pair
+    for (int b = 0; b < nbatch; ++b) {
+      const int p0 = sch->pair_off[b], np = sch->pair_off[b + 1] - p0;
+      const int t0 = sch->tgt_off[b], nt = sch->tgt_off[b + 1] - t0;
+      exchange_batch_fixed<T>(g.nx, src, tgt, occ, sch->d_pairs + p0, np, sch->d_tgts + t0, nt, sch->d_contribs,
+                              ktab, twg, scratch, out, st);
+    }
+    return sch->total_pairs;
+  }
+  set_smem_attrs<T>();
+  const size_t smem = tile_smem_bytes(sizeof(cx<T>));
   for (int b = 0; b < nbatch; ++b) {
     const int p0 = sch->pair_off[b], np = sch->pair_off[b + 1] - p0;
     const int t0 = sch->tgt_off[b], nt = sch->tgt_off[b + 1] - t0;

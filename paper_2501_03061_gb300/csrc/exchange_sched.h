@@ -53,6 +53,11 @@ template <class T>
 void exchange_batch_generic(const GridPlan& gp, const cx<T>* src, const cx<T>* tgt, const double* occ,
                             const PairDesc* pairs, int np, const TargetDesc* tgts, int nt, const Contrib* contribs,
                             const T* ktab, const cx<T>* tw, cx<T>* scratch, cx<T>* out, cudaStream_t st);
+// the same passes with compile-time FFT kernels for a cubic grid of side n (fixed_cubic)
+template <class T>
+void exchange_batch_fixed(int n, const cx<T>* src, const cx<T>* tgt, const double* occ, const PairDesc* pairs, int np,
+                          const TargetDesc* tgts, int nt, const Contrib* contribs, const T* ktab, const cx<T>* tw,
+                          cx<T>* scratch, cx<T>* out, cudaStream_t st);
 double kernel_value(const pt_kernel& k, double G2);
 
 bool exchange64_applies(const pt_grid& g);

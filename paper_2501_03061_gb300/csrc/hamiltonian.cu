@@ -8,9 +8,15 @@
 #include <algorithm>
 
 #include "fft.cuh"
+#include "fft_fixed.cuh"
 #include "internal.h"
 
 namespace pt {
+
+// compile-time-size passes for cubic grids (hamiltonian_fixed.cu)
+template <class T>
+void apply_h_batch_fixed(int n, const cx<T>* psi, const double* vloc, const cx<T>* X, double alpha, int j0, int nb,
+                         cx<T>* scratch, const double* g2d, double ecut, const cx<T>* tw, cx<T>* out, cudaStream_t st);
 
 namespace {
 
@@ -151,6 +157,12 @@ void apply_h_t(pt_ctx* ctx, const cx<T>* psi, int M, cx<T>* out, const double* v
   int mb = int(std::max<size_t>(1, budget / (2 * field)));
   mb = std::min(mb, M);
   cx<T>* scratch = static_cast<cx<T>*>(ctx->get("h_scratch", 2 * size_t(mb) * field));
+  if (fixed_cubic(g)) {
+    for (int j0 = 0; j0 < M; j0 += mb)
+      apply_h_batch_fixed<T>(g.nx, psi, vloc, X, alpha, j0, std::min(mb, M - j0), scratch,
+                             static_cast<const double*>(ft.g2d), ecut, static_cast<const cx<T>*>(ft.tw), out, st);
+    return;
+  }
   set_attrs<T>();
   const size_t one = 3 * kMaxDim * sizeof(cx<T>) + tile_bytes(sizeof(cx<T>));
   const size_t two = one + tile_bytes(sizeof(cx<T>));

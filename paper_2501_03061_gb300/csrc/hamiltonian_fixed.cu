@@ -1,0 +1,174 @@
+// H psi = P_sph[ -1/2 Lap psi + V_loc psi + alpha X ] (Eq. 1 with frozen V_Hxc + V_ext) on cubic
+// grids with a compile-time side N: the three passes of hamiltonian.cu (x/y plane transforms of
+// psi and of y = V_loc psi + alpha X; one column kernel that transforms both along z, combines
+// |G|^2/2 FFT(psi) + FFT(y) inside the sphere |G|^2/2 <= Ecut and transforms back along z; an
+// inverse plane pass), with the FFT stages of fft_fixed.cuh.
+#include <algorithm>
+
+#include "fft_fixed.cuh"
+#include "internal.h"
+
+namespace pt {
+
+namespace {
+
+constexpr int FT = 256;
+
+template <int N, class T>
+constexpr size_t tile_bytes_n() {
+  return size_t(N) * kPitch<N> * sizeof(cx<T>);
+}
+
+// item k of the batch: psi_{j0+k/2} (k even) or y_{j0+k/2} = V_loc psi + alpha X (k odd)
+template <int N, class T>
+__global__ void __launch_bounds__(FT) k_hx_fwd_plane(const cx<T>* __restrict__ psi, const double* __restrict__ vloc,
+                                                     const cx<T>* __restrict__ X, T alpha, int j0,
+                                                     cx<T>* __restrict__ scratch, const cx<T>* __restrict__ twg) {
+  extern __shared__ unsigned char smem_raw[];
+  cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
+  cx<T>* tw = buf + N * kPitch<N>;
+  constexpr int PL = N * N;
+  constexpr size_t NG = size_t(N) * N * N;
+  const int z = blockIdx.x, k = blockIdx.y;
+  for (int t = threadIdx.x; t < N; t += FT) tw[t] = twg[t];
+  const size_t off = size_t(j0 + (k >> 1)) * NG + size_t(z) * PL;
+  const cx<T>* f = psi + off;
+  if (k & 1) {
+    const double* v = vloc + size_t(z) * PL;
+    const cx<T>* xx = X ? X + off : nullptr;
+#pragma unroll 4
+    for (int e = threadIdx.x; e < PL; e += FT) {
+      const int yy = e / N, x = e - yy * N;
+      cx<T> val = f[e] * T(v[e]);
+      if (xx) val = val + xx[e] * alpha;
+      buf[yy * kPitch<N> + x] = val;
+    }
+  } else {
+#pragma unroll 4
+    for (int e = threadIdx.x; e < PL; e += FT) {
+      const int yy = e / N, x = e - yy * N;
+      buf[yy * kPitch<N> + x] = f[e];
+    }
+  }
+  __syncthreads();
+  cfft_fast<N, false, FT>(buf, tw);
+  cfft_slow<N, false, FT>(buf, tw);
+  cx<T>* o = scratch + size_t(k) * NG + size_t(z) * PL;
+#pragma unroll 4
+  for (int e = threadIdx.x; e < PL; e += FT) {
+    const int yy = e / N, x = e - yy * N;
+    o[e] = buf[yy * kPitch<N> + x];
+  }
+}
+
+template <int N, class T>
+__global__ void __launch_bounds__(FT) k_hx_column(cx<T>* __restrict__ scratch, const double* __restrict__ g2,
+                                                  double ecut, T inv_ng, const cx<T>* __restrict__ twg) {
+  extern __shared__ unsigned char smem_raw[];
+  cx<T>* ba = reinterpret_cast<cx<T>*>(smem_raw);
+  cx<T>* bb = ba + N * kPitch<N>;
+  cx<T>* tw = bb + N * kPitch<N>;
+  constexpr size_t NG = size_t(N) * N * N;
+  const int yrow = blockIdx.x, j = blockIdx.y;
+  for (int t = threadIdx.x; t < N; t += FT) tw[t] = twg[t];
+  cx<T>* fa = scratch + size_t(2 * j) * NG;
+  cx<T>* fb = fa + NG;
+#pragma unroll 4
+  for (int e = threadIdx.x; e < N * N; e += FT) {
+    const int z = e / N, x = e - z * N;
+    const size_t gi = (size_t(z) * N + yrow) * N + x;
+    ba[z * kPitch<N> + x] = fa[gi];
+    bb[z * kPitch<N> + x] = fb[gi];
+  }
+  __syncthreads();
+  cfft_slow<N, false, FT>(ba, tw);
+  cfft_slow<N, false, FT>(bb, tw);
+  // |G|^2 and the sphere test in FP64 so that the cutoff boundary does not depend on the precision
+  const double* g2x = g2;
+  const double* g2y = g2 + N;
+  const double* g2z = g2 + 2 * N;
+#pragma unroll 4
+  for (int e = threadIdx.x; e < N * N; e += FT) {
+    const int z = e / N, x = e - z * N;
+    const double half = 0.5 * (g2x[x] + g2y[yrow] + g2z[z]);
+    cx<T> v = czero<T>();
+    if (half <= ecut) v = (ba[z * kPitch<N> + x] * T(half) + bb[z * kPitch<N> + x]) * inv_ng;
+    ba[z * kPitch<N> + x] = v;
+  }
+  __syncthreads();
+  cfft_slow<N, true, FT>(ba, tw);
+#pragma unroll 4
+  for (int e = threadIdx.x; e < N * N; e += FT) {
+    const int z = e / N, x = e - z * N;
+    fa[(size_t(z) * N + yrow) * N + x] = ba[z * kPitch<N> + x];
+  }
+}
+
+template <int N, class T>
+__global__ void __launch_bounds__(FT) k_hx_inv_plane(const cx<T>* __restrict__ scratch, int j0, cx<T>* __restrict__ out,
+                                                     const cx<T>* __restrict__ twg) {
+  extern __shared__ unsigned char smem_raw[];
+  cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
+  cx<T>* tw = buf + N * kPitch<N>;
+  constexpr int PL = N * N;
+  constexpr size_t NG = size_t(N) * N * N;
+  const int z = blockIdx.x, j = blockIdx.y;
+  for (int t = threadIdx.x; t < N; t += FT) tw[t] = twg[t];
+  const cx<T>* f = scratch + size_t(2 * j) * NG + size_t(z) * PL;
+#pragma unroll 4
+  for (int e = threadIdx.x; e < PL; e += FT) {
+    const int yy = e / N, x = e - yy * N;
+    buf[yy * kPitch<N> + x] = f[e];
+  }
+  __syncthreads();
+  cfft_slow<N, true, FT>(buf, tw);
+  cfft_fast<N, true, FT>(buf, tw);
+  cx<T>* o = out + size_t(j0 + j) * NG + size_t(z) * PL;
+#pragma unroll 4
+  for (int e = threadIdx.x; e < PL; e += FT) {
+    const int yy = e / N, x = e - yy * N;
+    o[e] = buf[yy * kPitch<N> + x];
+  }
+}
+
+template <int N, class T>
+void h_batch_n(const cx<T>* psi, const double* vloc, const cx<T>* X, T alpha, int j0, int nb, cx<T>* scratch,
+               const double* g2d, double ecut, const cx<T>* tw, cx<T>* out, cudaStream_t st) {
+  static bool done = false;
+  const size_t one = tile_bytes_n<N, T>() + N * sizeof(cx<T>);
+  const size_t two = 2 * tile_bytes_n<N, T>() + N * sizeof(cx<T>);
+  if (!done) {
+    PT_CUDA_CHECK(cudaFuncSetAttribute(k_hx_fwd_plane<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(one)));
+    PT_CUDA_CHECK(cudaFuncSetAttribute(k_hx_inv_plane<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(one)));
+    PT_CUDA_CHECK(cudaFuncSetAttribute(k_hx_column<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(two)));
+    done = true;
+  }
+  constexpr double ng = double(N) * N * N;
+  PT_LAUNCH((k_hx_fwd_plane<N, T>), dim3(N, 2 * nb), FT, one, st, psi, vloc, X, alpha, j0, scratch, tw);
+  PT_LAUNCH((k_hx_column<N, T>), dim3(N, nb), FT, two, st, scratch, g2d, ecut, T(1.0 / ng), tw);
+  PT_LAUNCH((k_hx_inv_plane<N, T>), dim3(N, nb), FT, one, st, scratch, j0, out, tw);
+}
+
+}  // namespace
+
+template <class T>
+void apply_h_batch_fixed(int n, const cx<T>* psi, const double* vloc, const cx<T>* X, double alpha, int j0, int nb,
+                         cx<T>* scratch, const double* g2d, double ecut, const cx<T>* tw, cx<T>* out, cudaStream_t st) {
+  switch (n) {
+#define PT_CASE(s)                                                                                     \
+  case s:                                                                                              \
+    h_batch_n<s, T>(psi, vloc, X, T(alpha), j0, nb, scratch, g2d, ecut, tw, out, st);                  \
+    return;
+    PT_FIXED_SIZES(PT_CASE)
+#undef PT_CASE
+    default:
+      fail(PT_INVALID_ARG, "no compile-time FFT kernels for this grid side");
+  }
+}
+
+template void apply_h_batch_fixed<float>(int, const c64*, const double*, const c64*, double, int, int, c64*,
+                                         const double*, double, const c64*, c64*, cudaStream_t);
+template void apply_h_batch_fixed<double>(int, const c128*, const double*, const c128*, double, int, int, c128*,
+                                          const double*, double, const c128*, c128*, cudaStream_t);
+
+}  // namespace pt
