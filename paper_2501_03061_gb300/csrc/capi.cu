@@ -157,6 +157,10 @@ pt_status pt_set_option(pt_ctx* ctx, const char* key, double value) {
       (std::string(key) == "graphs" ? ctx->use_graphs : ctx->autotune) = value != 0.0 ? 1 : 0;
       return PT_OK;
     }
+    if (std::string(key) == "exchange64_engine") {
+      ctx->exchange64_engine = value != 0.0 ? 1 : 0;
+      return PT_OK;
+    }
     if (std::string(key) == "tc_period") {
       if (value < 1 || value > 64) pt::fail(PT_INVALID_ARG, "tc_period must be in [1, 64]");
       ctx->tc_period = int(value);

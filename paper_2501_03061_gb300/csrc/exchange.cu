@@ -270,7 +270,7 @@ long long exchange_t(pt_ctx* ctx, const cx<T>* src, const double* occ, int N, co
   const size_t budget = ctx->budget_override ? ctx->budget_override : exchange_scratch_budget(ctx);
   int B = int(std::floor(std::sqrt(double(std::max<size_t>(1, budget / field)))));
   B = std::max(1, std::min(B, std::max(N, M)));
-  if (exchange64_applies(g) && sizeof(T) == 4) B = std::min(B, 6);
+  if (exchange64_applies(g) && ctx->exchange64_engine == 0 && sizeof(T) == 4) B = std::min(B, 6);
   char key[128];
   snprintf(key, sizeof(key), "sched:%d:%d:%d:%d", N, M, int(sym), B);
   auto it = ctx->caches.find(key);
@@ -281,14 +281,12 @@ long long exchange_t(pt_ctx* ctx, const cx<T>* src, const double* occ, int N, co
   } else {
     sch = std::static_pointer_cast<ScheduleImpl>(it->second);
   }
-  if (exchange64_applies(g)) {
-    if constexpr (sizeof(T) == 4) {
+  if constexpr (sizeof(T) == 4) {
+    if (exchange64_applies(g) && ctx->exchange64_engine == 0) {
       exchange64_tma(ctx, *sch, src, occ, tgt, M, out, ktab, static_cast<const cx<T>*>(ft.tw), st);
       if (!ctx->defer_checks) exchange_check(ctx, st);
-    } else {
-      exchange64<T>(ctx, *sch, src, occ, tgt, out, ktab, static_cast<const cx<T>*>(ft.tw), st);
+      return sch->total_pairs;
     }
-    return sch->total_pairs;
   }
   cx<T>* scratch = static_cast<cx<T>*>(ctx->get("exchange_scratch", size_t(sch->max_pairs) * field));
   const cx<T>* twg = static_cast<const cx<T>*>(ft.tw);
@@ -339,6 +337,8 @@ template void exchange_batch_generic<double>(const GridPlan&, const c128*, const
                                              const double*, const c128*, c128*, c128*, cudaStream_t);
 
 size_t exchange_scratch_budget(const pt_ctx* ctx) { return ctx->scratch_budget; }
+
+bool exchange64_applies(const pt_grid& g) { return g.nx == 64 && g.ny == 64 && g.nz == 64; }
 
 void exchange_check(pt_ctx* ctx, cudaStream_t st) {
   int* err = static_cast<int*>(ctx->get("exchange_err", sizeof(int)));

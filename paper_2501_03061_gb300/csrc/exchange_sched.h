@@ -66,8 +66,5 @@ void exchange64_tma(pt_ctx* ctx, const ScheduleImpl& sch, const c64* src, const 
                     c64* out, const float* ktab, const c64* tw, cudaStream_t st);
 // synchronise st and fail with PT_TIMEOUT if a bounded device wait expired
 void exchange_check(pt_ctx* ctx, cudaStream_t st);
-template <class T>
-void exchange64(pt_ctx* ctx, const ScheduleImpl& sch, const cx<T>* src, const double* occ, const cx<T>* tgt,
-                cx<T>* out, const T* ktab, const cx<T>* tw, cudaStream_t st);
 
 }  // namespace pt
