@@ -54,7 +54,7 @@ void ace_from_w(pt_ctx* ctx, const void* W, const void* phi, int N, const pt_gri
   PT_CUDA_CHECK(cudaMemcpyAsync(&h_info, info, sizeof(int), cudaMemcpyDeviceToHost, st));
   PT_CUDA_CHECK(cudaStreamSynchronize(st));
   if (h_info) fail(PT_NOT_PD, "ACE: -<phi|V_x phi> is not positive definite (pivot " + std::to_string(h_info) + ")");
-  tri_inv_lower(L, N, Li, st);
+  tri_inv_lower(ctx, L, N, Li, st);
   conj_transpose(Li, N, LiH, st);
   // xi_k = sum_j conj(Linv[k][j]) W_j  ->  rotate with Bm = Linv^H
   if (prec == PT_FP64)

@@ -220,45 +220,67 @@ __global__ void __launch_bounds__(256) k_chol_diag(c128* __restrict__ A, int N, 
                                                    c128* __restrict__ Winv, int* __restrict__ info) {
   __shared__ c128 a[CB][CB + 1];
   __shared__ c128 x[CB][CB + 1];
+  // lower triangle (i >= j) listed column by column: entry (j, i) at j*bs - j(j-1)/2 + (i - j), so
+  // the trailing triangle of step k (j > k) is one contiguous range and no thread idles on the
+  // upper half
+  __shared__ unsigned short tri[CB * (CB + 1) / 2];
   if (*info) return;
   const int tid = threadIdx.x;
   for (int e = tid; e < bs * bs; e += blockDim.x) {
     const int i = e / bs, j = e % bs;
     a[i][j] = A[size_t(kb + i) * N + kb + j];
+    if (i >= j) tri[j * bs - j * (j - 1) / 2 + (i - j)] = static_cast<unsigned short>((j << 8) | i);
   }
   __syncthreads();
+  const int tri_end = bs * (bs + 1) / 2;
+  // FP64 square roots and divisions are long instruction sequences on the FP64 pipe: one thread
+  // takes them and broadcasts the results
+  __shared__ double rdiag[CB];
+  __shared__ double s_rk;
   for (int k = 0; k < bs; ++k) {
     const double piv = a[k][k].re;
     if (!(piv > 0.0) || !isfinite(piv)) {
       if (tid == 0) *info = kb + k + 1;
       return;  // uniform: every thread read the same pivot
     }
-    const double dk = sqrt(piv);
     __syncthreads();
-    if (tid == 0) a[k][k] = c128{dk, 0.0};
-    for (int i = k + 1 + tid; i < bs; i += blockDim.x) a[i][k] = a[i][k] * (1.0 / dk);
+    if (tid == 0) {
+      const double dk = sqrt(piv);
+      a[k][k] = c128{dk, 0.0};
+      s_rk = 1.0 / dk;
+      rdiag[k] = s_rk;
+    }
     __syncthreads();
-    for (int e = tid; e < bs * bs; e += blockDim.x) {
-      const int i = e / bs, j = e % bs;
-      if (j > k && i >= j) a[i][j] = a[i][j] - cmulc(a[j][k], a[i][k]);
+    const double rk = s_rk;
+    for (int i = k + 1 + tid; i < bs; i += blockDim.x) a[i][k] = a[i][k] * rk;
+    __syncthreads();
+    for (int e = (k + 1) * bs - (k + 1) * k / 2 + tid; e < tri_end; e += blockDim.x) {
+      const int i = tri[e] & 255, j = tri[e] >> 8;
+      a[i][j] = a[i][j] - cmulc(a[j][k], a[i][k]);
     }
     __syncthreads();
   }
-  // inverse of the lower-triangular factor, one column per thread
-  if (tid < bs) {
-    const int j = tid;
+  // inverse X of the lower-triangular factor, one row at a time with all threads:
+  //   X[i][i] = 1 / L[i][i],  X[i][j] = -(sum_{p=j}^{i-1} L[i][p] X[p][j]) / L[i][i]  (j < i);
+  // thread (part, j) sums every 8th p, the 8 parts meet in shared memory
+  __shared__ c128 red[8][CB];
+  {
+    const int j = tid & (CB - 1), part = tid >> 5;
     for (int i = 0; i < bs; ++i) {
-      if (i < j) {
-        x[i][j] = czero<double>();
-        continue;
+      c128 acc = czero<double>();
+      if (j < i)
+        for (int p = j + part; p < i; p += 8) acc = acc + cmul(a[i][p], x[p][j]);
+      red[part][j] = acc;
+      __syncthreads();
+      if (part == 0) {
+        c128 t = czero<double>();
+        for (int q = 0; q < 8; ++q) t = t + red[q][j];
+        const double inv = rdiag[i];
+        x[i][j] = j < i ? t * (-inv) : (j == i ? c128{inv, 0.0} : czero<double>());
       }
-      c128 acc = c128{i == j ? 1.0 : 0.0, 0.0};
-      for (int p = j; p < i; ++p) acc = acc - cmul(a[i][p], x[p][j]);
-      const c128 lii = a[i][i];
-      x[i][j] = acc * (1.0 / lii.re);
+      __syncthreads();
     }
   }
-  __syncthreads();
   for (int e = tid; e < bs * bs; e += blockDim.x) {
     const int i = e / bs, j = e % bs;
     if (j <= i) A[size_t(kb + i) * N + kb + j] = a[i][j];
@@ -318,24 +340,6 @@ __global__ void k_chol_finish(const c128* __restrict__ A, int N, c128* __restric
   if (e >= N * N || *info) return;
   const int i = e / N, j = e % N;
   L[e] = (j > i) ? czero<double>() : A[e];
-}
-
-// X = L^{-1}, column c per CTA (forward substitution, column-oriented)
-__global__ void k_tri_inv_lower(const c128* __restrict__ L, int N, c128* __restrict__ X) {
-  extern __shared__ c128 b[];
-  const int c = blockIdx.x;
-  for (int i = threadIdx.x; i < N; i += blockDim.x) b[i] = c128{i == c ? 1.0 : 0.0, 0.0};
-  __syncthreads();
-  for (int k = c; k < N; ++k) {
-    const c128 lkk = L[size_t(k) * N + k];
-    const double den = lkk.re * lkk.re + lkk.im * lkk.im;
-    const c128 xk = cmul(b[k], c128{lkk.re / den, -lkk.im / den});
-    __syncthreads();
-    if (threadIdx.x == 0) b[k] = xk;
-    for (int i = k + 1 + threadIdx.x; i < N; i += blockDim.x) b[i] = b[i] - cmul(L[size_t(i) * N + k], xk);
-    __syncthreads();
-  }
-  for (int i = threadIdx.x; i < N; i += blockDim.x) X[size_t(i) * N + c] = (i < c) ? czero<double>() : b[i];
 }
 
 // out = U diag(f(lam)) (scale columns), f = lam^power
@@ -438,10 +442,12 @@ void heev(pt_ctx* ctx, const c128* S, int N, c128* Q, double* d, cudaStream_t st
 }
 
 void cholesky(pt_ctx* ctx, c128* A, int N, c128* L, int* info, cudaStream_t st) {
-  c128* winv = static_cast<c128*>(ctx->get("chol_winv", size_t(CB) * CB * sizeof(c128)));
+  // the inverses of all diagonal blocks are kept (rows kb..kb+bs of an N x CB array) for tri_inv_lower
+  c128* winv_all = static_cast<c128*>(ctx->get("chol_winv_all", size_t(N) * CB * sizeof(c128)));
   PT_CUDA_CHECK(cudaMemsetAsync(info, 0, sizeof(int), st));
   for (int kb = 0; kb < N; kb += CB) {
     const int bs = std::min(CB, N - kb);
+    c128* winv = winv_all + size_t(kb) * CB;
     PT_LAUNCH(k_chol_diag, 1, 256, 0, st, A, N, kb, bs, winv, info);
     const int rest = N - kb - bs;
     if (rest <= 0) break;
@@ -452,8 +458,32 @@ void cholesky(pt_ctx* ctx, c128* A, int N, c128* L, int* info, cudaStream_t st) 
   PT_LAUNCH(k_chol_finish, (N * N + 255) / 256, 256, 0, st, A, N, L, info);
 }
 
-void tri_inv_lower(const c128* L, int N, c128* X, cudaStream_t st) {
-  PT_LAUNCH(k_tri_inv_lower, N, 128, size_t(N) * sizeof(c128), st, L, N, X);
+// X = 0 except the diagonal CB-blocks, which take the inverses cholesky() kept
+__global__ void k_tri_inv_leaves(const c128* __restrict__ winv_all, int N, c128* __restrict__ X) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= N * N) return;
+  const int i = e / N, j = e % N;
+  const int bi = i / CB, bj = j / CB;
+  X[e] = (bi == bj) ? winv_all[size_t(i) * CB + (j - bj * CB)] : czero<double>();
+}
+
+void tri_inv_lower(pt_ctx* ctx, const c128* L, int N, c128* X, cudaStream_t st) {
+  // Bottom-up block inversion: for [L11 0; L21 L22] with X11 = L11^{-1}, X22 = L22^{-1} known,
+  // X21 = -X22 (L21 X11).  Leaves are the CB x CB inverses from the preceding cholesky().
+  const c128* winv_all = static_cast<const c128*>(ctx->get("chol_winv_all", size_t(N) * CB * sizeof(c128)));
+  c128* T = static_cast<c128*>(ctx->get("tri_inv_T", size_t(N) * N * sizeof(c128)));
+  PT_LAUNCH(k_tri_inv_leaves, (N * N + 255) / 256, 256, 0, st, winv_all, N, X);
+  for (int s = CB; s < N; s *= 2) {
+    for (int i0 = 0; i0 + s < N; i0 += 2 * s) {
+      const int n1 = s, n2 = std::min(s, N - i0 - s);
+      const c128* X11 = X + size_t(i0) * N + i0;
+      const c128* X22 = X + size_t(i0 + s) * N + (i0 + s);
+      const c128* L21 = L + size_t(i0 + s) * N + i0;
+      c128* X21 = X + size_t(i0 + s) * N + i0;
+      zgemm('N', 'N', n2, n1, n1, c128{1, 0}, L21, N, X11, N, c128{0, 0}, T, n1, st);
+      zgemm('N', 'N', n2, n1, n2, c128{-1, 0}, X22, N, T, n1, c128{0, 0}, X21, N, st);
+    }
+  }
 }
 
 void scale_cols_pow(const c128* U, const double* lam, int N, double power, c128* out, int* info, cudaStream_t st) {

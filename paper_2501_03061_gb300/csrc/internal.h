@@ -58,7 +58,8 @@ void heev(pt_ctx* ctx, const c128* S, int N, c128* Q, double* d, cudaStream_t st
           const c128* Q0 = nullptr);
 // A (overwritten) = L L^* ; L written to a separate buffer; *info = k+1 on a bad pivot k.
 void cholesky(pt_ctx* ctx, c128* A, int N, c128* L, int* info, cudaStream_t st);
-void tri_inv_lower(const c128* L, int N, c128* X, cudaStream_t st);
+// X = L^{-1} for the factor of the preceding cholesky(ctx, ...) (uses its diagonal-block inverses)
+void tri_inv_lower(pt_ctx* ctx, const c128* L, int N, c128* X, cudaStream_t st);
 void scale_cols_pow(const c128* U, const double* lam, int N, double power, c128* out, int* info, cudaStream_t st);
 void small_solve(const double* G, const double* rhs, int m, double reg, double* x, cudaStream_t st);
 void set_identity(c128* A, int N, cudaStream_t st);

@@ -316,7 +316,7 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
       tm.begin(PH_SUBNN);
       // S^{-1} A = L^{-*} (L^{-1} A)
       cholesky(ctx, Sm, N, Lc, info, st);
-      tri_inv_lower(Lc, N, Li, st);
+      tri_inv_lower(ctx, Lc, N, Li, st);
       zgemm('N', 'N', N, N, N, c128{1, 0}, Li, N, A, N, c128{0, 0}, T1, N, st);
       zgemm('C', 'N', N, N, N, c128{1, 0}, Li, N, T1, N, c128{0, 0}, SinvA, N, st);
       tm.end();

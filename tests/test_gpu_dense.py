@@ -19,10 +19,11 @@ def ctx():
     c.close()
 
 
-@pytest.mark.parametrize("N", [31, 32, 33, 70, 97])
+@pytest.mark.parametrize("N", [31, 32, 33, 70, 97, 160, 200])
 def test_ace_from_w_multi_panel_cholesky(ctx, N):
-    """build_ace_from runs the blocked Cholesky (32-wide panels) and the triangular inverse; the
-    resulting xi must match the oracle's construction for N across panel boundaries."""
+    """build_ace_from runs the blocked Cholesky (32-wide panels) and the bottom-up blocked
+    triangular inverse; the resulting xi must match the oracle's construction for N across panel
+    boundaries and merge levels (N = 200: blocks of 32 merged into 64, 128 and a partial 72)."""
     rng = np.random.default_rng(N)
     cell = synth.cubic(12, 9.0)
     phi = synth.random_orbitals(rng, cell, N, ecut=20.0)
