@@ -4,7 +4,7 @@
 //            C: N1 x N2 complex128 row-major).  Split over r, FP64 reduction of the splits.
 //   rotate:  Out_j(r) = alpha * sum_k A_k(r) Bm[k][j] + sum_e c_e E_e,j(r)
 //            (Bm: N1 x N2 complex128 row-major, converted to the orbital precision).
-//   lincomb, multi_dot, norms: streaming kernels over orbital blocks.
+//   lincomb, sqnorms: streaming kernels over orbital blocks.
 #include <algorithm>
 
 #include "common.cuh"
@@ -287,59 +287,7 @@ __global__ void k_potential_apply(cx<T>* __restrict__ out, const cx<T>* __restri
   }
 }
 
-// Re sum conj(u_a) v over an orbital segment (weight w1, precision T) and a complex128 segment
-// (weight w2); one partial per block and vector, reduced by k_reduce_dots.
-constexpr int DOT_MAX = 24;
-struct DotArgs {
-  const void* u1[DOT_MAX];
-  const c128* u2[DOT_MAX];
-};
-
-template <class T>
-__global__ void k_multi_dot(DotArgs args, int m, const cx<T>* __restrict__ v1, size_t n1, const c128* __restrict__ v2,
-                            size_t n2, double w1, double w2, double* __restrict__ part) {
-  __shared__ double red[DOT_MAX][8];
-  Acc<T> s1[DOT_MAX];
-  double s[DOT_MAX];
-  const size_t stride = size_t(gridDim.x) * blockDim.x;
-  for (size_t e = size_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n1; e += stride) {
-    const cx<T> vv = v1[e];
-    // fixed trip count keeps the accumulators in registers; the guard skips absent vectors
-#pragma unroll
-    for (int a = 0; a < DOT_MAX; ++a) {
-      if (a < m) {
-        const cx<T> uu = static_cast<const cx<T>*>(args.u1[a])[e];
-        s1[a].add(fma(uu.re, vv.re, uu.im * vv.im));
-      }
-    }
-  }
-#pragma unroll
-  for (int a = 0; a < DOT_MAX; ++a) s[a] = w1 * s1[a].value();
-  for (size_t e = size_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n2; e += stride) {
-    const c128 vv = v2[e];
-#pragma unroll
-    for (int a = 0; a < DOT_MAX; ++a) {
-      if (a < m) {
-        const c128 uu = args.u2[a][e];
-        s[a] += w2 * (uu.re * vv.re + uu.im * vv.im);
-      }
-    }
-  }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int a = 0; a < DOT_MAX; ++a) {
-    double x = s[a];
-    for (int off = 16; off; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
-    if (lane == 0) red[a][warp] = x;
-  }
-  __syncthreads();
-  if (threadIdx.x < m) {
-    double x = 0;
-    for (int w = 0; w < int(blockDim.x >> 5); ++w) x += red[threadIdx.x][w];
-    part[size_t(threadIdx.x) * gridDim.x + blockIdx.x] = x;
-  }
-}
-
+// one value per vector from the per-block partials part[a * nblk + b]
 __global__ void k_reduce_dots(const double* __restrict__ part, int nblk, int m, double* __restrict__ out) {
   const int a = blockIdx.x;
   double x = 0;
@@ -432,22 +380,6 @@ void potential_apply(pt_ctx* ctx, cx<T>* out, const cx<T>* psi, const double* v,
   PT_LAUNCH(k_potential_apply<T>, stream_blocks(ctx, n, 256), 256, 0, st, out, psi, v, ng, n, X, T(a));
 }
 
-template <class T>
-void multi_dot(pt_ctx* ctx, const void* const* u1, const c128* const* u2, int m, const cx<T>* v1, size_t n1,
-               const c128* v2, size_t n2, double w1, double w2, double* out, cudaStream_t st) {
-  if (m > DOT_MAX) fail(PT_INVALID_ARG, "too many vectors in multi_dot");
-  if (m == 0) return;
-  DotArgs args{};
-  for (int a = 0; a < m; ++a) {
-    args.u1[a] = u1 ? u1[a] : nullptr;
-    args.u2[a] = u2 ? u2[a] : nullptr;
-  }
-  const int threads = 256;
-  const int nblk = std::max(1, std::min(ctx->num_sms * 4, int((n1 + threads - 1) / threads)));
-  double* part = static_cast<double*>(ctx->get("dot_parts", size_t(DOT_MAX) * nblk * sizeof(double)));
-  PT_LAUNCH(k_multi_dot<T>, nblk, threads, 0, st, args, m, v1, n1, v2, n2, w1, w2, part);
-  PT_LAUNCH(k_reduce_dots, m, 256, 0, st, part, nblk, m, out);
-}
 
 template void gram<float>(pt_ctx*, const c64*, const c64*, int, int, size_t, double, c128*, cudaStream_t, bool);
 template void gram<double>(pt_ctx*, const c128*, const c128*, int, int, size_t, double, c128*, cudaStream_t, bool);
@@ -461,9 +393,76 @@ template void potential_apply<float>(pt_ctx*, c64*, const c64*, const double*, s
                                      cudaStream_t);
 template void potential_apply<double>(pt_ctx*, c128*, const c128*, const double*, size_t, int, const c128*, double,
                                       cudaStream_t);
-template void multi_dot<float>(pt_ctx*, const void* const*, const c128* const*, int, const c64*, size_t,
-                               const c128*, size_t, double, double, double*, cudaStream_t);
-template void multi_dot<double>(pt_ctx*, const void* const*, const c128* const*, int, const c128*, size_t,
-                                const c128*, size_t, double, double, double*, cudaStream_t);
+// ---------------------------------------------------------------- squared norms ----
+// out[q] = w1 ||a_q||^2 + w2 ||s_q||^2 for two two-segment vectors (q = 0, 1): one streaming pass
+// with 16-byte loads, compensated per-thread sums in the orbital precision, FP64 across threads.
+constexpr int NRT = 256;
+
+template <class T>
+__global__ void __launch_bounds__(NRT) k_sqnorms(const cx<T>* __restrict__ a0, const cx<T>* __restrict__ a1, size_t n1,
+                                                 const c128* __restrict__ s0, const c128* __restrict__ s1, size_t n2,
+                                                 double w1, double w2, int vec, double* __restrict__ part) {
+  Acc<T> acc[2];
+  const size_t tid = size_t(blockIdx.x) * blockDim.x + threadIdx.x, stride = size_t(gridDim.x) * blockDim.x;
+  if (sizeof(T) == 4 && vec) {
+    // two complex64 per float4
+    const size_t n4 = n1 / 2;
+    const float4* p0 = reinterpret_cast<const float4*>(a0);
+    const float4* p1 = reinterpret_cast<const float4*>(a1);
+    for (size_t e = tid; e < n4; e += stride) {
+      const float4 u = p0[e], v = p1[e];
+      acc[0].add(T(fmaf(u.x, u.x, fmaf(u.y, u.y, fmaf(u.z, u.z, u.w * u.w)))));
+      acc[1].add(T(fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, v.w * v.w)))));
+    }
+    if ((n1 & 1) && tid == 0) {
+      const cx<T> u = a0[n1 - 1], v = a1[n1 - 1];
+      acc[0].add(u.re * u.re + u.im * u.im);
+      acc[1].add(v.re * v.re + v.im * v.im);
+    }
+  } else {
+    for (size_t e = tid; e < n1; e += stride) {
+      const cx<T> u = a0[e], v = a1[e];
+      acc[0].add(u.re * u.re + u.im * u.im);
+      acc[1].add(v.re * v.re + v.im * v.im);
+    }
+  }
+  double s[2] = {w1 * acc[0].value(), w1 * acc[1].value()};
+  for (size_t e = tid; e < n2; e += stride) {
+    const c128 u = s0[e], v = s1[e];
+    s[0] += w2 * (u.re * u.re + u.im * u.im);
+    s[1] += w2 * (v.re * v.re + v.im * v.im);
+  }
+  __shared__ double red[2][NRT / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    double x = s[q];
+    for (int off = 16; off; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+    if (lane == 0) red[q][warp] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    double x = 0;
+    for (int w = 0; w < NRT / 32; ++w) x += red[threadIdx.x][w];
+    part[size_t(threadIdx.x) * gridDim.x + blockIdx.x] = x;
+  }
+}
+
+template <class T>
+void sqnorms(pt_ctx* ctx, const cx<T>* a0, const c128* s0, const cx<T>* a1, const c128* s1, size_t n1, size_t n2,
+             double w1, double w2, double* out, cudaStream_t st) {
+  const int nblk = ctx->num_sms * 4;
+  double* part = static_cast<double*>(ctx->get("sqnorm_part", size_t(2) * nblk * sizeof(double)));
+  const int vec = ((reinterpret_cast<uintptr_t>(a0) | reinterpret_cast<uintptr_t>(a1)) % 16) == 0;
+  PT_LAUNCH(k_sqnorms<T>, nblk, NRT, 0, st, a0, a1, n1, s0, s1, n2, w1, w2, vec, part);
+  PT_LAUNCH(k_reduce_dots, 2, 256, 0, st, part, nblk, 2, out);
+}
+
+template void sqnorms<float>(pt_ctx*, const c64*, const c128*, const c64*, const c128*, size_t, size_t, double, double,
+                             double*, cudaStream_t);
+template void sqnorms<double>(pt_ctx*, const c128*, const c128*, const c128*, const c128*, size_t, size_t, double,
+                              double, double*, cudaStream_t);
+
+
 
 }  // namespace pt

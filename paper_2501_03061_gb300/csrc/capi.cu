@@ -52,6 +52,7 @@ void pt_ctx::release_all() {
   bufs.clear();
   held = 0;
   tc_err_clean = false;
+  ptim_q_n = 0;
   // captured graphs hold pointers into the freed workspace
   for (auto it = caches.begin(); it != caches.end();) {
     if (it->first.rfind("graph:", 0) == 0) it = caches.erase(it);

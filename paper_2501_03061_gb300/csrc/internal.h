@@ -34,9 +34,11 @@ void lincomb(pt_ctx* ctx, cx<T>* out, size_t n, const Term* terms, int nterms, c
 template <class T>
 void potential_apply(pt_ctx* ctx, cx<T>* out, const cx<T>* psi, const double* v, size_t ng, int M, const cx<T>* X,
                      double a, cudaStream_t st);
+// out[0] = w1 ||a0||^2 + w2 ||s0||^2, out[1] = w1 ||a1||^2 + w2 ||s1||^2 (device doubles)
 template <class T>
-void multi_dot(pt_ctx* ctx, const void* const* u1, const c128* const* u2, int m, const cx<T>* v1, size_t n1,
-               const c128* v2, size_t n2, double w1, double w2, double* out, cudaStream_t st);
+void sqnorms(pt_ctx* ctx, const cx<T>* a0, const c128* s0, const cx<T>* a1, const c128* s1, size_t n1, size_t n2,
+             double w1, double w2, double* out, cudaStream_t st);
+
 
 // ---- tensor-core Gram (gram_tc.cu) ----
 void gram_tc(pt_ctx* ctx, const c64* A, const c64* B, int N1, int N2, size_t ng, double scale, c128* C,

@@ -126,16 +126,15 @@ struct Step {
 
   void* buf(const char* name, size_t bytes) { return ctx->get(name, bytes); }
 
-  // ||a||^2 of a two-segment vector with weight dV on the orbital segment (FP64 result on host)
-  double norm2(const cx<T>* phi, const c128* sig) {
+  // ||a||^2 and ||b||^2 (weight dV on the orbital segment, 1 on sigma) in one pass and one synchronisation
+  void norm2_pair(const cx<T>* aphi, const c128* asig, const cx<T>* bphi, const c128* bsig, double* ra, double* rb) {
     double* dev = static_cast<double*>(buf("ptim_norm", 2 * sizeof(double)));
-    const void* u1[1] = {phi};
-    const c128* u2[1] = {sig};
-    multi_dot<T>(ctx, u1, u2, 1, phi, n1, sig, n2, dV, 1.0, dev, st);
-    double h = 0;
-    PT_CUDA_CHECK(cudaMemcpyAsync(&h, dev, sizeof(double), cudaMemcpyDeviceToHost, st));
+    sqnorms<T>(ctx, aphi, asig, bphi, bsig, n1, n2, dV, 1.0, dev, st);
+    double h[2] = {0, 0};
+    PT_CUDA_CHECK(cudaMemcpyAsync(h, dev, sizeof(h), cudaMemcpyDeviceToHost, st));
     PT_CUDA_CHECK(cudaStreamSynchronize(st));
-    return h;
+    *ra = h[0];
+    *rb = h[1];
   }
 
   void midpoint(cx<T>* phih, c128* sigh, const cx<T>* phi, const cx<T>* phin, const c128* sig, const c128* sign) {
@@ -230,12 +229,14 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
     }
   } ev_guard{ev};
   // V_x[P_h] Phi_h through the sigma_h eigenbasis: (V_x phit) Q^*, phit = Phi_h Q
-  // sigma_h changes little between outer iterations: later eigensolves start from the last basis
-  bool have_q = false;
+  // sigma_h changes little between outer iterations and between steps: eigensolves start from the
+  // last basis the context holds (any unitary start is correct; a near one converges in a sweep or two)
   auto exchange_on_midpoint = [&](cx<T>* out, bool energy) {
     tm.begin(PH_EIG);
-    heev(ctx, sigh, N, Q, d, st, 30, have_q ? Q : nullptr);
-    have_q = true;
+    const bool warm = ctx->ptim_q_n == N;
+    ctx->ptim_q_n = 0;  // Q is being rewritten
+    heev(ctx, sigh, N, Q, d, st, 30, warm ? Q : nullptr);
+    ctx->ptim_q_n = N;
     tm.end();
     tm.begin(PH_ROT);
     rotate<T>(ctx, phih, Q, N, N, N, S.ng, c128{1, 0}, nullptr, 0, phit, st);
@@ -272,7 +273,8 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
       if (have_anchor) {
         PT_LAUNCH(k_diff<T>, sblocks, nthreads, 0, st, aphi, phih, aphi, S.n1);
         PT_LAUNCH(k_diff<double>, sblocks2, nthreads, 0, st, asig, sigh, asig, S.n2);
-        const double ch = S.norm2(aphi, asig), nr = S.norm2(phih, sigh);
+        double ch = 0, nr = 0;
+        S.norm2_pair(aphi, asig, phih, sigh, &ch, &nr);
         if (std::sqrt(ch / nr) < P.tol && inner_conv) {
           converged = true;
           break;
@@ -335,8 +337,8 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
       tm.begin(PH_AND);
       int h_info = 0;
       PT_CUDA_CHECK(cudaMemcpyAsync(&h_info, info, sizeof(int), cudaMemcpyDeviceToHost, st));
-      const double rr = S.norm2(rphi, rsig);  // synchronises st
-      const double xx = S.norm2(phi, sig);
+      double rr = 0, xx = 0;
+      S.norm2_pair(rphi, rsig, phi, sig, &rr, &xx);  // synchronises st
       if (h_info) fail(PT_NOT_PD, "PT-IM: overlap of the midpoint orbitals is not positive definite");
       const double res = std::sqrt(rr / xx);
       stv.residual = res;
@@ -424,7 +426,9 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
     if (Z != A) PT_CUDA_CHECK(cudaMemcpyAsync(A, Z, mb, cudaMemcpyDeviceToDevice, st));
     if (Y != Lc) PT_CUDA_CHECK(cudaMemcpyAsync(Lc, Y, mb, cudaMemcpyDeviceToDevice, st));
   } else {
+    ctx->ptim_q_n = 0;
     heev(ctx, Sm, N, Q, d, st);
+    ctx->ptim_q_n = N;
     scale_cols_pow(Q, d, N, -0.5, T1, info, st);
     zgemm('N', 'C', N, N, N, c128{1, 0}, T1, N, Q, N, c128{0, 0}, A, N, st);   // S^{-1/2}
     scale_cols_pow(Q, d, N, 0.5, T1, info, st);
