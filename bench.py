@@ -30,6 +30,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Vx·Ψ pair-FFTs/s and PT-IM steps/s vs plain FP64 GPU form; serve p50/p99"
+# DRAM bytes (read + write) per steady-state launch of the 64^3 FP32 exchange kernel, from an ncu
+# --set full capture of two launches with pair tiles of 4 x 4 orbitals (the tile the benchmark cell
+# uses); the kernel's device code is unchanged since that capture
+EXCHANGE64_TRAFFIC_PER_LAUNCH = 197.2e6
 UNIT = "PT-IM steps/s"
 WORKLOAD = "ptim_ace_step_64^3_N320_128site_L20.5"
 # model iteration counts used to scale a bounded CPU sample to one step: the paper's ~5 outer x ~13 inner
@@ -51,9 +55,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 form comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
-    ap.add_argument("--mode", default="step", choices=["step", "exchange", "serve", "batched"],
+    ap.add_argument("--mode", default="step",
+                    choices=["step", "exchange", "serve", "batched", "precision", "contractions"],
                     help="step: PT-IM steps (the benchmark); exchange: only V_x applications on the same cell "
-                         "(profiler captures of the exchange kernel)")
+                         "(profiler captures of the exchange kernel); serve / batched: configs 5 / 4 alone; "
+                         "precision: config 3 per-result errors; contractions: Gram/rotation engines at 64^3")
     ap.add_argument("--serve-window", type=float, default=15.0, help="seconds of arrivals per serving phase")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement in step mode")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
@@ -215,6 +221,99 @@ def run_exchange_only(args):
     print(json.dumps({"mode": "exchange", "N": args.N, "precision": args.precision, "ms_per_application": ms,
                       "pair_ffts_per_s": pairs / (ms / 1e3)}), flush=True)
     ctx.close()
+
+
+def precision_forms() -> dict:
+    """Config 3: the config-1 cell (24^3, N = 16) in the FP32 forms, each result's error against
+    the library's FP64 form on the same inputs (the FP64 form itself is held to the FP64 oracle at
+    1e-11 by the parity tests).  Results: W = V_x Psi, M = Psi^* W, xi, V_ACE Psi, E_x."""
+    import numpy as np
+    import torch
+
+    from paper_2501_03061_gb300 import api, synth
+
+    w = synth.exchange_small()
+    ctx = api.Context(0)
+    dv = w.cell.volume / w.cell.ng
+
+    def run(precision, tc):
+        ctx.set_option("tc_gram", tc)
+        dt = np.complex128 if precision == "fp64" else np.complex64
+        phi = torch.from_numpy(w.phi.astype(dt)).cuda()
+        occ = torch.from_numpy(w.occ).cuda()
+        W = ctx.apply_exchange(phi, occ, cell=w.cell, kernel=w.kernel, precision=precision)
+        M = ctx.overlap(phi, W, cell=w.cell, precision=precision)
+        ace = ctx.build_ace(phi, occ, cell=w.cell, kernel=w.kernel, precision=precision)
+        xi = ace.xi()
+        va = ctx.apply_ace(ace, phi)
+        ace.close()
+        ex = 2 * 0.125 * float(torch.sum(occ * torch.diagonal(M).real))
+        out = {k: v.cpu().numpy().astype(np.complex128) for k, v in (("W", W), ("M", M), ("xi", xi), ("Vace", va))}
+        out["Ex"] = ex
+        return out
+
+    try:
+        ref = run("fp64", 0)
+        res = {}
+        for name, prec, tc in (("fp32_cuda_cores", "fp32", 0), ("fp32_tensor_3xTF32", "fp32", 1),
+                               ("tf32_tensor", "tf32", 0)):
+            r = run(prec, tc)
+            e = {k: float(np.linalg.norm(r[k] - ref[k]) / np.linalg.norm(ref[k])) for k in ("W", "M", "xi", "Vace")}
+            e["Ex_Ha_per_atom"] = abs(r["Ex"] - ref["Ex"]) / w.natoms
+            res[name] = e
+    finally:
+        ctx.set_option("tc_gram", 0)
+        ctx.close()
+    return {"workload": "24^3 cell, L = 10, N = 16, kT = 0.01", "reference": "FP64 GPU form",
+            "errors": res, "note": "relative Frobenius errors per result; E_x absolute per atom (8 atoms)",
+            "dV": dv}
+
+
+def contraction_measurement() -> dict:
+    """Overlap (Hermitian and general) and rotation at 64^3, N = 320 in each engine: CUDA events
+    around 5 calls each, errors against the FP64 form of the same call."""
+    import torch
+
+    from paper_2501_03061_gb300 import api, synth
+
+    cell = synth.cubic(64, 20.5)
+    N = 320
+    g = torch.Generator(device="cuda")
+    g.manual_seed(5)
+    a = torch.randn((N, 64, 64, 64), dtype=torch.complex64, device="cuda", generator=g)
+    b = torch.randn((N, 64, 64, 64), dtype=torch.complex64, device="cuda", generator=g)
+    B = torch.randn((N, N), dtype=torch.complex128, device="cuda", generator=g) / N ** 0.5
+    ctx = api.Context(0)
+    res = {}
+    try:
+        refs = {}
+        a64 = a.to(torch.complex128)
+        refs["overlap_herm"] = ctx.overlap(a64, a64, cell=cell, precision="fp64")
+        refs["rotate"] = ctx.rotate(a64, B, cell=cell, precision="fp64")
+        b64 = b.to(torch.complex128)
+        refs["overlap_general"] = ctx.overlap(a64, b64, cell=cell, precision="fp64")
+        del a64, b64
+        torch.cuda.empty_cache()
+        calls = {"overlap_herm": lambda p: ctx.overlap(a, a, cell=cell, precision=p),
+                 "overlap_general": lambda p: ctx.overlap(a, b, cell=cell, precision=p),
+                 "rotate": lambda p: ctx.rotate(a, B, cell=cell, precision=p)}
+        for eng, prec, tc in (("cuda_cores_fp32", "fp32", 0), ("tensor_3xTF32", "fp32", 1), ("tensor_TF32", "tf32", 0)):
+            ctx.set_option("tc_gram", tc)
+            for name, f in calls.items():
+                out = f(prec)
+                torch.cuda.synchronize()
+                s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s.record()
+                for _ in range(5):
+                    out = f(prec)
+                e.record()
+                torch.cuda.synchronize()
+                err = float((out.to(torch.complex128) - refs[name]).norm() / refs[name].norm())
+                res[f"{name}/{eng}"] = {"ms": s.elapsed_time(e) / 5, "rel_error": err}
+    finally:
+        ctx.set_option("tc_gram", 0)
+        ctx.close()
+    return {"workload": "64^3 grid, N = 320 (random complex fields), B = N x N", "results": res}
 
 
 def serve_measurement(window_s: float, slots: int = 6) -> dict:
@@ -419,6 +518,13 @@ def run_gb300(args):
     ms_per_step = ms / args.steps
     value = world * args.steps / (ms / 1e3)
 
+    # launches of one exchange application (the exchange kernel is the only kernel it launches)
+    l0 = api.kernel_launches()
+    ctx.apply_exchange(phi, torch.from_numpy(w.occ).to(devc), out=torch.empty_like(phi), cell=w.cell,
+                       kernel=w.kernel, precision=args.precision)
+    torch.cuda.synchronize()
+    ex_launches_per_app = api.kernel_launches() - l0
+
     pair_ffts = sum(s["pair_ffts"] for s in stats)
     ex_ms = sum(s["exchange_ms"] for s in stats)
     ex_calls = sum(s["exchange_calls"] for s in stats)
@@ -483,6 +589,13 @@ def run_gb300(args):
                 "exchange_speedup_fp32_vs_fp64": t64 / t32}
         del pd, p32
 
+    prec_res = None
+    if rank == 0 and world == 1 and not args.no_fp64:
+        try:
+            prec_res = precision_forms()
+        except Exception as e:  # noqa: BLE001
+            prec_res = {"error": str(e)[:300]}
+
     serve_res = None
     if rank == 0 and world == 1 and not args.no_serve:
         try:
@@ -514,7 +627,11 @@ def run_gb300(args):
             "phases_ms_per_step": {k: sum(s["phase_ms"][k] for s in stats) / len(stats)
                                    for k in stats[0]["phase_ms"]},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": (achieved / peak) if achieved else None, "traffic": None,
+                         "frac": (achieved / peak) if achieved else None,
+                         "traffic": EXCHANGE64_TRAFFIC_PER_LAUNCH if args.precision == "fp32" else None,
+                         "traffic_unit": "bytes per launch (ncu dram read + write)",
+                         "algorithmic_bytes_per_launch": (N * (N + 1) // 2) * bytes_per_pair / ex_launches_per_app,
+                         "launches_per_application": ex_launches_per_app,
                          "kernel": "pair-FFT exchange (plane/column/plane passes)",
                          "model": "6 complex fields of Ng per symmetric pair FFT",
                          "peak_source": peak_src,
@@ -523,6 +640,7 @@ def run_gb300(args):
             "gpu_launches": launches,
             "clocks": clocks,
             "plain_fp64_form": fp64,
+            "precision_forms": prec_res,
             "serve": serve_res,
         }
         if cpu is not None and "t_step_s" in cpu:
@@ -570,6 +688,10 @@ def main():
         run_reference(args)
     elif args.mode == "exchange":
         run_exchange_only(args)
+    elif args.mode == "precision":
+        print(json.dumps({"mode": "precision", "precision_forms": precision_forms()}), flush=True)
+    elif args.mode == "contractions":
+        print(json.dumps({"mode": "contractions", "contractions": contraction_measurement()}), flush=True)
     elif args.mode == "batched":
         import torch
         torch.cuda.set_device(0)

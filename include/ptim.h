@@ -68,8 +68,9 @@ typedef enum {
   PT_FP64 = 0,          /* every step in FP64 (the plain FP64 form) */
   PT_FP32 = 1,          /* pair products, FFTs and Ng-long contractions in FP32;
                            N x N factorisations, residuals and Loewdin in FP64 */
-  PT_FP32_TC_TF32 = 2,  /* as PT_FP32 with the ACE/subspace GEMMs on TF32 tensor cores */
-  PT_FP32_TC_BF16 = 3   /* as PT_FP32 with the ACE/subspace GEMMs on BF16 tensor cores */
+  PT_FP32_TC_TF32 = 2,  /* as PT_FP32 with the Gram/rotation contractions as one TF32 tensor-core product */
+  PT_FP32_TC_BF16 = 3   /* BF16 tensor-core contractions: not built; calls that need a contraction
+                           return PT_UNSUPPORTED, the exchange alone runs as PT_FP32 */
 } pt_precision;
 
 typedef struct pt_ctx pt_ctx;

@@ -83,6 +83,7 @@ void set_device(pt_ctx* ctx) { pt::check_cuda(cudaSetDevice(ctx->device), "cudaS
 // 3xTF32 tensor cores when the context option asks for it, CUDA cores otherwise
 void set_engine(pt_ctx* ctx, pt_precision prec) {
   ctx->active_tc = (prec == PT_FP32_TC_TF32) ? 2 : ((prec == PT_FP32 && ctx->tc_gram) ? 1 : 0);
+  ctx->bf16_requested = (prec == PT_FP32_TC_BF16);
 }
 
 void check_common(pt_ctx* ctx, const pt_grid* grid, pt_precision prec) {

@@ -101,6 +101,7 @@ struct pt_ctx {
   size_t scratch_budget = size_t(48) << 20;  // bytes of pair fields per exchange batch (L2-resident)
   int tc_gram = 0;     // option: FP32 form's Gram contractions on tensor cores (3xTF32) when 1
   int active_tc = 0;   // per call: 0 CUDA cores, 1 tensor cores 3xTF32, 2 tensor cores single TF32
+  bool bf16_requested = false;  // per call: the BF16 form, whose contractions are not built
   int ptim_q_n = 0;            // the "ptim_Q" buffer holds a complete unitary ptim_q_n x ptim_q_n basis
   int exchange64_engine = 0;  // option: 64^3 exchange on the TMA pipeline (0) or the compile-time tile kernels (1)
   int tc_period = 2;   // option: K stages (32 floats each) accumulated in TMEM between readouts

@@ -184,3 +184,16 @@ def test_rotate_64cubed_N320_tensor_cores_sampled(ctx):
         scale = float(np.sum(np.abs(Q[:, j]) * np.abs(Af[:, r])))
         assert abs(got[j, r] - ref) <= ROT_TOL["fp32_tc"] * scale
         assert abs(simt[j, r] - ref) <= ROT_TOL["fp32"] * scale
+
+
+def test_bf16_contractions_are_reported_unsupported(ctx):
+    """The BF16 form has no contraction kernels: the call fails with PT_UNSUPPORTED instead of
+    silently running another precision."""
+    from paper_2501_03061_gb300 import _lib as L
+    from paper_2501_03061_gb300 import api
+    rng = np.random.default_rng(320)
+    cell = synth.cubic(16, 6.0)
+    a = dev(fields(rng, cell, 8))
+    with pytest.raises(api.PtimError) as ei:
+        ctx.overlap(a, a, cell=cell, precision="bf16")
+    assert ei.value.status == L.PT_UNSUPPORTED
