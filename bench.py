@@ -538,8 +538,10 @@ def run_gb300(args):
     # ---- end to end: pinned host buffers, H2D inside the timed region, D2H of the result ----
     e2e = None
     if not args.no_e2e:
-        hphi = phi0.pin_memory()
-        hsig = sig0.pin_memory()
+        # a propagation through the public API with the state on the host between steps: each step's
+        # input is copied up from pinned memory and its output copied back, then fed to the next step
+        hphi = phi.cpu().pin_memory()
+        hsig = sigma.cpu().pin_memory()
         hv = vloc0.pin_memory()
         ophi = torch.empty_like(hphi).pin_memory()
         osig = torch.empty_like(hsig).pin_memory()
@@ -553,6 +555,9 @@ def run_gb300(args):
             ctx.ptim_step(dphi, dsig, dv, **kw)
             ophi.copy_(dphi, non_blocking=True)
             osig.copy_(dsig, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+            hphi, ophi = ophi, hphi
+            hsig, osig = osig, hsig
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
         if world > 1:
