@@ -93,6 +93,12 @@ size_t pt_workspace_bytes(const pt_ctx* ctx);
 pt_status pt_trim(pt_ctx* ctx);
 /* Set a tuning option of the context.  Keys (besides "graphs" and "autotune" of the batched
  * exchange, 0 or 1):
+ *   "ptim_inner_kappa", "ptim_inner_cap"  the PT-IM step solves the inner fixed point of an
+ *                    outer iteration to max(tol, min(cap, kappa * Delta)), Delta the relative move
+ *                    of the midpoint since the last ACE anchor (cap alone in the first outer
+ *                    iteration); the step still converges only when the midpoint has settled to
+ *                    tol and the last inner loop met tol.  Defaults 0.1 and 1e-2; kappa = 0 uses
+ *                    tol throughout.
  *   "scratch_bytes"  bytes of pair/orbital fields one FFT batch may hold (default 48 MiB, sized
  *                    to stay resident in L2; smaller values give more, smaller batches).
  *   "tc_gram"        1: in the PT_FP32 form, run the Gram contractions (A^H B over the grid) on

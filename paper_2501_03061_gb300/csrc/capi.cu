@@ -159,6 +159,11 @@ pt_status pt_set_option(pt_ctx* ctx, const char* key, double value) {
       (std::string(key) == "graphs" ? ctx->use_graphs : ctx->autotune) = value != 0.0 ? 1 : 0;
       return PT_OK;
     }
+    if (std::string(key) == "ptim_inner_kappa" || std::string(key) == "ptim_inner_cap") {
+      if (!(value >= 0.0) || value > 1.0) pt::fail(PT_INVALID_ARG, std::string(key) + " must be in [0, 1]");
+      (std::string(key) == "ptim_inner_kappa" ? ctx->ptim_inner_kappa : ctx->ptim_inner_cap) = value;
+      return PT_OK;
+    }
     if (std::string(key) == "exchange64_engine") {
       ctx->exchange64_engine = value != 0.0 ? 1 : 0;
       return PT_OK;

@@ -102,6 +102,8 @@ struct pt_ctx {
   int tc_gram = 0;     // option: FP32 form's Gram contractions on tensor cores (3xTF32) when 1
   int active_tc = 0;   // per call: 0 CUDA cores, 1 tensor cores 3xTF32, 2 tensor cores single TF32
   bool bf16_requested = false;  // per call: the BF16 form, whose contractions are not built
+  double ptim_inner_kappa = 0.1;  // option: inner tolerance = max(tol, min(cap, kappa * midpoint move))
+  double ptim_inner_cap = 1e-2;   // option: loosest inner tolerance (also that of the first outer iteration)
   int ptim_q_n = 0;            // the "ptim_Q" buffer holds a complete unitary ptim_q_n x ptim_q_n basis
   int exchange64_engine = 0;  // option: 64^3 exchange on the TMA pipeline (0) or the compile-time tile kernels (1)
   int tc_period = 2;   // option: K stages (32 floats each) accumulated in TMEM between readouts

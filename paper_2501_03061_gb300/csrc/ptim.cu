@@ -266,28 +266,50 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
     tm.end();
   };
 
+  // Inner tolerance per outer iteration.  While the midpoint the ACE operator is built on still
+  // moves by a relative Delta between outer iterations, the inner fixed point of that operator is
+  // only needed to kappa * Delta (at most `inner_cap`, at least tol); the step converges only when
+  // the midpoint has settled to tol AND the last inner loop met tol itself.  kappa = 0 keeps tol
+  // throughout.
+  const double kappa = ctx->ptim_inner_kappa, cap = ctx->ptim_inner_cap;
+  double inner_tol = P.tol;
   const int max_outer = P.use_ace ? P.max_outer : 1;
+  int aces = 0;
   for (int outer = 0; outer < max_outer && !converged; ++outer) {
     S.midpoint(phih, sigh, phi, phin, sig, sign);
     if (P.use_ace) {
+      bool rebuild = true;
       if (have_anchor) {
         PT_LAUNCH(k_diff<T>, sblocks, nthreads, 0, st, aphi, phih, aphi, S.n1);
         PT_LAUNCH(k_diff<double>, sblocks2, nthreads, 0, st, asig, sigh, asig, S.n2);
         double ch = 0, nr = 0;
         S.norm2_pair(aphi, asig, phih, sigh, &ch, &nr);
-        if (std::sqrt(ch / nr) < P.tol && inner_conv) {
-          converged = true;
-          break;
+        const double delta = std::sqrt(ch / nr);
+        if (delta < P.tol) {
+          if (inner_conv) {
+            converged = true;
+            break;
+          }
+          // the operator is exact to tol on this midpoint: finish the inner solve with it (the anchor
+          // stays where the operator was built, so the next check measures the distance to it)
+          rebuild = false;
+          inner_tol = P.tol;
+        } else {
+          inner_tol = kappa > 0.0 ? std::max(P.tol, std::min(cap, kappa * delta)) : P.tol;
         }
+      } else {
+        inner_tol = kappa > 0.0 ? std::max(P.tol, cap) : P.tol;
       }
-      PT_CUDA_CHECK(cudaMemcpyAsync(aphi, phih, fb, cudaMemcpyDeviceToDevice, st));
-      PT_CUDA_CHECK(cudaMemcpyAsync(asig, sigh, mb, cudaMemcpyDeviceToDevice, st));
-      have_anchor = true;
-      stv.outer = outer + 1;
-      exchange_on_midpoint(W, true);
-      tm.begin(PH_ACE_BUILD);
-      ace_from_w(ctx, W, phih, N, g, prec, xi, st);
-      tm.end();
+      if (rebuild) {
+        PT_CUDA_CHECK(cudaMemcpyAsync(aphi, phih, fb, cudaMemcpyDeviceToDevice, st));
+        PT_CUDA_CHECK(cudaMemcpyAsync(asig, sigh, mb, cudaMemcpyDeviceToDevice, st));
+        have_anchor = true;
+        stv.outer = ++aces;
+        exchange_on_midpoint(W, true);
+        tm.begin(PH_ACE_BUILD);
+        ace_from_w(ctx, W, phih, N, g, prec, xi, st);
+        tm.end();
+      }
     } else {
       stv.outer = 1;
     }
@@ -343,9 +365,9 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
       const double res = std::sqrt(rr / xx);
       stv.residual = res;
       if (!std::isfinite(res)) fail(PT_NONFINITE, "PT-IM residual is not finite");
-      if (res < P.tol) {
+      if (res < inner_tol) {
         tm.end();
-        inner_conv = true;
+        inner_conv = res < P.tol;
         break;
       }
       // ---- Anderson (type II, real coefficients) ----
