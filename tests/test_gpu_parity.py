@@ -289,17 +289,22 @@ def test_ptim_step_fp32_matches_oracle(ctx, ptim_ref, tc_gram):
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("sym", [True, False])
-def test_exchange_64cubed_specialised_path(ctx, precision, sym):
-    """The 64^3 kernel (pipelined plane/column/plane roles) against the oracle, several batches."""
-    rng = np.random.default_rng(64 + sym)
+@pytest.mark.parametrize("tile", [2, 6])
+def test_exchange_64cubed_specialised_path(ctx, precision, sym, tile):
+    """The 64^3 kernels (pipelined plane/column/plane/accumulate roles in FP32) against the oracle:
+    several batches of 2x2 or 6x6 pair tiles, ragged at the edge (N = 7 or 13), an exact-zero
+    occupation (skipped pairs), separate targets."""
+    rng = np.random.default_rng(64 + sym + 10 * tile)
     cell = synth.cubic(64, 20.5)
-    src = synth.random_orbitals(rng, cell, 7)
-    tgt = src if sym else synth.random_orbitals(rng, cell, 3)
-    occ = np.array([1.0, 0.0, 0.8, 0.45, 0.2, 0.05, 0.7])
+    n = 7 if tile == 2 else 13
+    src = synth.random_orbitals(rng, cell, n)
+    tgt = src if sym else synth.random_orbitals(rng, cell, 3 if tile == 2 else 8)
+    occ = np.linspace(1.0, 0.05, n)
+    occ[1] = 0.0
     g = O.grid_of(cell)
     ref = O.apply_exchange(src, occ, tgt, O.exchange_kernel(g, 1, synth.SCREENED_MU))
     dt = np.complex128 if precision == "fp64" else np.complex64
-    ctx.set_option("scratch_bytes", 4 * g.ng * (16 if precision == "fp64" else 8))  # 2x2 pair tiles
+    ctx.set_option("scratch_bytes", tile * tile * g.ng * (16 if precision == "fp64" else 8))
     try:
         out = ctx.apply_exchange(dev(src.astype(dt)), dev(occ), None if sym else dev(tgt.astype(dt)), cell=cell,
                                  kernel={"type": 1, "mu": synth.SCREENED_MU}, precision=precision)
