@@ -67,10 +67,8 @@ def parse():
 
 
 def dist_env():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return world, rank, local
+    from paper_2501_03061_gb300 import replicas
+    return replicas.env()
 
 
 # ------------------------------------------------------------------------------------------
@@ -457,7 +455,7 @@ def run_gb300(args):
     import torch
     import torch.distributed as dist
 
-    from paper_2501_03061_gb300 import api, synth
+    from paper_2501_03061_gb300 import api, replicas, synth
 
     world, rank, local = dist_env()
     if world > 1:
@@ -510,13 +508,9 @@ def run_gb300(args):
     barrier()
     launches = api.kernel_launches() - l0
     clocks = sampler.stop() if sampler else None
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], device=devc)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    job_s, value = replicas.job_throughput(ev0.elapsed_time(ev1) / 1e3, args.steps, devc)
+    ms = job_s * 1e3
     ms_per_step = ms / args.steps
-    value = world * args.steps / (ms / 1e3)
 
     # launches of one exchange application (the exchange kernel is the only kernel it launches)
     l0 = api.kernel_launches()
@@ -559,12 +553,8 @@ def run_gb300(args):
             hphi, ophi = ophi, hphi
             hsig, osig = osig, hsig
         torch.cuda.synchronize()
-        te = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([te], device=devc)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
-        e2e = {"value": world * args.steps / te, "unit": UNIT,
+        te, e2e_value = replicas.job_throughput(time.perf_counter() - t0, args.steps, devc)
+        e2e = {"value": e2e_value, "unit": UNIT,
                "h2d_bytes_per_step": int(hphi.numel() * hphi.element_size() + hsig.numel() * 16 + hv.numel() * 8),
                "d2h_bytes_per_step": int(ophi.numel() * ophi.element_size() + osig.numel() * 16)}
 
