@@ -254,7 +254,7 @@ def precision_forms() -> dict:
         ref = run("fp64", 0)
         res = {}
         for name, prec, tc in (("fp32_cuda_cores", "fp32", 0), ("fp32_tensor_3xTF32", "fp32", 1),
-                               ("tf32_tensor", "tf32", 0)):
+                               ("tf32_tensor", "tf32", 0), ("bf16_tensor", "bf16", 0)):
             r = run(prec, tc)
             e = {k: float(np.linalg.norm(r[k] - ref[k]) / np.linalg.norm(ref[k])) for k in ("W", "M", "xi", "Vace")}
             e["Ex_Ha_per_atom"] = abs(r["Ex"] - ref["Ex"]) / w.natoms
@@ -295,7 +295,8 @@ def contraction_measurement() -> dict:
         calls = {"overlap_herm": lambda p: ctx.overlap(a, a, cell=cell, precision=p),
                  "overlap_general": lambda p: ctx.overlap(a, b, cell=cell, precision=p),
                  "rotate": lambda p: ctx.rotate(a, B, cell=cell, precision=p)}
-        for eng, prec, tc in (("cuda_cores_fp32", "fp32", 0), ("tensor_3xTF32", "fp32", 1), ("tensor_TF32", "tf32", 0)):
+        for eng, prec, tc in (("cuda_cores_fp32", "fp32", 0), ("tensor_3xTF32", "fp32", 1), ("tensor_TF32", "tf32", 0),
+                              ("tensor_BF16", "bf16", 0)):
             ctx.set_option("tc_gram", tc)
             for name, f in calls.items():
                 out = f(prec)

@@ -69,8 +69,9 @@ typedef enum {
   PT_FP32 = 1,          /* pair products, FFTs and Ng-long contractions in FP32;
                            N x N factorisations, residuals and Loewdin in FP64 */
   PT_FP32_TC_TF32 = 2,  /* as PT_FP32 with the Gram/rotation contractions as one TF32 tensor-core product */
-  PT_FP32_TC_BF16 = 3   /* BF16 tensor-core contractions: not built; calls that need a contraction
-                           return PT_UNSUPPORTED, the exchange alone runs as PT_FP32 */
+  PT_FP32_TC_BF16 = 3   /* as PT_FP32 with the Gram/rotation contractions as one BF16 tensor-core
+                           product (operands rounded to bf16, FP32 accumulation); an error-study
+                           form: the pair products and FFTs of the exchange run as in PT_FP32 */
 } pt_precision;
 
 typedef struct pt_ctx pt_ctx;

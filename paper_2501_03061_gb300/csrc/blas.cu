@@ -315,7 +315,10 @@ template <class T>
 void gram(pt_ctx* ctx, const cx<T>* A, const cx<T>* B, int N1, int N2, size_t ng, double scale, c128* C,
           cudaStream_t st, bool herm) {
   if constexpr (sizeof(T) == 4) {
-    if (ctx->bf16_requested) fail(PT_UNSUPPORTED, "BF16 tensor-core contractions are not built");
+    if (ctx->bf16_requested) {
+      gram_bf16(ctx, A, B, N1, N2, ng, scale, C, st, herm);
+      return;
+    }
     if (ctx->active_tc && gram_tc_applies(A, B, ng)) {
       gram_tc(ctx, A, B, N1, N2, ng, scale, C, st, herm, ctx->active_tc == 1);
       return;
@@ -348,7 +351,10 @@ template <class T>
 void rotate(pt_ctx* ctx, const cx<T>* A, const c128* Bm, int ldb, int N1, int N2, size_t ng, c128 alpha,
             const Term* terms, int nterms, cx<T>* out, cudaStream_t st) {
   if constexpr (sizeof(T) == 4) {
-    if (ctx->bf16_requested) fail(PT_UNSUPPORTED, "BF16 tensor-core contractions are not built");
+    if (ctx->bf16_requested && nterms <= 3) {
+      rotate_bf16(ctx, A, Bm, ldb, N1, N2, ng, alpha, terms, nterms, out, st);
+      return;
+    }
     if (ctx->active_tc && nterms <= 3 && rotate_tc_applies(A, ng)) {
       rotate_tc(ctx, A, Bm, ldb, N1, N2, ng, alpha, terms, nterms, out, st, ctx->active_tc == 1);
       return;

@@ -79,8 +79,9 @@ pt_status guarded(pt_ctx* ctx, F&& f) {
 
 void set_device(pt_ctx* ctx) { pt::check_cuda(cudaSetDevice(ctx->device), "cudaSetDevice"); }
 
-// contraction engine for this call: TF32 form on single-product tensor cores, FP32 form on
-// 3xTF32 tensor cores when the context option asks for it, CUDA cores otherwise
+// contraction engine for this call: TF32 form on single-product tensor cores, BF16 form on bf16
+// tensor cores (packed operands), FP32 form on 3xTF32 tensor cores when the context option asks
+// for it, CUDA cores otherwise
 void set_engine(pt_ctx* ctx, pt_precision prec) {
   ctx->active_tc = (prec == PT_FP32_TC_TF32) ? 2 : ((prec == PT_FP32 && ctx->tc_gram) ? 1 : 0);
   ctx->bf16_requested = (prec == PT_FP32_TC_BF16);
@@ -262,7 +263,7 @@ pt_status pt_build_ace_from(pt_ctx* ctx, const void* W, const void* phi, int N, 
     }
     try {
       pt::ace_from_w(ctx, W, phi, N, *grid, prec, a->xi, static_cast<cudaStream_t>(stream));
-      if (ctx->active_tc) pt::gram_tc_check(ctx, static_cast<cudaStream_t>(stream));
+      if (ctx->active_tc || ctx->bf16_requested) pt::gram_tc_check(ctx, static_cast<cudaStream_t>(stream));
     } catch (...) {
       cudaFree(a->xi);
       delete a;
@@ -311,7 +312,7 @@ pt_status pt_overlap(pt_ctx* ctx, const void* A, int N1, const void* B, int N2, 
       pt::gram<double>(ctx, static_cast<const c128*>(A), static_cast<const c128*>(B), N1, N2, ng, dV, Cm, st, herm);
     else
       pt::gram<float>(ctx, static_cast<const c64*>(A), static_cast<const c64*>(B), N1, N2, ng, dV, Cm, st, herm);
-    if (ctx->active_tc) pt::gram_tc_check(ctx, st);
+    if (ctx->active_tc || ctx->bf16_requested) pt::gram_tc_check(ctx, st);
     return PT_OK;
   });
 }
@@ -338,7 +339,7 @@ pt_status pt_rotate(pt_ctx* ctx, const void* A, int N1, const void* B, int N2, c
     else
       pt::rotate<float>(ctx, static_cast<const c64*>(A), Bm, N2, N1, N2, ng, c128{1, 0}, nullptr, 0,
                         static_cast<c64*>(out), st);
-    if (ctx->active_tc) pt::gram_tc_check(ctx, st);
+    if (ctx->active_tc || ctx->bf16_requested) pt::gram_tc_check(ctx, st);
     return PT_OK;
   });
 }
@@ -353,7 +354,7 @@ pt_status pt_apply_ace(pt_ctx* ctx, const pt_ace* ace, const void* psi, int M, v
     set_device(ctx);
     set_engine(ctx, ace->prec);
     pt::ace_apply(ctx, ace->xi, ace->N, psi, M, out, ace->grid, ace->prec, static_cast<cudaStream_t>(stream));
-    if (ctx->active_tc) pt::gram_tc_check(ctx, static_cast<cudaStream_t>(stream));
+    if (ctx->active_tc || ctx->bf16_requested) pt::gram_tc_check(ctx, static_cast<cudaStream_t>(stream));
     return PT_OK;
   });
 }
@@ -392,7 +393,7 @@ pt_status pt_apply_H(pt_ctx* ctx, const void* psi, int M, void* out, const doubl
       X = buf;
     }
     pt::apply_h(ctx, psi, M, out, vloc, X, alpha, ecut, *grid, prec, st);
-    if (ctx->active_tc && ace) pt::gram_tc_check(ctx, st);
+    if ((ctx->active_tc || ctx->bf16_requested) && ace) pt::gram_tc_check(ctx, st);
     return PT_OK;
   });
 }
@@ -427,7 +428,7 @@ pt_status pt_ptim_step(pt_ctx* ctx, void* phi, void* sigma, int N, const double*
     set_engine(ctx, prec);
     pt_status r =
         pt::ptim_step(ctx, phi, sigma, N, vloc, *grid, *kernel, P, prec, stats, static_cast<cudaStream_t>(stream));
-    if (ctx->active_tc) pt::gram_tc_check(ctx, static_cast<cudaStream_t>(stream));
+    if (ctx->active_tc || ctx->bf16_requested) pt::gram_tc_check(ctx, static_cast<cudaStream_t>(stream));
     return r;
   });
 }

@@ -296,6 +296,11 @@ void encode_tmap_4d_f32(CUtensorMap* map, const void* base, const uint64_t dims[
   encode_tmap_4d(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, base, dims, strides_bytes, box, swizzle);
 }
 
+void encode_tmap_4d_bf16(CUtensorMap* map, const void* base, const uint64_t dims[4], const uint64_t strides_bytes[3],
+                         const uint32_t box[4], CUtensorMapSwizzle swizzle) {
+  encode_tmap_4d(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, base, dims, strides_bytes, box, swizzle);
+}
+
 void encode_tmap_4d_u64(CUtensorMap* map, const void* base, const uint64_t dims[4], const uint64_t strides_bytes[3],
                         const uint32_t box[4], CUtensorMapSwizzle swizzle) {
   const cuuint32_t estr[4] = {1, 1, 1, 1};

@@ -51,6 +51,12 @@ void rotate_tc(pt_ctx* ctx, const c64* A, const c128* Bm, int ldb, int N1, int N
                const Term* terms, int nterms, c64* out, cudaStream_t st, bool split3);
 bool rotate_tc_applies(const void* A, size_t ng);
 
+// ---- BF16 tensor-core contractions (contract_bf16.cu): operands packed to bf16, FP32 accumulation ----
+void gram_bf16(pt_ctx* ctx, const c64* A, const c64* B, int N1, int N2, size_t ng, double scale, c128* C,
+               cudaStream_t st, bool herm);
+void rotate_bf16(pt_ctx* ctx, const c64* A, const c128* Bm, int ldb, int N1, int N2, size_t ng, c128 alpha,
+                 const Term* terms, int nterms, c64* out, cudaStream_t st);
+
 // ---- FP64 N x N (dense.cu) ----
 void zgemm(char opA, char opB, int m, int n, int k, c128 alpha, const c128* A, int lda, const c128* B, int ldb,
            c128 beta, c128* C, int ldc, cudaStream_t st);

@@ -74,6 +74,9 @@ __device__ __forceinline__ void tma_store_wait_all() { asm volatile("cp.async.bu
 // order this thread's generic-proxy shared-memory writes before later async-proxy (TMA) reads
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+// Host: 4-D tiled tensor map over 2-byte bfloat16 values, dims innermost first.
+void encode_tmap_4d_bf16(CUtensorMap* map, const void* base, const uint64_t dims[4], const uint64_t strides_bytes[3],
+                         const uint32_t box[4], CUtensorMapSwizzle swizzle);
 // Host: 4-D tiled tensor map over 4-byte floats, dims innermost first.
 void encode_tmap_4d_f32(CUtensorMap* map, const void* base, const uint64_t dims[4], const uint64_t strides_bytes[3],
                         const uint32_t box[4], CUtensorMapSwizzle swizzle);

@@ -4,8 +4,11 @@ PT-IM's S = <phi|phi>) and the rotation out_j = sum_k B[k][j] A_k (phit = Phi Q,
 The FP32 forms are compared with the FP64 oracle evaluated on the same FP32-rounded inputs, so
 the bound measures the contraction alone: |C_gpu - C_ref| <= tol * dV sum_r |a_i(r)| |b_j(r)|
 element by element (the scale a product-sum's rounding error is proportional to), with
-tol 1e-6 for compensated FP32 on CUDA cores, 1e-5 for the 3-product TF32 tensor-core form and
-2e-3 for a single TF32 product (10 explicit mantissa bits: unit roundoff 2^-11 per product).
+tol 1e-6 for compensated FP32 on CUDA cores, 1e-5 for the 3-product TF32 tensor-core form,
+2e-3 for a single TF32 product (10 explicit mantissa bits: unit roundoff 2^-11 per product) and
+4e-3 for a single BF16 product (7 explicit mantissa bits: unit roundoff u = 2^-9, and a product of
+two rounded factors is off by at most (2u + u^2) |a| |b| = 3.91e-3 |a| |b|; the FP32 sums in TMEM
+and the compensated readout add about 1e-5 of that scale).
 """
 import numpy as np
 import pytest
@@ -16,7 +19,7 @@ from paper_2501_03061_gb300 import synth
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp32": 1e-6, "fp32_tc": 1e-5, "tf32": 2e-3}
+TOL = {"fp32": 1e-6, "fp32_tc": 1e-5, "tf32": 2e-3, "bf16": 4e-3}
 
 
 @pytest.fixture(scope="module")
@@ -65,7 +68,7 @@ def check(got, A, B, dV, tol):
     return float((err / scale).max())
 
 
-@pytest.mark.parametrize("mode", ["fp64", "fp32", "fp32_tc", "tf32"])
+@pytest.mark.parametrize("mode", ["fp64", "fp32", "fp32_tc", "tf32", "bf16"])
 def test_overlap_general_ragged(ctx, mode):
     """N1 = 70, N2 = 130 (ragged 64-wide tiles), 24^3 grid."""
     rng = np.random.default_rng(301)
@@ -79,7 +82,7 @@ def test_overlap_general_ragged(ctx, mode):
         check(got, A, B, O.grid_of(cell).dV, TOL[mode])
 
 
-@pytest.mark.parametrize("mode", ["fp32", "fp32_tc", "tf32"])
+@pytest.mark.parametrize("mode", ["fp32", "fp32_tc", "tf32", "bf16"])
 def test_overlap_hermitian_ragged_K_tail(ctx, mode):
     """S = <A|A> with N = 97 (mirrored tiles) on a 9 x 10 x 12 grid: 2 Ng = 2160 floats is not a
     multiple of the 32-float stage, so the last stage is partly zero-filled."""
@@ -149,10 +152,10 @@ def check_rotate(got, A, B, tol):
     assert np.all(err <= tol * scale), float((err / scale).max())
 
 
-ROT_TOL = {"fp32": 1e-5, "fp32_tc": 1e-5, "tf32": 2e-3}
+ROT_TOL = {"fp32": 1e-5, "fp32_tc": 1e-5, "tf32": 2e-3, "bf16": 4e-3}
 
 
-@pytest.mark.parametrize("mode", ["fp64", "fp32", "fp32_tc", "tf32"])
+@pytest.mark.parametrize("mode", ["fp64", "fp32", "fp32_tc", "tf32", "bf16"])
 @pytest.mark.parametrize("shape", [(24, 24, 24), (9, 10, 12)])
 def test_rotate_ragged(ctx, mode, shape):
     """N1 = 70 (partial last K stage of 16 orbitals), N2 = 130 (partial last 64-orbital tile);
@@ -186,14 +189,28 @@ def test_rotate_64cubed_N320_tensor_cores_sampled(ctx):
         assert abs(simt[j, r] - ref) <= ROT_TOL["fp32"] * scale
 
 
-def test_bf16_contractions_are_reported_unsupported(ctx):
-    """The BF16 form has no contraction kernels: the call fails with PT_UNSUPPORTED instead of
-    silently running another precision."""
-    from paper_2501_03061_gb300 import _lib as L
-    from paper_2501_03061_gb300 import api
+def test_bf16_64cubed_N320_sampled(ctx):
+    """The BF16 form at the full size of the ACE contractions (64^3 grid, N = 320): the overlap and
+    the rotation on sampled entries against the FP64 definitions, within the single-BF16-product
+    bound."""
     rng = np.random.default_rng(320)
-    cell = synth.cubic(16, 6.0)
-    a = dev(fields(rng, cell, 8))
-    with pytest.raises(api.PtimError) as ei:
-        ctx.overlap(a, a, cell=cell, precision="bf16")
-    assert ei.value.status == L.PT_UNSUPPORTED
+    cell = synth.cubic(64, 20.5)
+    A = fields(rng, cell, 320)
+    a = dev(A)
+    S = ctx.overlap(a, a, cell=cell, precision="bf16").cpu().numpy()
+    Q, _ = np.linalg.qr(rng.standard_normal((320, 320)) + 1j * rng.standard_normal((320, 320)))
+    R = ctx.rotate(a, dev(Q), cell=cell, precision="bf16").cpu().numpy().reshape(320, -1)
+    dV = O.grid_of(cell).dV
+    Af = A.reshape(320, -1).astype(np.complex128)
+    absn = np.abs(Af)
+    for _ in range(64):
+        i, j = (int(v) for v in rng.integers(0, 320, size=2))
+        ref = dV * np.vdot(Af[i], Af[j])
+        assert abs(S[i, j] - ref) <= TOL["bf16"] * dV * float(absn[i] @ absn[j])
+        r = int(rng.integers(0, Af.shape[1]))
+        ref = np.sum(Q[:, j] * Af[:, r])
+        assert abs(R[j, r] - ref) <= ROT_TOL["bf16"] * float(np.sum(np.abs(Q[:, j]) * absn[:, r]))
+    # tiles below the diagonal are exact conjugate mirrors of the ones above
+    t = np.arange(320) // 64
+    off = t[:, None] != t[None, :]
+    assert np.abs(S - S.conj().T)[off].max() == 0.0
