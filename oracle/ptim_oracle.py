@@ -26,7 +26,9 @@ Parity status per function: every public function here is pinned by the
 `-m "not gpu"` tests (direct convolution, plane-wave closed forms, Hermiticity,
 ACE identity, triple-sum vs diagonalised exchange, PT-IM invariants, the
 Cayley closed form, stationary states, energy conservation and an RK4
-cross-check).  The Anderson trajectory itself (iteration counts, the exact
+cross-check; for V_Hxc: the Hartree potential of cosine densities, the Slater
+constant, the Perdew-Zunger high-density limit and branch continuity, potentials
+as derivatives of their energies, and PT-IM with V_Hxc[rho(t)] against RK4).  The Anderson trajectory itself (iteration counts, the exact
 stop point) is parity unpinned: only converged states are compared.
 """
 from __future__ import annotations
@@ -262,6 +264,79 @@ def apply_H(phi: np.ndarray, vloc: np.ndarray, g: Grid, ecut: float, alpha: floa
 
 
 # ----------------------------------------------------------------------------------------
+# Self-consistent local potential V_Hxc[rho] (Eq. 1): Hartree by the periodic Poisson
+# equation, exchange-correlation in the local density approximation
+# ----------------------------------------------------------------------------------------
+
+def hartree_potential(rho: np.ndarray, g: Grid) -> np.ndarray:
+    """V_H solving -Lap V_H = 4 pi (rho - mean rho) on the periodic cell.
+
+    V_H(G) = 4 pi rho(G) / |G|^2 for G != 0 and V_H(0) = 0: the G = 0 term of a periodic cell
+    is cancelled by the neutralising background (the paper does not state it; this is the
+    standard plane-wave reading).
+    """
+    g2 = g_squared(g)
+    rg = np.fft.fftn(rho)
+    vg = np.zeros_like(rg)
+    nz = g2 > 0
+    vg[nz] = 4 * np.pi * rg[nz] / g2[nz]
+    return np.fft.ifftn(vg).real
+
+
+# Perdew-Zunger (Phys. Rev. B 23, 5048 (1981)) fit of the Ceperley-Alder correlation energy
+# of the unpolarised electron gas, per electron, as a function of rs = (3/(4 pi rho))^(1/3)
+PZ_GAMMA, PZ_BETA1, PZ_BETA2 = -0.1423, 1.0529, 0.3334   # rs >= 1
+PZ_A, PZ_B, PZ_C, PZ_D = 0.0311, -0.048, 0.0020, -0.0116  # rs < 1
+RHO_FLOOR = 1e-30  # below this density (and for rounding-negative densities) eps = v = 0
+
+
+def lda_xc(rho: np.ndarray):
+    """(eps_xc, v_xc) per point of the LDA: Slater exchange + Perdew-Zunger correlation.
+
+    eps_x = -(3/4) (3 rho / pi)^(1/3),  v_x = d(rho eps_x)/d rho = (4/3) eps_x.
+    eps_c from the two Perdew-Zunger branches; v_c = eps_c - (rs/3) d eps_c / d rs.
+    The paper's hybrid functional is not named beyond its screened exchange; the local part
+    here is the LDA (the semilocal part of HSE-type functionals is PBE, a gradient correction
+    that this reading leaves out).
+    """
+    rho = np.asarray(rho, dtype=np.float64)
+    eps = np.zeros_like(rho)
+    v = np.zeros_like(rho)
+    m = rho > RHO_FLOOR
+    r = rho[m]
+    ex = -0.75 * np.cbrt(3.0 * r / np.pi)
+    vx = 4.0 / 3.0 * ex
+    rs = np.cbrt(3.0 / (4.0 * np.pi * r))
+    ec = np.empty_like(r)
+    vc = np.empty_like(r)
+    hi = rs >= 1.0
+    s = np.sqrt(rs[hi])
+    den = 1.0 + PZ_BETA1 * s + PZ_BETA2 * rs[hi]
+    ec[hi] = PZ_GAMMA / den
+    vc[hi] = ec[hi] * (1.0 + 7.0 / 6.0 * PZ_BETA1 * s + 4.0 / 3.0 * PZ_BETA2 * rs[hi]) / den
+    lo = ~hi
+    x = rs[lo]
+    lnx = np.log(x)
+    ec[lo] = PZ_A * lnx + PZ_B + PZ_C * x * lnx + PZ_D * x
+    vc[lo] = PZ_A * lnx + (PZ_B - PZ_A / 3.0) + 2.0 / 3.0 * PZ_C * x * lnx + (2.0 * PZ_D - PZ_C) / 3.0 * x
+    eps[m] = ex + ec
+    v[m] = vx + vc
+    return eps, v
+
+
+def hxc_potential(rho: np.ndarray, g: Grid) -> np.ndarray:
+    """V_Hxc[rho] = V_H[rho] + v_xc(rho)."""
+    return hartree_potential(rho, g) + lda_xc(rho)[1]
+
+
+def hxc_energy(rho: np.ndarray, g: Grid) -> tuple[float, float]:
+    """(E_H, E_xc) = (1/2 int rho V_H, int rho eps_xc); V_Hxc is their functional derivative."""
+    eh = 0.5 * g.dV * float(np.sum(rho * hartree_potential(rho, g)))
+    exc = g.dV * float(np.sum(rho * lda_xc(rho)[0]))
+    return eh, exc
+
+
+# ----------------------------------------------------------------------------------------
 # PT-IM time step (Sec. II-A Eqs. PTIM, n+1/2, p_tilde, lisan, x=tx; Alg. 1; Sec. IV-A2 double loop)
 # ----------------------------------------------------------------------------------------
 
@@ -276,6 +351,8 @@ class PtimParams:
     anderson_depth: int = 20      # maximum mixing dimension (Sec. VI)
     anderson_beta: float = 1.0
     use_ace: bool = True
+    hxc: bool = False             # V_Hxc[rho_h] from the midpoint density in every iteration
+    spin: float = 2.0             # electrons per orbital in rho = spin * P(r, r)
 
 
 @dataclasses.dataclass
@@ -337,7 +414,8 @@ def ptim_step(phi_n: np.ndarray, sigma_n: np.ndarray, vloc: np.ndarray, g: Grid,
     map (Eq. lisan, read with balanced parentheses):
         T_Phi   = Phi_n   - i dt (I - Pt) H Phi_h,   Pt = Phi_h S^{-1} Phi_h^*,  S = Phi_h^* Phi_h
         T_sigma = sigma_n - i dt [A, sigma_h],        A = Phi_h^* H Phi_h
-    with H = H[P_h], P_h = Phi_h sigma_h Phi_h^* (Eq. p_tilde).  Initial guess:
+    with H = H[P_h], P_h = Phi_h sigma_h Phi_h^* (Eq. p_tilde); with p.hxc the local potential
+    is V_loc + V_Hxc[spin * P_h(r, r)], else V_loc alone (V_ext + V_Hxc frozen).  Initial guess:
     x = (Phi_n, sigma_n).  Outer loop: diagonalise sigma_h, W = V_x[P_h] Phi_h,
     ACE from (Phi_h, W).  Inner loop: Anderson on x = T(x) with the ACE frozen
     (or V_x applied exactly when use_ace is False).  Outer stop: the midpoint
@@ -385,7 +463,10 @@ def ptim_step(phi_n: np.ndarray, sigma_n: np.ndarray, vloc: np.ndarray, g: Grid,
             stats.inner += 1
             phi_h = 0.5 * (phi + phi_n)
             sig_h = 0.5 * (sigma + sigma_n)
-            Hphi = apply_H(phi_h, vloc, g, p.ecut, p.alpha, exch(phi_h, sig_h))
+            v = vloc
+            if p.hxc:  # H_{n+1/2} = H[P_{n+1/2}] (Eq. p_tilde): V_Hxc from rho of the midpoint
+                v = vloc + hxc_potential(p.spin * density(phi_h, sig_h).real, g)
+            Hphi = apply_H(phi_h, v, g, p.ecut, p.alpha, exch(phi_h, sig_h))
             A = overlap(phi_h, Hphi, dV)
             S = overlap(phi_h, phi_h, dV)
             SinvA = np.linalg.solve(S, A)
@@ -429,13 +510,16 @@ def density(phi: np.ndarray, sigma: np.ndarray) -> np.ndarray:
 
 
 def total_energy(phi: np.ndarray, sigma: np.ndarray, vloc: np.ndarray, g: Grid, K: np.ndarray,
-                 ecut: float, alpha: float = 0.25, spin: float = 2.0) -> float:
-    """E = spin * Tr[P (-1/2 Lap + V_loc)] + spin*(alpha/2) Tr[P V_x[P]], P = Phi sigma Phi^*.
+                 ecut: float, alpha: float = 0.25, spin: float = 2.0, hxc: bool = False) -> float:
+    """E = spin * Tr[P (-1/2 Lap + V_loc)] + spin*(alpha/2) Tr[P V_x[P]] (+ E_H + E_xc), P = Phi sigma Phi^*.
 
-    Tr[P O] = sum_ij sigma_ij <phi_j|O phi_i>.  The frozen-potential energy
-    whose functional derivative is spin*H for the Hamiltonian used here.
+    Tr[P O] = sum_ij sigma_ij <phi_j|O phi_i>.  The energy whose functional
+    derivative is spin*H for the Hamiltonian used here (with hxc, rho = spin P(r, r)).
     """
     hphi = project_sphere(apply_kinetic_local(phi, vloc, g), g, ecut)
     B = overlap(phi, hphi, g.dV)  # B[j, i] = <phi_j|h phi_i>
     e_one = spin * np.real(np.sum(sigma * B.T))
-    return float(e_one + exchange_energy(phi, sigma, K, g.dV, alpha, spin))
+    e = e_one + exchange_energy(phi, sigma, K, g.dV, alpha, spin)
+    if hxc:
+        e += sum(hxc_energy(spin * density(phi, sigma).real, g))
+    return float(e)
