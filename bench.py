@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--tc-gram", type=int, default=1, choices=[0, 1],
                     help="1: Gram and rotation contractions of the FP32 step on tensor cores (3-product "
                          "TF32); 0: CUDA cores")
+    ap.add_argument("--hxc", action="store_true",
+                    help="rebuild V_Hxc[rho] (Hartree + LDA) from the midpoint density in every inner iteration "
+                         "instead of keeping the local potential frozen")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 form comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
@@ -481,8 +484,10 @@ def run_gb300(args):
     sigma = sig0.to(devc)
     vloc = vloc0.to(devc)
     workload = WORKLOAD if N == 320 else WORKLOAD.replace("N320", f"N{N}")
+    if args.hxc:
+        workload = workload.replace("ptim_ace_step", "ptim_ace_hxc_step")
     kw = dict(cell=w.cell, kernel=w.kernel, precision=args.precision, dt=0.5, alpha=0.25, ecut=10.0,
-              tol=args.tol, max_outer=20, max_inner=100, anderson_depth=20, allow_unconverged=True)
+              tol=args.tol, max_outer=20, max_inner=100, anderson_depth=20, hxc=args.hxc, allow_unconverged=True)
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -613,6 +618,8 @@ def run_gb300(args):
             "config": {"workload": workload, "grid": [64, 64, 64], "N": N, "atoms": 128, "precision": args.precision,
                        "tol": args.tol, "dt_au": 0.5, "parallelism": f"replicas{world}",
                        "contraction_engine": "tcgen05 3xTF32" if args.tc_gram else "CUDA cores",
+                       "local_potential": ("V_loc + V_Hxc[rho_h] (Hartree + LDA), rebuilt every inner iteration"
+                                           if args.hxc else "V_loc (V_ext + V_Hxc frozen)"),
                        "l2": "inputs larger than L2 (phi alone is %d MB)" % (N * ng * esz >> 20)},
             "pair_ffts_per_s": pair_ffts / (ms / 1e3) if ms > 0 else None,
             "exchange": {"pair_ffts": pair_ffts, "calls": ex_calls, "ms": ex_ms,

@@ -215,6 +215,26 @@ pt_status pt_apply_H(pt_ctx* ctx, const void* psi, int M, void* out, const doubl
                      const pt_ace* ace, double alpha, double ecut, const pt_grid* grid,
                      pt_precision prec, void* stream);
 
+/* ---- self-consistent local potential (Eq. 1: V_Hxc[P]) ------------------------------------ */
+
+/* rho(r) = spin * P(r, r) = spin * Re sum_ij sigma_ij phi_i(r) conj(phi_j(r)) for the density
+ * matrix P = Phi sigma Phi^* (Sec. II-A, Eq. mix_P).  phi: Ng x N orbital-major, precision prec
+ * (16-byte aligned); sigma: N x N complex128 row-major (Hermitian); rho: Ng doubles.  All device
+ * pointers.  The FP32 forms form chi = Phi sigma with the library's rotation (tensor cores when
+ * enabled) and sum the products in FP64.  Workspace: one Ng x N block held by the context. */
+pt_status pt_density(pt_ctx* ctx, const void* phi, const void* sigma, int N, const pt_grid* grid, pt_precision prec,
+                     double spin, double* rho, void* stream);
+
+/* v = vloc + V_H[rho] + v_xc(rho), all FP64 (Eq. 1's V_Hxc; the paper does not name its local
+ * functional: this is the LDA).  V_H(G) = 4 pi rho(G)/|G|^2 with V_H(G = 0) = 0 (neutralising
+ * background); v_xc = d(rho eps_xc)/d rho with Slater exchange and the Perdew-Zunger (1981)
+ * correlation of the unpolarised gas; eps = v = 0 where rho <= 1e-30.  rho, vloc, v: Ng doubles
+ * on the device (vloc may be NULL: zero; v must not alias rho).  energies: NULL or a host array
+ * of 2 that receives (E_H, E_xc) = (1/2 int rho V_H, int rho eps_xc) in Ha; with energies the
+ * call synchronises the stream. */
+pt_status pt_hxc_potential(pt_ctx* ctx, const double* rho, const double* vloc, const pt_grid* grid, double* v,
+                           double* energies, void* stream);
+
 /* ---- occupation matrix (Sec. IV-A1, Eq. diag_sigma) -------------------------------------- */
 
 /* sigma = Q diag(d) Q^* for Hermitian sigma (its Hermitian part is used), FP64
@@ -234,7 +254,11 @@ typedef struct {
   int anderson_depth;    /* mixing history (<= 20) */
   double anderson_beta;  /* mixing parameter */
   int use_ace;           /* 1: PT-IM-ACE double loop; 0: V_x applied exactly every iteration */
-  double spin;           /* spin factor of the reported energies (2 = closed shell) */
+  double spin;           /* electrons per orbital: spin factor of the reported energies and of
+                            rho = spin * P(r, r) (2 = closed shell) */
+  int hxc;               /* 0: the local potential is vloc alone (V_ext + V_Hxc frozen);
+                            1: vloc + V_Hxc[rho_{n+1/2}] rebuilt from the midpoint density in
+                            every inner iteration (Eq. 1 with Eq. p_tilde; see pt_hxc_potential) */
 } pt_ptim_params;
 
 typedef struct {
@@ -250,7 +274,8 @@ typedef struct {
      0 exchange, 1 ACE build (Gram, Cholesky, xi), 2 ACE apply, 3 H application,
      4 subspace contractions (A, S, projection), 5 subspace N x N (Cholesky, inverse, S^{-1}A),
      6 sigma diagonalisation, 7 rotations into/out of the sigma eigenbasis, 8 sigma commutator,
-     9 Anderson mixing and residual norms, 10 final Loewdin orthonormalisation, 11 spare */
+     9 Anderson mixing and residual norms, 10 final Loewdin orthonormalisation,
+     11 V_Hxc (midpoint density, Hartree FFT, LDA; params.hxc = 1) */
   double phase_ms[12];
 } pt_ptim_stats;
 

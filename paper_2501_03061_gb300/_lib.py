@@ -29,7 +29,7 @@ class pt_exchange_item(C.Structure):
 class pt_ptim_params(C.Structure):
     _fields_ = [("dt", C.c_double), ("alpha", C.c_double), ("ecut", C.c_double), ("tol", C.c_double),
                 ("max_outer", C.c_int), ("max_inner", C.c_int), ("anderson_depth", C.c_int),
-                ("anderson_beta", C.c_double), ("use_ace", C.c_int), ("spin", C.c_double)]
+                ("anderson_beta", C.c_double), ("use_ace", C.c_int), ("spin", C.c_double), ("hxc", C.c_int)]
 
 
 class pt_ptim_stats(C.Structure):
@@ -38,7 +38,7 @@ class pt_ptim_stats(C.Structure):
                 ("exchange_calls", C.c_int), ("exchange_ms", C.c_double), ("phase_ms", C.c_double * 12)]
 
 PHASES = ("exchange", "ace_build", "ace_apply", "apply_H", "subspace_gemm", "subspace_nxn", "sigma_eig",
-          "sigma_rot", "commutator", "anderson", "loewdin", "spare")
+          "sigma_rot", "commutator", "anderson", "loewdin", "hxc")
 
 
 vp = C.c_void_p
@@ -63,6 +63,8 @@ PROTOTYPES = {
     "pt_rotate": (i32, [vp, vp, i32, vp, i32, C.POINTER(pt_grid), i32, vp, vp]),
     "pt_apply_H": (i32, [vp, vp, i32, vp, vp, vp, C.c_double, C.c_double, C.POINTER(pt_grid), i32, vp]),
     "pt_diag_occupations": (i32, [vp, vp, i32, vp, vp, vp]),
+    "pt_density": (i32, [vp, vp, vp, i32, C.POINTER(pt_grid), i32, C.c_double, vp, vp]),
+    "pt_hxc_potential": (i32, [vp, vp, vp, C.POINTER(pt_grid), vp, C.POINTER(C.c_double), vp]),
     "pt_ptim_step": (i32, [vp, vp, vp, i32, vp, C.POINTER(pt_grid), C.POINTER(pt_kernel),
                            C.POINTER(pt_ptim_params), i32, C.POINTER(pt_ptim_stats), vp]),
     "pt_ptim_footprint": (C.c_size_t, [i32, C.POINTER(pt_grid), i32, i32]),

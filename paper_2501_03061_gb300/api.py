@@ -233,6 +233,33 @@ class Context:
         self._check(st, "pt_apply_H")
         return out
 
+    # ---- self-consistent local potential ------------------------------------------------------
+    def density(self, phi, sigma, *, cell, precision="fp64", spin=2.0, out=None, stream=None):
+        """rho = spin * P(r, r), P = Phi sigma Phi^* (float64 tensor shaped like one orbital)."""
+        self._orb(phi, precision, "phi")
+        sigma = sigma.to(device=self.device, dtype=torch.complex128).contiguous()
+        if out is None:
+            out = torch.empty(phi.shape[1:], dtype=torch.float64, device=self.device)
+        g = _grid(cell)
+        st = self.lib.pt_density(self.h, _ptr(phi), _ptr(sigma), phi.shape[0], C.byref(g), L.PRECISIONS[precision],
+                                 float(spin), _ptr(out), _stream(stream))
+        self._check(st, "pt_density")
+        return out
+
+    def hxc_potential(self, rho, vloc=None, *, cell, energies=False, out=None, stream=None):
+        """vloc + V_H[rho] + v_xc(rho) (FP64); with energies=True also returns (E_H, E_xc)."""
+        rho = rho.to(device=self.device, dtype=torch.float64).contiguous()
+        if vloc is not None:
+            vloc = vloc.to(device=self.device, dtype=torch.float64).contiguous()
+        if out is None:
+            out = torch.empty_like(rho)
+        g = _grid(cell)
+        e = (C.c_double * 2)()
+        st = self.lib.pt_hxc_potential(self.h, _ptr(rho), None if vloc is None else _ptr(vloc), C.byref(g),
+                                       _ptr(out), e if energies else None, _stream(stream))
+        self._check(st, "pt_hxc_potential")
+        return (out, (float(e[0]), float(e[1]))) if energies else out
+
     # ---- occupations ----------------------------------------------------------------------
     def diag_occupations(self, sigma, stream=None):
         sigma = sigma.to(device=self.device, dtype=torch.complex128).contiguous()
@@ -246,14 +273,14 @@ class Context:
     # ---- PT-IM step -------------------------------------------------------------------------
     def ptim_step(self, phi, sigma, vloc, *, cell, kernel=None, precision="fp64", dt=0.5, alpha=0.25, ecut=10.0,
                   tol=1e-6, max_outer=30, max_inner=200, anderson_depth=20, anderson_beta=1.0, use_ace=True,
-                  spin=2.0, stream=None, allow_unconverged=False):
+                  spin=2.0, hxc=False, stream=None, allow_unconverged=False):
         """Advance (phi, sigma) by one PT-IM(-ACE) step in place; returns the step statistics."""
         self._orb(phi, precision, "phi")
         if sigma.dtype != torch.complex128 or not sigma.is_contiguous() or sigma.device != self.device:
             raise ValueError("sigma must be a contiguous complex128 tensor on the device")
         vloc = vloc.to(device=self.device, dtype=torch.float64).contiguous()
         p = L.pt_ptim_params(dt, alpha, ecut, tol, max_outer, max_inner, anderson_depth, anderson_beta,
-                             int(bool(use_ace)), spin)
+                             int(bool(use_ace)), spin, int(bool(hxc)))
         s = L.pt_ptim_stats()
         g, k = _grid(cell), _kernel(kernel)
         st = self.lib.pt_ptim_step(self.h, _ptr(phi), _ptr(sigma), phi.shape[0], _ptr(vloc), C.byref(g), C.byref(k),

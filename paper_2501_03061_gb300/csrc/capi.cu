@@ -1,5 +1,6 @@
 // The exported C ABI (include/ptim.h): argument checks, context, error conversion.
 #include <cstring>
+#include <vector>
 
 #include "common.cuh"
 #include "internal.h"
@@ -398,6 +399,59 @@ pt_status pt_apply_H(pt_ctx* ctx, const void* psi, int M, void* out, const doubl
   });
 }
 
+pt_status pt_density(pt_ctx* ctx, const void* phi, const void* sigma, int N, const pt_grid* grid, pt_precision prec,
+                     double spin, double* rho, void* stream) {
+  return guarded(ctx, [&]() -> pt_status {
+    check_common(ctx, grid, prec);
+    if (N <= 0) pt::fail(PT_INVALID_ARG, "N must be positive");
+    if (!phi || !sigma || !rho) pt::fail(PT_INVALID_ARG, "NULL buffer");
+    if (!(spin > 0.0)) pt::fail(PT_INVALID_ARG, "spin must be positive");
+    pt::require_aligned(phi, "phi");
+    set_device(ctx);
+    set_engine(ctx, prec);
+    auto st = static_cast<cudaStream_t>(stream);
+    const size_t ng = pt::ng_of(*grid);
+    void* chi = ctx->get("density_chi", ng * size_t(N) * pt::elem_bytes(prec));
+    if (prec == PT_FP64)
+      pt::density<double>(ctx, static_cast<const c128*>(phi), static_cast<const c128*>(sigma), N, ng, spin,
+                          static_cast<c128*>(chi), rho, st);
+    else
+      pt::density<float>(ctx, static_cast<const c64*>(phi), static_cast<const c128*>(sigma), N, ng, spin,
+                         static_cast<c64*>(chi), rho, st);
+    if (ctx->active_tc || ctx->bf16_requested) pt::gram_tc_check(ctx, st);
+    return PT_OK;
+  });
+}
+
+pt_status pt_hxc_potential(pt_ctx* ctx, const double* rho, const double* vloc, const pt_grid* grid, double* v,
+                           double* energies, void* stream) {
+  return guarded(ctx, [&]() -> pt_status {
+    if (!ctx) pt::fail(PT_INVALID_ARG, "context is NULL");
+    pt::validate_grid(grid);
+    if (!rho || !v) pt::fail(PT_INVALID_ARG, "NULL buffer");
+    if (v == rho) pt::fail(PT_INVALID_ARG, "v must not alias rho");
+    set_device(ctx);
+    auto st = static_cast<cudaStream_t>(stream);
+    double* part = energies ? static_cast<double*>(ctx->get("hxc_part", 2 * size_t(grid->nz) * sizeof(double)))
+                            : nullptr;
+    pt::hxc_potential(ctx, rho, vloc, *grid, v, part, st);
+    if (energies) {
+      std::vector<double> h(2 * size_t(grid->nz));
+      PT_CUDA_CHECK(cudaMemcpyAsync(h.data(), part, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+      PT_CUDA_CHECK(cudaStreamSynchronize(st));
+      double eh = 0.0, exc = 0.0;
+      for (int z = 0; z < grid->nz; ++z) {
+        eh += h[2 * z];
+        exc += h[2 * z + 1];
+      }
+      const double dv = pt::dv_of(*grid);
+      energies[0] = eh * dv;
+      energies[1] = exc * dv;
+    }
+    return PT_OK;
+  });
+}
+
 pt_status pt_diag_occupations(pt_ctx* ctx, const void* sigma, int N, void* Q, double* d, void* stream) {
   return guarded(ctx, [&]() -> pt_status {
     if (!ctx) pt::fail(PT_INVALID_ARG, "context is NULL");
@@ -422,7 +476,7 @@ pt_status pt_ptim_step(pt_ctx* ctx, void* phi, void* sigma, int N, const double*
     if (!vloc) pt::fail(PT_INVALID_ARG, "vloc is NULL");
     const pt_ptim_params& P = *params;
     if (!(P.dt > 0) || !(P.tol > 0) || P.max_inner <= 0 || P.max_outer <= 0 || P.anderson_depth <= 0 ||
-        P.anderson_depth > 20)
+        P.anderson_depth > 20 || (P.hxc != 0 && P.hxc != 1) || (P.hxc && !(P.spin > 0)))
       pt::fail(PT_INVALID_ARG, "invalid PT-IM parameters");
     set_device(ctx);
     set_engine(ctx, prec);
@@ -451,7 +505,8 @@ size_t pt_ptim_footprint(int N, const pt_grid* grid, pt_precision prec, int ande
   const size_t gram_parts = size_t(4 * 160 + 64) * nn;  // split partials, bounded by 4 waves of tiles
   const size_t blocks = (12 + 2 * size_t(depth)) * block;
   const size_t small = 40 * nn + (size_t(64) << 20);
-  return blocks + exch + hscr + std::min(gram_parts, size_t(8) * block) + small;
+  const size_t hxc = 4 * ng * sizeof(double);  // rho, total potential, FFT scratch (params.hxc = 1)
+  return blocks + exch + hscr + std::min(gram_parts, size_t(8) * block) + small + hxc;
 }
 
 const char* pt_version(void) { return "ptim-gb300 0.1 (sm_103a)"; }

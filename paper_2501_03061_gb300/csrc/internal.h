@@ -51,6 +51,15 @@ void rotate_tc(pt_ctx* ctx, const c64* A, const c128* Bm, int ldb, int N1, int N
                const Term* terms, int nterms, c64* out, cudaStream_t st, bool split3);
 bool rotate_tc_applies(const void* A, size_t ng);
 
+// ---- self-consistent local potential (hxc.cu) ----
+// rho = spin * Re sum_ij sigma_ij phi_i conj(phi_j) (chi: Ng x N scratch of the block's precision)
+template <class T>
+void density(pt_ctx* ctx, const cx<T>* phi, const c128* sigma, int N, size_t ng, double spin, cx<T>* chi,
+             double* rho, cudaStream_t st);
+// v = vloc (may be null) + V_H[rho] + v_xc(rho); part (may be null): 2 nz per-plane sums (E_H, E_xc) / dV
+void hxc_potential(pt_ctx* ctx, const double* rho, const double* vloc, const pt_grid& g, double* v, double* part,
+                   cudaStream_t st);
+
 // ---- BF16 tensor-core contractions (contract_bf16.cu): operands packed to bf16, FP32 accumulation ----
 void gram_bf16(pt_ctx* ctx, const c64* A, const c64* B, int N1, int N2, size_t ng, double scale, c128* C,
                cudaStream_t st, bool herm);

@@ -57,7 +57,7 @@ class PhaseTimer {
   cudaStream_t st_;
   std::vector<Rec> recs_;
 };
-enum { PH_EXCH = 0, PH_ACE_BUILD, PH_ACE_APPLY, PH_H, PH_SUB, PH_SUBNN, PH_EIG, PH_ROT, PH_COMM, PH_AND, PH_LOEW };
+enum { PH_EXCH = 0, PH_ACE_BUILD, PH_ACE_APPLY, PH_H, PH_SUB, PH_SUBNN, PH_EIG, PH_ROT, PH_COMM, PH_AND, PH_LOEW, PH_HXC };
 
 __global__ void k_maxabs_diff(const c128* __restrict__ A, const c128* __restrict__ B, int n, double* __restrict__ out) {
   double m = 0;
@@ -203,6 +203,9 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
   double* rhs = static_cast<double*>(S.buf("ptim_rhs", kMaxDepth * sizeof(double)));
   double* gamma = static_cast<double*>(S.buf("ptim_gamma", kMaxDepth * sizeof(double)));
   int* idx_d = static_cast<int*>(S.buf("ptim_idx", 2 * kMaxDepth * sizeof(int)));
+  // self-consistent V_Hxc: midpoint density and the total local potential V_loc + V_Hxc[rho_h]
+  double* rho = P.hxc ? static_cast<double*>(S.buf("ptim_rho", S.ng * sizeof(double))) : nullptr;
+  double* vtot = P.hxc ? static_cast<double*>(S.buf("ptim_vtot", S.ng * sizeof(double))) : nullptr;
 
   PT_CUDA_CHECK(cudaMemcpyAsync(phin, phi, fb, cudaMemcpyDeviceToDevice, st));
   PT_CUDA_CHECK(cudaMemcpyAsync(sign, sig, mb, cudaMemcpyDeviceToDevice, st));
@@ -322,6 +325,16 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
       cx<T>* rphi = rphi_buf[inner & 1];
       c128* rsig = rsig_buf[inner & 1];
       S.midpoint(phih, sigh, phi, phin, sig, sign);
+      const double* vh = vloc;
+      if (P.hxc) {
+        // H_{n+1/2} = H[P_{n+1/2}] (Eq. p_tilde): rho_h = spin P_h(r, r); X is free until the
+        // exchange term below, so it holds chi = Phi_h sigma_h
+        tm.begin(PH_HXC);
+        density<T>(ctx, phih, sigh, N, S.ng, P.spin, X, rho, st);
+        hxc_potential(ctx, rho, vloc, g, vtot, nullptr, st);
+        tm.end();
+        vh = vtot;
+      }
       if (P.use_ace) {
         tm.begin(PH_ACE_APPLY);
         ace_apply(ctx, xi, N, phih, N, X, g, prec, st);
@@ -330,7 +343,7 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
         exchange_on_midpoint(X, inner == 0);
       }
       tm.begin(PH_H);
-      apply_h(ctx, phih, N, Hphi, vloc, X, P.alpha, P.ecut, g, prec, st);
+      apply_h(ctx, phih, N, Hphi, vh, X, P.alpha, P.ecut, g, prec, st);
       tm.end();
       tm.begin(PH_SUB);
       // A = <Phi_h|H Phi_h> and S = <Phi_h|Phi_h> are Hermitian: upper tiles only, mirrored
