@@ -28,7 +28,10 @@ ACE identity, triple-sum vs diagonalised exchange, PT-IM invariants, the
 Cayley closed form, stationary states, energy conservation and an RK4
 cross-check; for V_Hxc: the Hartree potential of cosine densities, the Slater
 constant, the Perdew-Zunger high-density limit and branch continuity, potentials
-as derivatives of their energies, and PT-IM with V_Hxc[rho(t)] against RK4).  The Anderson trajectory itself (iteration counts, the exact
+as derivatives of their energies, and PT-IM with V_Hxc[rho(t)] against RK4; for
+the velocity-gauge field: plane-wave eigenvalues 1/2 |G + A|^2, the Cayley
+closed form under a constant field, the current of plane waves, and PT-IM with
+A(t_{n+1/2}) against RK4 with A(t)).  The Anderson trajectory itself (iteration counts, the exact
 stop point) is parity unpinned: only converged states are compared.
 """
 from __future__ import annotations
@@ -239,10 +242,29 @@ def sphere_mask(g: Grid, ecut: float) -> np.ndarray:
     return (0.5 * g_squared(g) <= ecut).astype(np.float64)
 
 
-def apply_kinetic_local(phi: np.ndarray, vloc: np.ndarray, g: Grid) -> np.ndarray:
-    """(-1/2 Laplacian + V_loc) phi without projection: kinetic by FFT, potential pointwise."""
-    g2 = g_squared(g)
-    kin = np.fft.ifftn(0.5 * g2 * np.fft.fftn(phi, axes=FFT_AXES), axes=FFT_AXES)
+def g_vectors(g: Grid):
+    """(Gx, Gy, Gz) on the grid, each broadcast to (nz, ny, nx); G = 2 pi m / L, m wrapped."""
+    gx = 2 * np.pi * _wrapped(g.nx) / g.Lx
+    gy = 2 * np.pi * _wrapped(g.ny) / g.Ly
+    gz = 2 * np.pi * _wrapped(g.nz) / g.Lz
+    shape = (g.nz, g.ny, g.nx)
+    return (np.broadcast_to(gx[None, None, :], shape), np.broadcast_to(gy[None, :, None], shape),
+            np.broadcast_to(gz[:, None, None], shape))
+
+
+def kinetic_factor(g: Grid, A=None) -> np.ndarray:
+    """1/2 |G + A|^2: the kinetic operator 1/2 (-i grad + A)^2 of the velocity gauge in G space
+    (Eq. 1's V_ext(t) for a spatially uniform field E(t) = -dA/dt in a periodic cell; A = 0 is the
+    field-free 1/2 |G|^2)."""
+    if A is None or not np.any(A):
+        return 0.5 * g_squared(g)
+    G = g_vectors(g)
+    return 0.5 * sum((G[a] + A[a]) ** 2 for a in range(3))
+
+
+def apply_kinetic_local(phi: np.ndarray, vloc: np.ndarray, g: Grid, A=None) -> np.ndarray:
+    """(1/2 (-i grad + A)^2 + V_loc) phi without projection: kinetic by FFT, potential pointwise."""
+    kin = np.fft.ifftn(kinetic_factor(g, A) * np.fft.fftn(phi, axes=FFT_AXES), axes=FFT_AXES)
     return kin + vloc[None] * phi
 
 
@@ -252,14 +274,18 @@ def project_sphere(psi: np.ndarray, g: Grid, ecut: float) -> np.ndarray:
     return np.fft.ifftn(mask * np.fft.fftn(psi, axes=FFT_AXES), axes=FFT_AXES)
 
 
-def apply_H(phi: np.ndarray, vloc: np.ndarray, g: Grid, ecut: float, alpha: float, vx_phi: np.ndarray) -> np.ndarray:
-    """H phi = P_sph[ -1/2 Lap phi + V_loc phi + alpha V_x phi ]   (Eq. 1 with frozen V_Hxc+V_ext).
+def apply_H(phi: np.ndarray, vloc: np.ndarray, g: Grid, ecut: float, alpha: float, vx_phi: np.ndarray,
+            A=None) -> np.ndarray:
+    """H phi = P_sph[ 1/2 (-i grad + A)^2 phi + V_loc phi + alpha V_x phi ]   (Eq. 1).
 
     vx_phi is V_x phi computed by the caller (exactly or through ACE).  The
     projection onto the Ecut sphere keeps the propagation in the plane-wave
-    basis of the paper (Ecut = 10 Ha); pair densities inside V_x are not masked.
+    basis of the paper (Ecut = 10 Ha; the sphere is the field-free |G|^2/2 <=
+    Ecut, the basis does not move with A); pair densities inside V_x are not
+    masked.  A: the uniform vector potential of V_ext(t) (None: no field).  V_x
+    needs no field term: as a functional of P it is gauge covariant.
     """
-    y = apply_kinetic_local(phi, vloc, g) + alpha * vx_phi
+    y = apply_kinetic_local(phi, vloc, g, A) + alpha * vx_phi
     return project_sphere(y, g, ecut)
 
 
@@ -353,6 +379,7 @@ class PtimParams:
     use_ace: bool = True
     hxc: bool = False             # V_Hxc[rho_h] from the midpoint density in every iteration
     spin: float = 2.0             # electrons per orbital in rho = spin * P(r, r)
+    A: tuple = (0.0, 0.0, 0.0)    # vector potential A(t_{n+1/2}) of V_ext at the step's midpoint time
 
 
 @dataclasses.dataclass
@@ -414,7 +441,8 @@ def ptim_step(phi_n: np.ndarray, sigma_n: np.ndarray, vloc: np.ndarray, g: Grid,
     map (Eq. lisan, read with balanced parentheses):
         T_Phi   = Phi_n   - i dt (I - Pt) H Phi_h,   Pt = Phi_h S^{-1} Phi_h^*,  S = Phi_h^* Phi_h
         T_sigma = sigma_n - i dt [A, sigma_h],        A = Phi_h^* H Phi_h
-    with H = H[P_h], P_h = Phi_h sigma_h Phi_h^* (Eq. p_tilde); with p.hxc the local potential
+    with H = H(t_{n+1/2}, P_h), P_h = Phi_h sigma_h Phi_h^* (Eq. p_tilde): the time enters through
+    p.A = A(t_{n+1/2}), the caller's vector potential at the midpoint time; with p.hxc the local potential
     is V_loc + V_Hxc[spin * P_h(r, r)], else V_loc alone (V_ext + V_Hxc frozen).  Initial guess:
     x = (Phi_n, sigma_n).  Outer loop: diagonalise sigma_h, W = V_x[P_h] Phi_h,
     ACE from (Phi_h, W).  Inner loop: Anderson on x = T(x) with the ACE frozen
@@ -466,7 +494,7 @@ def ptim_step(phi_n: np.ndarray, sigma_n: np.ndarray, vloc: np.ndarray, g: Grid,
             v = vloc
             if p.hxc:  # H_{n+1/2} = H[P_{n+1/2}] (Eq. p_tilde): V_Hxc from rho of the midpoint
                 v = vloc + hxc_potential(p.spin * density(phi_h, sig_h).real, g)
-            Hphi = apply_H(phi_h, v, g, p.ecut, p.alpha, exch(phi_h, sig_h))
+            Hphi = apply_H(phi_h, v, g, p.ecut, p.alpha, exch(phi_h, sig_h), np.asarray(p.A, dtype=float))
             A = overlap(phi_h, Hphi, dV)
             S = overlap(phi_h, phi_h, dV)
             SinvA = np.linalg.solve(S, A)
@@ -509,14 +537,31 @@ def density(phi: np.ndarray, sigma: np.ndarray) -> np.ndarray:
     return np.einsum("ir,ij,jr->r", P, sigma, P.conj()).reshape(phi.shape[1:])
 
 
+def current(phi: np.ndarray, sigma: np.ndarray, g: Grid, A=None, spin: float = 2.0) -> np.ndarray:
+    """Cell-averaged velocity density J = (spin/Omega) Re Tr[P (-i grad + A)], P = Phi sigma Phi^*.
+
+    Tr[P O] = sum_ij sigma_ij <phi_j|O phi_i>; -i grad is G in Fourier space.  This is the
+    observable of a velocity-gauge run (the electric current is -J for electrons of charge -1).
+    """
+    A = np.zeros(3) if A is None else np.asarray(A, dtype=float)
+    G = g_vectors(g)
+    fphi = np.fft.fftn(phi, axes=FFT_AXES)
+    out = np.zeros(3)
+    for a in range(3):
+        dphi = np.fft.ifftn((G[a] + A[a])[None] * fphi, axes=FFT_AXES)  # (-i d_a + A_a) phi_i
+        B = overlap(phi, dphi, g.dV)  # B[j, i] = <phi_j|(-i d_a + A_a) phi_i>
+        out[a] = spin / g.volume * float(np.real(np.sum(sigma * B.T)))
+    return out
+
+
 def total_energy(phi: np.ndarray, sigma: np.ndarray, vloc: np.ndarray, g: Grid, K: np.ndarray,
-                 ecut: float, alpha: float = 0.25, spin: float = 2.0, hxc: bool = False) -> float:
+                 ecut: float, alpha: float = 0.25, spin: float = 2.0, hxc: bool = False, A=None) -> float:
     """E = spin * Tr[P (-1/2 Lap + V_loc)] + spin*(alpha/2) Tr[P V_x[P]] (+ E_H + E_xc), P = Phi sigma Phi^*.
 
     Tr[P O] = sum_ij sigma_ij <phi_j|O phi_i>.  The energy whose functional
     derivative is spin*H for the Hamiltonian used here (with hxc, rho = spin P(r, r)).
     """
-    hphi = project_sphere(apply_kinetic_local(phi, vloc, g), g, ecut)
+    hphi = project_sphere(apply_kinetic_local(phi, vloc, g, A), g, ecut)
     B = overlap(phi, hphi, g.dV)  # B[j, i] = <phi_j|h phi_i>
     e_one = spin * np.real(np.sum(sigma * B.T))
     e = e_one + exchange_energy(phi, sigma, K, g.dV, alpha, spin)
