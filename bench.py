@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--hxc", action="store_true",
                     help="rebuild V_Hxc[rho] (Hartree + LDA) from the midpoint density in every inner iteration "
                          "instead of keeping the local potential frozen")
+    ap.add_argument("--field", type=float, default=0.0,
+                    help="peak vector potential A0 (bohr^-1) of a sin^2-enveloped pulse along x (velocity gauge); "
+                         "0: no field")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 form comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
@@ -486,16 +489,28 @@ def run_gb300(args):
     workload = WORKLOAD if N == 320 else WORKLOAD.replace("N320", f"N{N}")
     if args.hxc:
         workload = workload.replace("ptim_ace_step", "ptim_ace_hxc_step")
+    if args.field:
+        workload = workload.replace("_step_", "_field_step_")
     kw = dict(cell=w.cell, kernel=w.kernel, precision=args.precision, dt=0.5, alpha=0.25, ecut=10.0,
               tol=args.tol, max_outer=20, max_inner=100, anderson_depth=20, hxc=args.hxc, allow_unconverged=True)
     stream = torch.cuda.current_stream()
+    # sin^2-enveloped pulse (omega = 0.057 Ha, 800 nm; 20 fs envelope), started at its peak region
+    pulse_T, pulse_w, t_clock = 826.0, 0.057, [413.0]
+
+    def step_kw():
+        if not args.field:
+            return kw
+        t = t_clock[0] + 0.25  # midpoint time of a dt = 0.5 step
+        t_clock[0] += 0.5
+        a = args.field * math.sin(math.pi * t / pulse_T) ** 2 * math.sin(pulse_w * t)
+        return dict(kw, A=(a, 0.0, 0.0))
 
     def barrier():
         if world > 1:
             dist.barrier()
 
     for _ in range(args.warmup):
-        ctx.ptim_step(phi, sigma, vloc, **kw)
+        ctx.ptim_step(phi, sigma, vloc, **step_kw())
     torch.cuda.synchronize()
 
     sampler = ClockSampler() if rank == 0 else None
@@ -508,7 +523,7 @@ def run_gb300(args):
     ev0.record(stream)
     stats = []
     for _ in range(args.steps):
-        stats.append(ctx.ptim_step(phi, sigma, vloc, **kw))
+        stats.append(ctx.ptim_step(phi, sigma, vloc, **step_kw()))
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -552,7 +567,7 @@ def run_gb300(args):
             dphi = hphi.to(devc, non_blocking=True)
             dsig = hsig.to(devc, non_blocking=True)
             dv = hv.to(devc, non_blocking=True)
-            ctx.ptim_step(dphi, dsig, dv, **kw)
+            ctx.ptim_step(dphi, dsig, dv, **step_kw())
             ophi.copy_(dphi, non_blocking=True)
             osig.copy_(dsig, non_blocking=True)
             torch.cuda.current_stream().synchronize()
@@ -620,6 +635,8 @@ def run_gb300(args):
                        "contraction_engine": "tcgen05 3xTF32" if args.tc_gram else "CUDA cores",
                        "local_potential": ("V_loc + V_Hxc[rho_h] (Hartree + LDA), rebuilt every inner iteration"
                                            if args.hxc else "V_loc (V_ext + V_Hxc frozen)"),
+                       "field": ({"gauge": "velocity", "A0": args.field, "omega_Ha": pulse_w, "envelope_au": pulse_T,
+                                  "t_start_au": 413.0} if args.field else None),
                        "l2": "inputs larger than L2 (phi alone is %d MB)" % (N * ng * esz >> 20)},
             "pair_ffts_per_s": pair_ffts / (ms / 1e3) if ms > 0 else None,
             "exchange": {"pair_ffts": pair_ffts, "calls": ex_calls, "ms": ex_ms,

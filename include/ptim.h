@@ -206,14 +206,24 @@ pt_status pt_overlap(pt_ctx* ctx, const void* A, int N1, const void* B, int N2, 
 pt_status pt_rotate(pt_ctx* ctx, const void* A, int N1, const void* B, int N2, const pt_grid* grid,
                     pt_precision prec, void* out, void* stream);
 
-/* ---- Hamiltonian (Eq. 1 with frozen V_Hxc + V_ext) -------------------------------------- */
+/* ---- Hamiltonian (Eq. 1) ----------------------------------------------------------------- */
 
-/* out = P_sph[ -1/2 Lap psi + vloc * psi + alpha * V_ACE psi ], the projection
- * P_sph keeping the plane waves with |G|^2/2 <= ecut.  ace may be NULL (no
- * exchange term).  vloc: Ng doubles (device).  psi/out Ng x M, out != psi. */
+/* out = P_sph[ 1/2 (-i grad + A)^2 psi + vloc * psi + alpha * V_ACE psi ], the projection
+ * P_sph keeping the plane waves with |G|^2/2 <= ecut (the sphere does not move with A).
+ * ace may be NULL (no exchange term).  vloc: Ng doubles (device; V_ext's scalar part and
+ * V_Hxc, frozen or from pt_hxc_potential).  A: NULL (no field) or a host array of 3 doubles,
+ * the uniform vector potential of the velocity gauge (V_ext(t) of Eq. 1 for a field
+ * E(t) = -dA/dt).  psi/out Ng x M, out != psi. */
 pt_status pt_apply_H(pt_ctx* ctx, const void* psi, int M, void* out, const double* vloc,
-                     const pt_ace* ace, double alpha, double ecut, const pt_grid* grid,
+                     const pt_ace* ace, double alpha, double ecut, const double* A, const pt_grid* grid,
                      pt_precision prec, void* stream);
+
+/* The velocity-gauge current J_a = spin/Omega Re Tr[P (-i d_a + A_a)], P = Phi sigma Phi^*
+ * (Tr[P O] = sum_ij sigma_ij <phi_j|O phi_i>; the electric current density of electrons is -J).
+ * phi: Ng x N device orbitals (precision prec, 16-byte aligned); sigma: N x N complex128 device;
+ * A: NULL or host double[3]; J: host double[3].  Synchronises the stream. */
+pt_status pt_current(pt_ctx* ctx, const void* phi, const void* sigma, int N, const pt_grid* grid, pt_precision prec,
+                     const double* A, double spin, double* J, void* stream);
 
 /* ---- self-consistent local potential (Eq. 1: V_Hxc[P]) ------------------------------------ */
 
@@ -259,6 +269,9 @@ typedef struct {
   int hxc;               /* 0: the local potential is vloc alone (V_ext + V_Hxc frozen);
                             1: vloc + V_Hxc[rho_{n+1/2}] rebuilt from the midpoint density in
                             every inner iteration (Eq. 1 with Eq. p_tilde; see pt_hxc_potential) */
+  double A[3];           /* V_ext(t) as a uniform vector potential (velocity gauge, bohr^-1): the
+                            value A(t_n + dt/2) at the step's midpoint time (Eq. p_tilde's
+                            H(t_{n+1/2}, P)), supplied by the caller; {0, 0, 0}: no field */
 } pt_ptim_params;
 
 typedef struct {

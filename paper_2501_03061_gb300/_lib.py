@@ -29,7 +29,8 @@ class pt_exchange_item(C.Structure):
 class pt_ptim_params(C.Structure):
     _fields_ = [("dt", C.c_double), ("alpha", C.c_double), ("ecut", C.c_double), ("tol", C.c_double),
                 ("max_outer", C.c_int), ("max_inner", C.c_int), ("anderson_depth", C.c_int),
-                ("anderson_beta", C.c_double), ("use_ace", C.c_int), ("spin", C.c_double), ("hxc", C.c_int)]
+                ("anderson_beta", C.c_double), ("use_ace", C.c_int), ("spin", C.c_double), ("hxc", C.c_int),
+                ("A", C.c_double * 3)]
 
 
 class pt_ptim_stats(C.Structure):
@@ -61,7 +62,10 @@ PROTOTYPES = {
     "pt_ace_destroy": (None, [vp]),
     "pt_overlap": (i32, [vp, vp, i32, vp, i32, C.POINTER(pt_grid), i32, vp, vp]),
     "pt_rotate": (i32, [vp, vp, i32, vp, i32, C.POINTER(pt_grid), i32, vp, vp]),
-    "pt_apply_H": (i32, [vp, vp, i32, vp, vp, vp, C.c_double, C.c_double, C.POINTER(pt_grid), i32, vp]),
+    "pt_apply_H": (i32, [vp, vp, i32, vp, vp, vp, C.c_double, C.c_double, C.POINTER(C.c_double),
+                         C.POINTER(pt_grid), i32, vp]),
+    "pt_current": (i32, [vp, vp, vp, i32, C.POINTER(pt_grid), i32, C.POINTER(C.c_double), C.c_double,
+                         C.POINTER(C.c_double), vp]),
     "pt_diag_occupations": (i32, [vp, vp, i32, vp, vp, vp]),
     "pt_density": (i32, [vp, vp, vp, i32, C.POINTER(pt_grid), i32, C.c_double, vp, vp]),
     "pt_hxc_potential": (i32, [vp, vp, vp, C.POINTER(pt_grid), vp, C.POINTER(C.c_double), vp]),

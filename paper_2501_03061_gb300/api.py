@@ -10,6 +10,7 @@ from __future__ import annotations
 import ctypes as C
 import math
 
+import numpy as np
 import torch
 
 from . import _lib as L
@@ -47,6 +48,16 @@ def _stream(stream):
 
 def _ptr(t: torch.Tensor):
     return C.c_void_p(t.data_ptr())
+
+
+def _vec3(A):
+    """A host double[3] for an optional 3-vector argument (None -> NULL)."""
+    if A is None:
+        return None
+    a = [float(v) for v in A]
+    if len(a) != 3:
+        raise ValueError("A must have 3 components")
+    return (C.c_double * 3)(*a)
 
 
 class Ace:
@@ -221,17 +232,29 @@ class Context:
 
     # ---- Hamiltonian ------------------------------------------------------------------------
     def apply_H(self, psi, vloc, ace: Ace | None = None, alpha=0.25, ecut=10.0, *, cell, precision="fp64",
-                out=None, stream=None):
+                A=None, out=None, stream=None):
+        """H psi with the velocity-gauge vector potential A (3 floats, or None for no field)."""
         self._orb(psi, precision, "psi")
         vloc = vloc.to(device=self.device, dtype=torch.float64).contiguous()
         if out is None:
             out = torch.empty_like(psi)
         g = _grid(cell)
         st = self.lib.pt_apply_H(self.h, _ptr(psi), psi.shape[0], _ptr(out), _ptr(vloc),
-                                 None if ace is None else ace.handle, float(alpha), float(ecut), C.byref(g),
-                                 L.PRECISIONS[precision], _stream(stream))
+                                 None if ace is None else ace.handle, float(alpha), float(ecut), _vec3(A),
+                                 C.byref(g), L.PRECISIONS[precision], _stream(stream))
         self._check(st, "pt_apply_H")
         return out
+
+    def current(self, phi, sigma, *, cell, precision="fp64", A=None, spin=2.0, stream=None):
+        """J = spin/Omega Re Tr[P (-i grad + A)] as a (3,) numpy array (synchronises the stream)."""
+        self._orb(phi, precision, "phi")
+        sigma = sigma.to(device=self.device, dtype=torch.complex128).contiguous()
+        g = _grid(cell)
+        J = (C.c_double * 3)()
+        st = self.lib.pt_current(self.h, _ptr(phi), _ptr(sigma), phi.shape[0], C.byref(g), L.PRECISIONS[precision],
+                                 _vec3(A), float(spin), J, _stream(stream))
+        self._check(st, "pt_current")
+        return np.array([J[0], J[1], J[2]])
 
     # ---- self-consistent local potential ------------------------------------------------------
     def density(self, phi, sigma, *, cell, precision="fp64", spin=2.0, out=None, stream=None):
@@ -273,14 +296,15 @@ class Context:
     # ---- PT-IM step -------------------------------------------------------------------------
     def ptim_step(self, phi, sigma, vloc, *, cell, kernel=None, precision="fp64", dt=0.5, alpha=0.25, ecut=10.0,
                   tol=1e-6, max_outer=30, max_inner=200, anderson_depth=20, anderson_beta=1.0, use_ace=True,
-                  spin=2.0, hxc=False, stream=None, allow_unconverged=False):
+                  spin=2.0, hxc=False, A=None, stream=None, allow_unconverged=False):
         """Advance (phi, sigma) by one PT-IM(-ACE) step in place; returns the step statistics."""
         self._orb(phi, precision, "phi")
         if sigma.dtype != torch.complex128 or not sigma.is_contiguous() or sigma.device != self.device:
             raise ValueError("sigma must be a contiguous complex128 tensor on the device")
         vloc = vloc.to(device=self.device, dtype=torch.float64).contiguous()
         p = L.pt_ptim_params(dt, alpha, ecut, tol, max_outer, max_inner, anderson_depth, anderson_beta,
-                             int(bool(use_ace)), spin, int(bool(hxc)))
+                             int(bool(use_ace)), spin, int(bool(hxc)),
+                             (C.c_double * 3)(*(A if A is not None else (0.0, 0.0, 0.0))))
         s = L.pt_ptim_stats()
         g, k = _grid(cell), _kernel(kernel)
         st = self.lib.pt_ptim_step(self.h, _ptr(phi), _ptr(sigma), phi.shape[0], _ptr(vloc), C.byref(g), C.byref(k),

@@ -374,7 +374,8 @@ void pt_ace_destroy(pt_ace* ace) {
 }
 
 pt_status pt_apply_H(pt_ctx* ctx, const void* psi, int M, void* out, const double* vloc, const pt_ace* ace,
-                     double alpha, double ecut, const pt_grid* grid, pt_precision prec, void* stream) {
+                     double alpha, double ecut, const double* A, const pt_grid* grid, pt_precision prec,
+                     void* stream) {
   return guarded(ctx, [&]() -> pt_status {
     check_common(ctx, grid, prec);
     if (M <= 0) pt::fail(PT_INVALID_ARG, "M must be positive");
@@ -393,8 +394,24 @@ pt_status pt_apply_H(pt_ctx* ctx, const void* psi, int M, void* out, const doubl
       pt::ace_apply(ctx, ace->xi, ace->N, psi, M, buf, *grid, prec, st);
       X = buf;
     }
-    pt::apply_h(ctx, psi, M, out, vloc, X, alpha, ecut, *grid, prec, st);
+    pt::apply_h(ctx, psi, M, out, vloc, X, alpha, ecut, *grid, prec, st, A);
     if ((ctx->active_tc || ctx->bf16_requested) && ace) pt::gram_tc_check(ctx, st);
+    return PT_OK;
+  });
+}
+
+pt_status pt_current(pt_ctx* ctx, const void* phi, const void* sigma, int N, const pt_grid* grid, pt_precision prec,
+                     const double* A, double spin, double* J, void* stream) {
+  return guarded(ctx, [&]() -> pt_status {
+    check_common(ctx, grid, prec);
+    if (N <= 0) pt::fail(PT_INVALID_ARG, "N must be positive");
+    if (!phi || !sigma || !J) pt::fail(PT_INVALID_ARG, "NULL buffer");
+    pt::require_aligned(phi, "phi");
+    set_device(ctx);
+    set_engine(ctx, prec);
+    auto st = static_cast<cudaStream_t>(stream);
+    pt::current(ctx, phi, static_cast<const c128*>(sigma), N, *grid, prec, A, spin, J, st);
+    if (ctx->active_tc || ctx->bf16_requested) pt::gram_tc_check(ctx, st);
     return PT_OK;
   });
 }

@@ -206,4 +206,25 @@ const FftTables& fft_tables(pt_ctx* ctx, const pt_grid& g, pt_precision prec);
 // K(G)/Ng on the whole grid (precision of prec), cached in the context.
 const void* kernel_table(pt_ctx* ctx, const pt_grid& g, const pt_kernel& k, pt_precision prec);
 
+// ------------------------------------------------------------------------------------------
+// velocity-gauge kinetic factor: 1/2 |G + A|^2 = 1/2 |G|^2 + sum_a m_a c_a + a2h with
+// c_a = 2 pi A_a / L_a and a2h = |A|^2 / 2 (m_a the wrapped integer frequency); A = 0 adds 0.0
+// ------------------------------------------------------------------------------------------
+struct KinField {
+  double c[3];
+  double a2h;
+  int on;  // 0: A = 0, the kinetic factor is 1/2 |G|^2 and no shift is evaluated
+};
+
+__host__ __device__ __forceinline__ int wrapped_freq(int i, int n) { return i < (n + 1) / 2 ? i : i - n; }
+
+__device__ __forceinline__ double kin_shift(const KinField& f, int x, int y, int z, int nx, int ny, int nz) {
+  if (!f.on) return 0.0;
+  return (double(wrapped_freq(x, nx)) * f.c[0] + double(wrapped_freq(y, ny)) * f.c[1] +
+          double(wrapped_freq(z, nz)) * f.c[2]) + f.a2h;
+}
+
+// host: the shift for vector potential A (host double[3], may be null) on grid g
+KinField make_kin_field(const pt_grid& g, const double* A);
+
 }  // namespace pt

@@ -1,7 +1,9 @@
-// H psi = P_sph[ -1/2 Lap psi + V_loc psi + alpha V_x psi ]   (Eq. 1 with frozen V_Hxc + V_ext).
+// H psi = P_sph[ 1/2 (-i grad + A)^2 psi + V_loc psi + alpha V_x psi ]   (Eq. 1; V_ext(t) as the
+// uniform vector potential A of the velocity gauge, V_Hxc inside V_loc).
 //
 // With y = V_loc psi + alpha X (X = V_ACE psi or V_x psi, computed by the caller):
-//   out = IFFT( mask(G) * ( |G|^2/2 * FFT(psi) + FFT(y) ) / Ng ),  mask = [|G|^2/2 <= Ecut].
+//   out = IFFT( mask(G) * ( |G + A|^2/2 * FFT(psi) + FFT(y) ) / Ng ),  mask = [|G|^2/2 <= Ecut]
+// (the basis sphere does not move with A).
 // The three FFT passes follow the exchange kernels: x/y plane transforms of both
 // fields, one column kernel that transforms both along z, combines them in G space
 // and transforms back along z, and an inverse plane pass that writes the result.
@@ -16,7 +18,8 @@ namespace pt {
 // compile-time-size passes for cubic grids (hamiltonian_fixed.cu)
 template <class T>
 void apply_h_batch_fixed(int n, const cx<T>* psi, const double* vloc, const cx<T>* X, double alpha, int j0, int nb,
-                         cx<T>* scratch, const double* g2d, double ecut, const cx<T>* tw, cx<T>* out, cudaStream_t st);
+                         cx<T>* scratch, const double* g2d, double ecut, KinField kf, const cx<T>* tw, cx<T>* out,
+                         cudaStream_t st);
 
 namespace {
 
@@ -66,7 +69,7 @@ __global__ void __launch_bounds__(NT) k_h_fwd_plane(GridPlan gp, const cx<T>* __
 
 template <class T>
 __global__ void __launch_bounds__(NT) k_h_column(GridPlan gp, cx<T>* __restrict__ scratch,
-                                                 const double* __restrict__ g2, double ecut, T inv_ng,
+                                                 const double* __restrict__ g2, double ecut, KinField kf, T inv_ng,
                                                  const cx<T>* __restrict__ twg) {
   extern __shared__ unsigned char smem_raw[];
   cx<T>* tw = reinterpret_cast<cx<T>*>(smem_raw);
@@ -96,7 +99,10 @@ __global__ void __launch_bounds__(NT) k_h_column(GridPlan gp, cx<T>* __restrict_
     const int z = e / nx, x = e - z * nx;
     const double half = 0.5 * (g2x[x] + g2y[yrow] + g2z[z]);
     cx<T> v = czero<T>();
-    if (half <= ecut) v = (ba[z * pitch + x] * T(half) + bb[z * pitch + x]) * inv_ng;
+    if (half <= ecut) {
+      const double kin = half + kin_shift(kf, x, yrow, z, nx, ny, nz);  // 1/2 |G + A|^2
+      v = (ba[z * pitch + x] * T(kin) + bb[z * pitch + x]) * inv_ng;
+    }
     ba[z * pitch + x] = v;
   }
   __syncthreads();
@@ -149,7 +155,8 @@ void set_attrs() {
 
 template <class T>
 void apply_h_t(pt_ctx* ctx, const cx<T>* psi, int M, cx<T>* out, const double* vloc, const cx<T>* X, double alpha,
-               double ecut, const pt_grid& g, pt_precision prec, cudaStream_t st) {
+               double ecut, const pt_grid& g, pt_precision prec, cudaStream_t st, const double* A) {
+  const KinField kf = make_kin_field(g, A);
   const FftTables& ft = fft_tables(ctx, g, prec);
   const size_t ng = ng_of(g);
   const size_t field = ng * sizeof(cx<T>);
@@ -160,7 +167,7 @@ void apply_h_t(pt_ctx* ctx, const cx<T>* psi, int M, cx<T>* out, const double* v
   if (fixed_cubic(g)) {
     for (int j0 = 0; j0 < M; j0 += mb)
       apply_h_batch_fixed<T>(g.nx, psi, vloc, X, alpha, j0, std::min(mb, M - j0), scratch,
-                             static_cast<const double*>(ft.g2d), ecut, static_cast<const cx<T>*>(ft.tw), out, st);
+                             static_cast<const double*>(ft.g2d), ecut, kf, static_cast<const cx<T>*>(ft.tw), out, st);
     return;
   }
   set_attrs<T>();
@@ -172,7 +179,7 @@ void apply_h_t(pt_ctx* ctx, const cx<T>* psi, int M, cx<T>* out, const double* v
     PT_LAUNCH(k_h_fwd_plane<T>, dim3(g.nz, 2 * nb), NT, one, st, ft.plan, psi, vloc, X, T(alpha), j0, scratch,
               twg);
     PT_LAUNCH(k_h_column<T>, dim3(g.ny, nb), NT, two, st, ft.plan, scratch, static_cast<const double*>(ft.g2d), ecut,
-              T(1.0 / double(ng)), twg);
+              kf, T(1.0 / double(ng)), twg);
     PT_LAUNCH(k_h_inv_plane<T>, dim3(g.nz, nb), NT, one, st, ft.plan, scratch, j0, out, twg);
   }
 }
@@ -180,13 +187,23 @@ void apply_h_t(pt_ctx* ctx, const cx<T>* psi, int M, cx<T>* out, const double* v
 }  // namespace
 
 void apply_h(pt_ctx* ctx, const void* psi, int M, void* out, const double* vloc, const void* X, double alpha,
-             double ecut, const pt_grid& g, pt_precision prec, cudaStream_t st) {
+             double ecut, const pt_grid& g, pt_precision prec, cudaStream_t st, const double* A) {
   if (prec == PT_FP64)
     apply_h_t<double>(ctx, static_cast<const c128*>(psi), M, static_cast<c128*>(out), vloc,
-                      static_cast<const c128*>(X), alpha, ecut, g, prec, st);
+                      static_cast<const c128*>(X), alpha, ecut, g, prec, st, A);
   else
     apply_h_t<float>(ctx, static_cast<const c64*>(psi), M, static_cast<c64*>(out), vloc, static_cast<const c64*>(X),
-                     alpha, ecut, g, prec, st);
+                     alpha, ecut, g, prec, st, A);
+}
+
+KinField make_kin_field(const pt_grid& g, const double* A) {
+  KinField f{{0.0, 0.0, 0.0}, 0.0, 0};
+  if (!A || (A[0] == 0.0 && A[1] == 0.0 && A[2] == 0.0)) return f;
+  f.on = 1;
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int a = 0; a < 3; ++a) f.c[a] = two_pi * A[a] / g.L[a];
+  f.a2h = 0.5 * (A[0] * A[0] + A[1] * A[1] + A[2] * A[2]);
+  return f;
 }
 
 }  // namespace pt

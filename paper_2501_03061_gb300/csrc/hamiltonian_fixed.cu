@@ -1,7 +1,7 @@
-// H psi = P_sph[ -1/2 Lap psi + V_loc psi + alpha X ] (Eq. 1 with frozen V_Hxc + V_ext) on cubic
-// grids with a compile-time side N: the three passes of hamiltonian.cu (x/y plane transforms of
-// psi and of y = V_loc psi + alpha X; one column kernel that transforms both along z, combines
-// |G|^2/2 FFT(psi) + FFT(y) inside the sphere |G|^2/2 <= Ecut and transforms back along z; an
+// H psi = P_sph[ 1/2 (-i grad + A)^2 psi + V_loc psi + alpha X ] (Eq. 1) on cubic grids with a
+// compile-time side N: the three passes of hamiltonian.cu (x/y plane transforms of psi and of
+// y = V_loc psi + alpha X; one column kernel that transforms both along z, combines
+// |G + A|^2/2 FFT(psi) + FFT(y) inside the sphere |G|^2/2 <= Ecut and transforms back along z; an
 // inverse plane pass), with the FFT stages of fft_fixed.cuh.
 #include <algorithm>
 
@@ -63,7 +63,8 @@ __global__ void __launch_bounds__(FT) k_hx_fwd_plane(const cx<T>* __restrict__ p
 
 template <int N, class T>
 __global__ void __launch_bounds__(FT) k_hx_column(cx<T>* __restrict__ scratch, const double* __restrict__ g2,
-                                                  double ecut, T inv_ng, const cx<T>* __restrict__ twg) {
+                                                  double ecut, KinField kf, T inv_ng,
+                                                  const cx<T>* __restrict__ twg) {
   extern __shared__ unsigned char smem_raw[];
   cx<T>* ba = reinterpret_cast<cx<T>*>(smem_raw);
   cx<T>* bb = ba + N * kPitch<N>;
@@ -92,7 +93,10 @@ __global__ void __launch_bounds__(FT) k_hx_column(cx<T>* __restrict__ scratch, c
     const int z = e / N, x = e - z * N;
     const double half = 0.5 * (g2x[x] + g2y[yrow] + g2z[z]);
     cx<T> v = czero<T>();
-    if (half <= ecut) v = (ba[z * kPitch<N> + x] * T(half) + bb[z * kPitch<N> + x]) * inv_ng;
+    if (half <= ecut) {
+      const double kin = half + kin_shift(kf, x, yrow, z, N, N, N);  // 1/2 |G + A|^2
+      v = (ba[z * kPitch<N> + x] * T(kin) + bb[z * kPitch<N> + x]) * inv_ng;
+    }
     ba[z * kPitch<N> + x] = v;
   }
   __syncthreads();
@@ -133,7 +137,7 @@ __global__ void __launch_bounds__(FT) k_hx_inv_plane(const cx<T>* __restrict__ s
 
 template <int N, class T>
 void h_batch_n(const cx<T>* psi, const double* vloc, const cx<T>* X, T alpha, int j0, int nb, cx<T>* scratch,
-               const double* g2d, double ecut, const cx<T>* tw, cx<T>* out, cudaStream_t st) {
+               const double* g2d, double ecut, KinField kf, const cx<T>* tw, cx<T>* out, cudaStream_t st) {
   static bool done = false;
   const size_t one = tile_bytes_n<N, T>() + N * sizeof(cx<T>);
   const size_t two = 2 * tile_bytes_n<N, T>() + N * sizeof(cx<T>);
@@ -145,7 +149,7 @@ void h_batch_n(const cx<T>* psi, const double* vloc, const cx<T>* X, T alpha, in
   }
   constexpr double ng = double(N) * N * N;
   PT_LAUNCH((k_hx_fwd_plane<N, T>), dim3(N, 2 * nb), FT, one, st, psi, vloc, X, alpha, j0, scratch, tw);
-  PT_LAUNCH((k_hx_column<N, T>), dim3(N, nb), FT, two, st, scratch, g2d, ecut, T(1.0 / ng), tw);
+  PT_LAUNCH((k_hx_column<N, T>), dim3(N, nb), FT, two, st, scratch, g2d, ecut, kf, T(1.0 / ng), tw);
   PT_LAUNCH((k_hx_inv_plane<N, T>), dim3(N, nb), FT, one, st, scratch, j0, out, tw);
 }
 
@@ -153,11 +157,12 @@ void h_batch_n(const cx<T>* psi, const double* vloc, const cx<T>* X, T alpha, in
 
 template <class T>
 void apply_h_batch_fixed(int n, const cx<T>* psi, const double* vloc, const cx<T>* X, double alpha, int j0, int nb,
-                         cx<T>* scratch, const double* g2d, double ecut, const cx<T>* tw, cx<T>* out, cudaStream_t st) {
+                         cx<T>* scratch, const double* g2d, double ecut, KinField kf, const cx<T>* tw, cx<T>* out,
+                         cudaStream_t st) {
   switch (n) {
 #define PT_CASE(s)                                                                                     \
   case s:                                                                                              \
-    h_batch_n<s, T>(psi, vloc, X, T(alpha), j0, nb, scratch, g2d, ecut, tw, out, st);                  \
+    h_batch_n<s, T>(psi, vloc, X, T(alpha), j0, nb, scratch, g2d, ecut, kf, tw, out, st);              \
     return;
     PT_FIXED_SIZES(PT_CASE)
 #undef PT_CASE
@@ -167,8 +172,8 @@ void apply_h_batch_fixed(int n, const cx<T>* psi, const double* vloc, const cx<T
 }
 
 template void apply_h_batch_fixed<float>(int, const c64*, const double*, const c64*, double, int, int, c64*,
-                                         const double*, double, const c64*, c64*, cudaStream_t);
+                                         const double*, double, KinField, const c64*, c64*, cudaStream_t);
 template void apply_h_batch_fixed<double>(int, const c128*, const double*, const c128*, double, int, int, c128*,
-                                          const double*, double, const c128*, c128*, cudaStream_t);
+                                          const double*, double, KinField, const c128*, c128*, cudaStream_t);
 
 }  // namespace pt

@@ -107,8 +107,12 @@ void anderson_update(pt_ctx* ctx, cx<T>* x, const cx<T>* r, const cx<T>* const* 
 
 // ---- Hamiltonian (hamiltonian.cu) ----
 // out = P_sph[ -1/2 Lap psi + y ],  y = vloc*psi + alpha*X (X may be null)
+// A: vector potential of the velocity-gauge field (host double[3]; null = no field)
 void apply_h(pt_ctx* ctx, const void* psi, int M, void* out, const double* vloc, const void* X, double alpha,
-             double ecut, const pt_grid& g, pt_precision prec, cudaStream_t st);
+             double ecut, const pt_grid& g, pt_precision prec, cudaStream_t st, const double* A = nullptr);
+// J_a = spin/Omega Re sum_ij sigma_ij <phi_j|(-i d_a + A_a) phi_i> (host J[3]; synchronises st)
+void current(pt_ctx* ctx, const void* phi, const c128* sigma, int N, const pt_grid& g, pt_precision prec,
+             const double* A, double spin, double* J, cudaStream_t st);
 
 void conj_transpose(const c128* A, int N, c128* B, cudaStream_t st);
 

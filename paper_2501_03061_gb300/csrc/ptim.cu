@@ -343,7 +343,7 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
         exchange_on_midpoint(X, inner == 0);
       }
       tm.begin(PH_H);
-      apply_h(ctx, phih, N, Hphi, vh, X, P.alpha, P.ecut, g, prec, st);
+      apply_h(ctx, phih, N, Hphi, vh, X, P.alpha, P.ecut, g, prec, st, P.A);
       tm.end();
       tm.begin(PH_SUB);
       // A = <Phi_h|H Phi_h> and S = <Phi_h|Phi_h> are Hermitian: upper tiles only, mirrored
