@@ -100,8 +100,12 @@ pt_status pt_trim(pt_ctx* ctx);
  *                    iteration); the step still converges only when the midpoint has settled to
  *                    tol and the last inner loop met tol.  Defaults 0.1 and 1e-2; kappa = 0 uses
  *                    tol throughout.
- *   "scratch_bytes"  bytes of pair/orbital fields one FFT batch may hold (default 48 MiB, sized
- *                    to stay resident in L2; smaller values give more, smaller batches).
+ *   "scratch_bytes"  bytes of pair/orbital fields one FFT batch may hold (default 512 MiB: the
+ *                    cost per pair falls with the pair tile even past L2 residency, 4-10% from
+ *                    48 MiB to 512 MiB; smaller values give more, smaller batches).
+ *   "exchange64_scratch_bytes"  the same for the 64^3 FP32 exchange pipeline (default 512 MiB:
+ *                    16 x 16 pair tiles, the largest its parameter block holds), which keeps four
+ *                    such batches in flight.
  *   "tc_gram"        1: in the PT_FP32 form, run the Gram contractions (A^H B over the grid) on
  *                    the tensor cores with a 3-product TF32 split (hi*hi + hi*lo + lo*hi) that
  *                    keeps FP32-level accuracy; 0 (default): CUDA cores.

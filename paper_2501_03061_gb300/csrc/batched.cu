@@ -4,8 +4,9 @@
 //
 // Host runtime around the exchange kernels:
 //   * autotuner: the pair-tile size of a grid (how many pair fields one FFT batch holds, which
-//     sets the L2 footprint and the launch count) is picked by timing a few candidate budgets on
-//     the first item of that grid (its first min(N, 32) orbitals) and kept in the context;
+//     sets the L2 footprint and the launch count) is picked by timing candidate budgets of
+//     12 MiB to 512 MiB on the first item of that grid (its first min(N, 32) orbitals) and kept
+//     in the context;
 //   * CUDA graphs: the first call with a given item set runs eagerly once (this sizes every
 //     workspace, builds schedules and tables and encodes nothing that later changes), then the
 //     whole batch is captured on a context-owned stream into one graph, which this and every
@@ -52,7 +53,7 @@ size_t tuned_budget(pt_ctx* ctx, const pt_exchange_item& it, pt_precision prec, 
   float best_ms = 1e30f;
   int last_b = -1;
   const size_t mib = size_t(1) << 20;
-  const size_t cands[] = {12 * mib, 24 * mib, 48 * mib, 96 * mib};
+  const size_t cands[] = {12 * mib, 24 * mib, 48 * mib, 96 * mib, 192 * mib, 512 * mib};
   try {
     for (size_t cand : cands) {
       // candidates that give the same pair tile are the same schedule

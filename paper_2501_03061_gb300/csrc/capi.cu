@@ -1,4 +1,5 @@
 // The exported C ABI (include/ptim.h): argument checks, context, error conversion.
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -182,6 +183,11 @@ pt_status pt_set_option(pt_ctx* ctx, const char* key, double value) {
     if (std::string(key) == "scratch_bytes") {
       if (!(value >= 1.0)) pt::fail(PT_INVALID_ARG, "scratch_bytes must be >= 1");
       ctx->scratch_budget = size_t(value);
+      return PT_OK;
+    }
+    if (std::string(key) == "exchange64_scratch_bytes") {
+      if (!(value >= 1.0)) pt::fail(PT_INVALID_ARG, "exchange64_scratch_bytes must be >= 1");
+      ctx->tma64_budget = size_t(value);
       return PT_OK;
     }
     pt::fail(PT_INVALID_ARG, std::string("unknown option ") + key);
@@ -511,11 +517,14 @@ size_t pt_ptim_footprint(int N, const pt_grid* grid, pt_precision prec, int ande
   const size_t field = ng * es;
   const size_t block = field * size_t(N);
   const int depth = anderson_depth < 1 ? 1 : (anderson_depth > 20 ? 20 : anderson_depth);
-  const size_t budget = size_t(48) << 20;  // default scratch_bytes of a context
+  const size_t budget = size_t(512) << 20;  // default scratch_bytes of a context
   size_t B = size_t(std::floor(std::sqrt(double(std::max<size_t>(1, budget / field)))));
   B = std::max<size_t>(1, std::min<size_t>(B, size_t(N)));
-  const bool tma64 = grid->nx == 64 && grid->ny == 64 && grid->nz == 64;
-  if (tma64 && prec != PT_FP64) B = std::min<size_t>(B, 6);
+  const bool tma64 = grid->nx == 64 && grid->ny == 64 && grid->nz == 64 && prec != PT_FP64;
+  if (tma64) {
+    const size_t b64 = size_t(std::floor(std::sqrt(double((size_t(512) << 20) / field))));  // default tma64_budget
+    B = std::max<size_t>(1, std::min<size_t>({b64, size_t(N), size_t(pt::kExchange64MaxTile)}));
+  }
   const size_t exch = (tma64 ? 4 : 1) * B * B * field;
   const size_t hscr = 2 * std::max<size_t>(1, std::min<size_t>(size_t(N), budget / (2 * field))) * field;
   const size_t nn = size_t(N) * N * sizeof(double) * 2;

@@ -98,7 +98,13 @@ struct pt_ctx {
   size_t held = 0;
   int num_sms = 0;
   size_t max_smem_optin = 0;
-  size_t scratch_budget = size_t(48) << 20;  // bytes of pair fields per exchange batch (L2-resident)
+  // bytes of pair fields per exchange batch (and of orbital fields per H batch); larger batches
+  // cost less per pair even past L2 residency (fewer launches, traffic amortised over the tile)
+  size_t scratch_budget = size_t(512) << 20;
+  // bytes of pair fields per batch on the 64^3 FP32 TMA pipeline: its cost per pair falls with the
+  // pair tile (fewer launches, W traffic amortised over more contributions), so it takes the
+  // largest tile its parameter block holds rather than an L2-sized one
+  size_t tma64_budget = size_t(512) << 20;
   int tc_gram = 0;     // option: FP32 form's Gram contractions on tensor cores (3xTF32) when 1
   int active_tc = 0;   // per call: 0 CUDA cores, 1 tensor cores 3xTF32, 2 tensor cores single TF32
   bool bf16_requested = false;  // per call: the BF16 form, whose contractions are not built

@@ -266,11 +266,14 @@ long long exchange_t(pt_ctx* ctx, const cx<T>* src, const double* occ, int N, co
   const T* ktab = static_cast<const T*>(kernel_table(ctx, g, k, prec));
   const size_t ng = ng_of(g);
   const size_t field = ng * sizeof(cx<T>);
-  // Pair batch: as many pair fields as fit a budget that keeps them L2-resident.
-  const size_t budget = ctx->budget_override ? ctx->budget_override : exchange_scratch_budget(ctx);
+  // Pair batch: as many pair fields as fit a budget that keeps them L2-resident (the 64^3 TMA
+  // pipeline takes its own, larger budget: see pt_ctx::tma64_budget).
+  const bool tma64 = sizeof(T) == 4 && exchange64_applies(g) && ctx->exchange64_engine == 0;
+  const size_t budget = ctx->budget_override ? ctx->budget_override
+                                             : (tma64 ? ctx->tma64_budget : exchange_scratch_budget(ctx));
   int B = int(std::floor(std::sqrt(double(std::max<size_t>(1, budget / field)))));
   B = std::max(1, std::min(B, std::max(N, M)));
-  if (exchange64_applies(g) && ctx->exchange64_engine == 0 && sizeof(T) == 4) B = std::min(B, 6);
+  if (tma64) B = std::min(B, kExchange64MaxTile);
   char key[128];
   snprintf(key, sizeof(key), "sched:%d:%d:%d:%d", N, M, int(sym), B);
   auto it = ctx->caches.find(key);

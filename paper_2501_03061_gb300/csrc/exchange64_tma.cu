@@ -27,7 +27,7 @@ namespace {
 constexpr int G = 64;
 constexpr int PITCH = 68;
 constexpr int THREADS = 512;
-constexpr int MAXB = 6;                          // tile side of the pair schedule on this path
+constexpr int MAXB = kExchange64MaxTile;         // tile side of the pair schedule on this path
 constexpr int MAXP = MAXB * MAXB, MAXT = 2 * MAXB, MAXC = 2 * MAXP;
 constexpr uint32_t TILE_BYTES = 32768;           // 64 x 64 complex64
 constexpr uint32_t SUB_BYTES = 8192;             // 16 columns x 64 rows of 128 B

@@ -85,7 +85,7 @@ def test_exchange_general_targets_ragged_multibatch(ctx, precision):
         out = ctx.apply_exchange(dev(src.astype(dt)), dev(occ), dev(tgt.astype(dt)), cell=cell,
                                  kernel={"type": 1, "mu": 0.2}, precision=precision)
     finally:
-        ctx.set_option("scratch_bytes", 48 << 20)
+        ctx.set_option("scratch_bytes", 512 << 20)
     assert rel(out.cpu().numpy().astype(np.complex128), ref) <= (FP64_TOL if precision == "fp64" else FP32_TOL)
 
 
@@ -102,7 +102,7 @@ def test_exchange_fp64_radix_mix(ctx, n, N):
     try:
         out = ctx.apply_exchange(dev(phi), dev(occ), cell=cell, kernel={"type": 1, "mu": 0.106}, precision="fp64")
     finally:
-        ctx.set_option("scratch_bytes", 48 << 20)
+        ctx.set_option("scratch_bytes", 512 << 20)
     assert rel(out.cpu().numpy(), ref) <= FP64_TOL
 
 
@@ -289,27 +289,30 @@ def test_ptim_step_fp32_matches_oracle(ctx, ptim_ref, tc_gram):
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("sym", [True, False])
-@pytest.mark.parametrize("tile", [2, 6])
+@pytest.mark.parametrize("tile", [2, 6, 10])
 def test_exchange_64cubed_specialised_path(ctx, precision, sym, tile):
     """The 64^3 kernels (pipelined plane/column/plane/accumulate roles in FP32) against the oracle:
-    several batches of 2x2 or 6x6 pair tiles, ragged at the edge (N = 7 or 13), an exact-zero
-    occupation (skipped pairs), separate targets."""
+    several batches of 2x2, 6x6 or 10x10 pair tiles (10: the largest the parameter block holds),
+    ragged at the edge (N = 7, 13 or 23), an exact-zero occupation (skipped pairs), separate
+    targets."""
     rng = np.random.default_rng(64 + sym + 10 * tile)
     cell = synth.cubic(64, 20.5)
-    n = 7 if tile == 2 else 13
+    n = {2: 7, 6: 13, 10: 23}[tile]
     src = synth.random_orbitals(rng, cell, n)
-    tgt = src if sym else synth.random_orbitals(rng, cell, 3 if tile == 2 else 8)
+    tgt = src if sym else synth.random_orbitals(rng, cell, {2: 3, 6: 8, 10: 12}[tile])
     occ = np.linspace(1.0, 0.05, n)
     occ[1] = 0.0
     g = O.grid_of(cell)
     ref = O.apply_exchange(src, occ, tgt, O.exchange_kernel(g, 1, synth.SCREENED_MU))
     dt = np.complex128 if precision == "fp64" else np.complex64
-    ctx.set_option("scratch_bytes", tile * tile * g.ng * (16 if precision == "fp64" else 8))
+    ctx.set_option("scratch_bytes", tile * tile * g.ng * 16)
+    ctx.set_option("exchange64_scratch_bytes", tile * tile * g.ng * 8)
     try:
         out = ctx.apply_exchange(dev(src.astype(dt)), dev(occ), None if sym else dev(tgt.astype(dt)), cell=cell,
                                  kernel={"type": 1, "mu": synth.SCREENED_MU}, precision=precision)
     finally:
-        ctx.set_option("scratch_bytes", 48 << 20)
+        ctx.set_option("scratch_bytes", 512 << 20)
+        ctx.set_option("exchange64_scratch_bytes", 512 << 20)
     assert rel(out.cpu().numpy().astype(np.complex128), ref) <= (FP64_TOL if precision == "fp64" else FP32_TOL)
 
 
