@@ -81,7 +81,7 @@ __device__ __forceinline__ Rot jacobi_rot(const c128* A, int N, int p, int q) {
   return r;
 }
 
-constexpr int JB = 16;  // pairs per CTA side (32 x 32 elements)
+constexpr int JB = 8;  // pairs per CTA side (16 x 16 elements): (N/16)^2 CTAs spread over every SM
 
 __global__ void __launch_bounds__(JB* JB) k_jacobi_round(const c128* __restrict__ Ain, c128* __restrict__ Aout,
                                                          c128* __restrict__ V, int N, int Np, int r) {
@@ -401,7 +401,8 @@ void zgemm(char opA, char opB, int m, int n, int k, c128 alpha, const c128* A, i
   PT_LAUNCH(k_zgemm, grid, ZT * ZT, 0, st, opA, opB, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
 }
 
-void heev(pt_ctx* ctx, const c128* S, int N, c128* Q, double* d, cudaStream_t st, int max_sweeps, const c128* Q0) {
+void heev(pt_ctx* ctx, const c128* S, int N, c128* Q, double* d, cudaStream_t st, int max_sweeps, const c128* Q0,
+          double rel_tol) {
   const int Np = N + (N & 1);
   c128* A0 = static_cast<c128*>(ctx->get("heev_A0", size_t(N) * N * sizeof(c128)));
   c128* A1 = static_cast<c128*>(ctx->get("heev_A1", size_t(N) * N * sizeof(c128)));
@@ -431,6 +432,7 @@ void heev(pt_ctx* ctx, const c128* S, int N, c128* Q, double* d, cudaStream_t st
     // quadratically, so a stalled sweep means rounding noise).
     const double floor2 = 1e-32 * double(N) * h[1];
     if (h[0] <= floor2 || h[0] == 0.0) break;
+    if (h[0] <= rel_tol * rel_tol * h[1]) break;
     if (h[0] <= 1e-24 * h[1] && h[0] > 0.25 * prev_off) break;
     prev_off = h[0];
     for (int r = 0; r < Np - 1; ++r) {

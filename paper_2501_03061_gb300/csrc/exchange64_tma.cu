@@ -108,7 +108,10 @@ __global__ void __launch_bounds__(THREADS, 2)
 
   if (bid < L.nA) {
     // ---------------- pass A ----------------
-    const int z = bid % G, p = bid / G;
+    // plane-major order: the CTAs of all pairs of the batch at one z run together, so the source
+    // planes shared by the pairs of a tile row or column are read from L2
+    const int np = L.nA / G;
+    const int z = bid / np, p = bid % np;
     const PairDesc pd = L.pa[p];
     if (tid == 0) {
       mbar_arrive_expect_tx(bar, 2 * TILE_BYTES);
@@ -222,8 +225,12 @@ __global__ void __launch_bounds__(THREADS, 2)
   bid -= L.nC;
   {
     // ---------------- pass D (half a plane per CTA) ----------------
-    const int z = (bid >> 1) % G, half = bid & 1;
-    const TargetDesc td = L.td[(bid >> 1) / G];
+    // plane-major order: all targets of the batch at one z run together, so the two targets of a
+    // symmetric pair read its v_ij plane close in time (the second read hits L2), as do the
+    // partner planes shared by a tile row
+    const int nt = L.nD / (2 * G);
+    const int z = (bid >> 1) / nt, half = bid & 1;
+    const TargetDesc td = L.td[(bid >> 1) % nt];
     constexpr int EPT = G * G / (2 * THREADS);
     const int e0 = half * (G * G / 2) + tid;
     const size_t zoff = size_t(z) * G * G;

@@ -73,9 +73,11 @@ void rotate_bf16(pt_ctx* ctx, const c64* A, const c128* Bm, int ldb, int N1, int
 void zgemm(char opA, char opB, int m, int n, int k, c128 alpha, const c128* A, int lda, const c128* B, int ldb,
            c128 beta, c128* C, int ldc, cudaStream_t st);
 // S (Hermitian part used) = Q diag(d) Q^*, ascending d.  Synchronises st once per sweep.
-// Q0 (optional): an orthonormal basis that nearly diagonalises S (warm start); may alias Q
+// Q0 (optional): an orthonormal basis that nearly diagonalises S (warm start); may alias Q.
+// rel_tol (optional): also stop once the off-diagonal Frobenius norm of Q^* S Q is at most
+// rel_tol * ||S||_F, which bounds ||S - Q diag(d) Q^*||_F (0: run to the FP64 rounding floor).
 void heev(pt_ctx* ctx, const c128* S, int N, c128* Q, double* d, cudaStream_t st, int max_sweeps = 30,
-          const c128* Q0 = nullptr);
+          const c128* Q0 = nullptr, double rel_tol = 0.0);
 // A (overwritten) = L L^* ; L written to a separate buffer; *info = k+1 on a bad pivot k.
 void cholesky(pt_ctx* ctx, c128* A, int N, c128* L, int* info, cudaStream_t st);
 // X = L^{-1} for the factor of the preceding cholesky(ctx, ...) (uses its diagonal-block inverses)
