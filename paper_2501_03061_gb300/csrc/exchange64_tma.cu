@@ -101,6 +101,7 @@ __global__ void __launch_bounds__(THREADS, 2)
   if (tid < G) tw[tid] = c_tw64[tid];
   if (tid == 0) {
     mbar_init(bar, 1);
+    mbar_init(bar + 8, 1);  // second tile of the two-item roles B and C
     fence_mbar_init();
   }
   __syncthreads();
@@ -150,76 +151,97 @@ __global__ void __launch_bounds__(THREADS, 2)
   }
   bid -= L.nA;
   if (bid < L.nB) {
-    // ---------------- pass B ----------------
-    const int ky = bid % G, p = bid / G;
+    // ---------------- pass B (two slabs per CTA: ky and ky + G/2) ----------------
+    // Both slab loads are issued at once (the second into the plane-transpose area, which this
+    // role does not use), so the second slab's load latency hides behind the first's transforms.
+    constexpr int H = G / 2;
+    const int ky0 = bid % H, p = bid / H;
     const int kx = grp;
     const PairDesc pd = L.pb[p];
     const int orb = L.slotB * L.max_pairs + p;
     if (tid == 0) {
       mbar_arrive_expect_tx(bar, TILE_BYTES);
-      for (int s = 0; s < 4; ++s) tma_load_4d(base + OFF_A + s * SUB_BYTES, &tm_slab, 16 * s, ky, 0, orb, bar);
+      for (int s = 0; s < 4; ++s) tma_load_4d(base + OFF_A + s * SUB_BYTES, &tm_slab, 16 * s, ky0, 0, orb, bar);
+      mbar_arrive_expect_tx(bar + 8, TILE_BYTES);
+      for (int s = 0; s < 4; ++s)
+        tma_load_4d(base + OFF_P + s * SUB_BYTES, &tm_slab, 16 * s, ky0 + H, 0, orb, bar + 8);
     }
-    float kv[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) kv[k] = ktab[(size_t(t + 8 * k) * G + ky) * G + kx];
     const bool skip = pair_skipped(pd, occ);
     c64* gs = reinterpret_cast<c64*>(sm + OFF_B) + grp * 64;
-    if (!mbar_wait(bar, 0, TIMEOUT_NS)) {
-      atomicOr(err, 2);
-      return;
+    for (int h = 0; h < 2; ++h) {
+      const int ky = ky0 + h * H;
+      const uint32_t off = h ? OFF_P : OFF_A;
+      float kv[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) kv[k] = ktab[(size_t(t + 8 * k) * G + ky) * G + kx];
+      if (!mbar_wait(bar + 8u * h, 0, TIMEOUT_NS)) {
+        atomicOr(err, 2);
+        return;
+      }
+      if (skip) continue;  // uniform over the CTA; both loads still land before it exits
+      c64 v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v[q] = *reinterpret_cast<const c64*>(sm + off + sw_off(kx, t + 8 * q));
+      fft64_tma(v, t, gs, gpar, tw, false);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = v[k] * kv[k];
+      fft64_tma(v, t, gs, gpar, tw, true);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) *reinterpret_cast<c64*>(sm + off + sw_off(kx, t + 8 * k)) = v[k];
+      fence_proxy_async_smem();
+      __syncthreads();
+      if (tid == 0) {
+        for (int s = 0; s < 4; ++s) tma_store_4d(&tm_slab, 16 * s, ky, 0, orb, base + off + s * SUB_BYTES);
+        tma_store_commit();
+      }
     }
-    if (skip) return;
-    c64 v[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] = *reinterpret_cast<const c64*>(sm + OFF_A + sw_off(kx, t + 8 * q));
-    fft64_tma(v, t, gs, gpar, tw, false);
-#pragma unroll
-    for (int k = 0; k < 8; ++k) v[k] = v[k] * kv[k];
-    fft64_tma(v, t, gs, gpar, tw, true);
-#pragma unroll
-    for (int k = 0; k < 8; ++k) *reinterpret_cast<c64*>(sm + OFF_A + sw_off(kx, t + 8 * k)) = v[k];
-    fence_proxy_async_smem();
-    __syncthreads();
-    if (tid == 0) {
-      for (int s = 0; s < 4; ++s) tma_store_4d(&tm_slab, 16 * s, ky, 0, orb, base + OFF_A + s * SUB_BYTES);
-      tma_store_commit();
-      tma_store_wait_all();
-    }
+    if (tid == 0 && !skip) tma_store_wait_all();
     return;
   }
   bid -= L.nB;
   if (bid < L.nC) {
-    // ---------------- pass C ----------------
-    const int z = bid % G, p = bid / G;
+    // ---------------- pass C (two planes per CTA: z and z + G/2) ----------------
+    // The second plane loads into the B tile, unused by this role, while the first is transformed.
+    constexpr int H = G / 2;
+    const int z0 = bid % H, p = bid / H;
     const PairDesc pd = L.pc[p];
     const int orb = L.slotC * L.max_pairs + p;
     if (tid == 0) {
       mbar_arrive_expect_tx(bar, TILE_BYTES);
-      for (int s = 0; s < 4; ++s) tma_load_4d(base + OFF_A + s * SUB_BYTES, &tm_plane, 16 * s, 0, z, orb, bar);
+      for (int s = 0; s < 4; ++s) tma_load_4d(base + OFF_A + s * SUB_BYTES, &tm_plane, 16 * s, 0, z0, orb, bar);
+      mbar_arrive_expect_tx(bar + 8, TILE_BYTES);
+      for (int s = 0; s < 4; ++s)
+        tma_load_4d(base + OFF_B + s * SUB_BYTES, &tm_plane, 16 * s, 0, z0 + H, orb, bar + 8);
     }
     const bool skip = pair_skipped(pd, occ);
-    if (!mbar_wait(bar, 0, TIMEOUT_NS)) {
-      atomicOr(err, 4);
-      return;
-    }
-    if (skip) return;
     const int kx = grp;
-    c64 v[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] = *reinterpret_cast<const c64*>(sm + OFF_A + sw_off(kx, t + 8 * q));
-    __syncthreads();
     c64* gs = reinterpret_cast<c64*>(sm + OFF_A) + grp * 64;
-    fft64_tma(v, t, gs, gpar, tw, true);  // inverse along y: lane t holds y = t + 8k
+    for (int h = 0; h < 2; ++h) {
+      const int z = z0 + h * H;
+      if (!mbar_wait(bar + 8u * h, 0, TIMEOUT_NS)) {
+        atomicOr(err, 4);
+        return;
+      }
+      if (skip) continue;  // uniform over the CTA; both loads still land before it exits
+      c64 v[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) P[(t + 8 * k) * PITCH + kx] = v[k];
-    __syncthreads();
-    const int y = grp;
+      for (int q = 0; q < 8; ++q)
+        v[q] = *reinterpret_cast<const c64*>(sm + (h ? OFF_B : OFF_A) + sw_off(kx, t + 8 * q));
+      // first plane: tile A consumed before it becomes the group-transpose area; second plane:
+      // every warp is done with the first plane's transpose areas
+      __syncthreads();
+      fft64_tma(v, t, gs, gpar, tw, true);  // inverse along y: lane t holds y = t + 8k
 #pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] = P[y * PITCH + t + 8 * q];
-    fft64_tma(v, t, gs, gpar, tw, true);  // inverse along x: lane t holds x = t + 8k
-    c64* o = scratch + size_t(orb) * ng + size_t(z) * G * G + y * G;
+      for (int k = 0; k < 8; ++k) P[(t + 8 * k) * PITCH + kx] = v[k];
+      __syncthreads();
+      const int y = grp;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) o[t + 8 * k] = v[k];
+      for (int q = 0; q < 8; ++q) v[q] = P[y * PITCH + t + 8 * q];
+      fft64_tma(v, t, gs, gpar, tw, true);  // inverse along x: lane t holds x = t + 8k
+      c64* o = scratch + size_t(orb) * ng + size_t(z) * G * G + y * G;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) o[t + 8 * k] = v[k];
+    }
     return;
   }
   bid -= L.nC;
@@ -367,11 +389,11 @@ void exchange64_tma(pt_ctx* ctx, const ScheduleImpl& sch, const c64* src, const 
     }
     const int b = k - 1, c = k - 2, d = k - 3;
     if (b >= 0 && b < nb) {
-      L.nB = G * copy_pairs(L.pb, b);
+      L.nB = (G / 2) * copy_pairs(L.pb, b);
       L.slotB = b % 4;
     }
     if (c >= 0 && c < nb) {
-      L.nC = G * copy_pairs(L.pc, c);
+      L.nC = (G / 2) * copy_pairs(L.pc, c);
       L.slotC = c % 4;
     }
     if (d >= 0) {
