@@ -643,7 +643,7 @@ def run_gb300(args):
                          "pair_ffts_per_s": pair_ffts / (ex_ms / 1e3) if ex_ms else None,
                          "share_of_step": ex_ms / ms if ms else None},
             "iterations": [{"outer": s["outer"], "inner": s["inner"], "residual": s["residual"],
-                            "converged": s["converged"]} for s in stats],
+                            "converged": s["converged"], "eig_sweeps": s["eig_sweeps"]} for s in stats],
             "phases_ms_per_step": {k: sum(s["phase_ms"][k] for s in stats) / len(stats)
                                    for k in stats[0]["phase_ms"]},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -294,6 +294,7 @@ typedef struct {
      9 Anderson mixing and residual norms, 10 final Loewdin orthonormalisation,
      11 V_Hxc (midpoint density, Hartree FFT, LDA; params.hxc = 1) */
   double phase_ms[12];
+  int eig_sweeps;           /* Jacobi sweeps of the sigma eigensolves (phase 6) */
 } pt_ptim_stats;
 
 /* One PT-IM(-ACE) step from (phi, sigma) = (Phi_n, sigma_n) to (Phi_{n+1}, sigma_{n+1}),

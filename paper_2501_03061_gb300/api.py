@@ -314,7 +314,7 @@ class Context:
         return {"status": L.STATUS_NAMES[st], "outer": s.outer, "inner": s.inner, "residual": s.residual,
                 "exch_energy": s.exch_energy, "orth_error": s.orth_error, "converged": bool(s.converged),
                 "pair_ffts": int(s.pair_ffts), "exchange_calls": int(s.exchange_calls),
-                "exchange_ms": float(s.exchange_ms),
+                "exchange_ms": float(s.exchange_ms), "eig_sweeps": int(s.eig_sweeps),
                 "phase_ms": {n: float(s.phase_ms[i]) for i, n in enumerate(L.PHASES)}}
 
 

@@ -401,8 +401,8 @@ void zgemm(char opA, char opB, int m, int n, int k, c128 alpha, const c128* A, i
   PT_LAUNCH(k_zgemm, grid, ZT * ZT, 0, st, opA, opB, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
 }
 
-void heev(pt_ctx* ctx, const c128* S, int N, c128* Q, double* d, cudaStream_t st, int max_sweeps, const c128* Q0,
-          double rel_tol) {
+int heev(pt_ctx* ctx, const c128* S, int N, c128* Q, double* d, cudaStream_t st, int max_sweeps, const c128* Q0,
+         double rel_tol) {
   const int Np = N + (N & 1);
   c128* A0 = static_cast<c128*>(ctx->get("heev_A0", size_t(N) * N * sizeof(c128)));
   c128* A1 = static_cast<c128*>(ctx->get("heev_A1", size_t(N) * N * sizeof(c128)));
@@ -422,6 +422,7 @@ void heev(pt_ctx* ctx, const c128* S, int N, c128* Q, double* d, cudaStream_t st
   dim3 grid((half + JB - 1) / JB, (half + JB - 1) / JB);
   double h[2] = {0, 0};
   double prev_off = INFINITY;
+  int sweeps = 0;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     PT_LAUNCH(k_offnorm, 1, 1024, 0, st, A0, N, nrm);
     PT_CUDA_CHECK(cudaMemcpyAsync(h, nrm, sizeof(h), cudaMemcpyDeviceToHost, st));
@@ -439,8 +440,10 @@ void heev(pt_ctx* ctx, const c128* S, int N, c128* Q, double* d, cudaStream_t st
       PT_LAUNCH(k_jacobi_round, grid, JB * JB, 0, st, A0, A1, V, N, Np, r);
       std::swap(A0, A1);
     }
+    ++sweeps;
   }
   PT_LAUNCH(k_sort_eig, 1, 256, 0, st, A0, V, N, Q, d);
+  return sweeps;
 }
 
 void cholesky(pt_ctx* ctx, c128* A, int N, c128* L, int* info, cudaStream_t st) {

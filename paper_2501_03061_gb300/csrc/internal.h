@@ -76,8 +76,9 @@ void zgemm(char opA, char opB, int m, int n, int k, c128 alpha, const c128* A, i
 // Q0 (optional): an orthonormal basis that nearly diagonalises S (warm start); may alias Q.
 // rel_tol (optional): also stop once the off-diagonal Frobenius norm of Q^* S Q is at most
 // rel_tol * ||S||_F, which bounds ||S - Q diag(d) Q^*||_F (0: run to the FP64 rounding floor).
-void heev(pt_ctx* ctx, const c128* S, int N, c128* Q, double* d, cudaStream_t st, int max_sweeps = 30,
-          const c128* Q0 = nullptr, double rel_tol = 0.0);
+// Returns the number of Jacobi sweeps run.
+int heev(pt_ctx* ctx, const c128* S, int N, c128* Q, double* d, cudaStream_t st, int max_sweeps = 30,
+         const c128* Q0 = nullptr, double rel_tol = 0.0);
 // A (overwritten) = L L^* ; L written to a separate buffer; *info = k+1 on a bad pivot k.
 void cholesky(pt_ctx* ctx, c128* A, int N, c128* L, int* info, cudaStream_t st);
 // X = L^{-1} for the factor of the preceding cholesky(ctx, ...) (uses its diagonal-block inverses)

@@ -240,7 +240,7 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
     ctx->ptim_q_n = 0;  // Q is being rewritten
     // FP32 forms: sigma_h = Q diag(d) Q^* to 1e-9 relative, two orders below the rounding of the
     // FP32 exchange it feeds (~1e-7); the FP64 form runs Jacobi to its rounding floor
-    heev(ctx, sigh, N, Q, d, st, 30, warm ? Q : nullptr, prec == PT_FP64 ? 0.0 : 1e-9);
+    stv.eig_sweeps += heev(ctx, sigh, N, Q, d, st, 30, warm ? Q : nullptr, prec == PT_FP64 ? 0.0 : 1e-9);
     ctx->ptim_q_n = N;
     tm.end();
     tm.begin(PH_ROT);
