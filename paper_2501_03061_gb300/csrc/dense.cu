@@ -71,13 +71,24 @@ __device__ __forceinline__ Rot jacobi_rot(const c128* A, int N, int p, int q) {
   if (q >= N) return r;  // padding player
   const double app = A[size_t(p) * N + p].re, aqq = A[size_t(q) * N + q].re;
   const c128 apq = A[size_t(p) * N + q];
-  const double b = hypot(apq.re, apq.im);
-  if (b == 0.0) return r;
-  const double zeta = (aqq - app) / (2.0 * b);
-  const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-  r.c = 1.0 / sqrt(1.0 + t * t);
+  // reciprocal square roots in place of square roots and divisions (each a long FP64 sequence on
+  // the round's critical path); an off-diagonal entry below 1e-140 is treated as zero
+  const double b2 = apq.re * apq.re + apq.im * apq.im;
+  if (!(b2 > 1e-280)) return r;
+  const double rb = rsqrt(b2);  // 1 / |a_pq|
+  const double zeta = (aqq - app) * (0.5 * rb);
+  const double az = fabs(zeta);
+  double t;
+  if (az > 1e100) {
+    t = 0.5 / az;  // 1 / (|zeta| + sqrt(1 + zeta^2)) to double precision
+  } else {
+    const double q2 = 1.0 + zeta * zeta;
+    t = 1.0 / (az + q2 * rsqrt(q2));
+  }
+  if (zeta < 0.0) t = -t;
+  r.c = rsqrt(1.0 + t * t);
   r.s = t * r.c;
-  r.u = c128{apq.re / b, apq.im / b};
+  r.u = c128{apq.re * rb, apq.im * rb};
   return r;
 }
 
@@ -245,10 +256,12 @@ __global__ void __launch_bounds__(256) k_chol_diag(c128* __restrict__ A, int N, 
     }
     __syncthreads();
     if (tid == 0) {
-      const double dk = sqrt(piv);
-      a[k][k] = c128{dk, 0.0};
-      s_rk = 1.0 / dk;
-      rdiag[k] = s_rk;
+      // one reciprocal square root instead of a square root and a division (each a long FP64
+      // sequence on the pivot's critical path)
+      const double rk0 = rsqrt(piv);
+      a[k][k] = c128{piv * rk0, 0.0};
+      s_rk = rk0;
+      rdiag[k] = rk0;
     }
     __syncthreads();
     const double rk = s_rk;
