@@ -109,6 +109,12 @@ struct RotArgs {
 };
 
 // B'[n'][k'] hi and lo parts (K-major rows of kpad floats, npad rows), alpha folded in
+// read-only load of one complex64 through the non-coherent path
+__device__ __forceinline__ c64 ldg_c64(const c64* p) {
+  const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+  return c64{v.x, v.y};
+}
+
 __global__ void k_rot_prep_b(const c128* __restrict__ Bm, int ldb, int N1, int N2, c128 alpha, int npad, int kpad,
                              float* __restrict__ bhi, float* __restrict__ blo) {
   const size_t e = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -337,17 +343,36 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int rb = tl / P.tiles_j, jt = tl % P.tiles_j;
       const long long r = (long long)rb * RM + lrow;
       if (r < P.ng) {
+        // The terms and the output are distinct per element (a term that is also the output is
+        // read before its element is written by the same thread), so the loads of later outputs
+        // may be issued ahead of earlier stores: restrict-qualified copies let the compiler batch
+        // them instead of paying one memory latency per output.
+        const c64* __restrict__ e0 = P.e[0];
+        const c64* __restrict__ e1 = P.e[1];
+        const c64* __restrict__ e2 = P.e[2];
+        c64* __restrict__ op = P.out;
+        const int jn = min(RJ, P.N2 - jt * RJ);
         // fully unrolled so that acc[] stays in registers
 #pragma unroll
-        for (int jj = 0; jj < RJ; ++jj) {
-          const int j = jt * RJ + jj;
-          if (j >= P.N2) continue;
-          const size_t idx = size_t(j) * size_t(P.ng) + size_t(r);
-          c64 o{acc[2 * jj], acc[2 * jj + 1]};
+        for (int j0 = 0; j0 < RJ; j0 += 4) {
+          c64 tv[3][4];
 #pragma unroll
-          for (int e = 0; e < 3; ++e)
-            if (P.e[e]) o = o + cmul(P.c[e], P.e[e][idx]);
-          P.out[idx] = o;
+          for (int u = 0; u < 4; ++u) {
+            const size_t idx = size_t(jt * RJ + j0 + u) * size_t(P.ng) + size_t(r);
+            const bool okj = j0 + u < jn;
+            tv[0][u] = (e0 && okj) ? ldg_c64(e0 + idx) : c64{0.f, 0.f};
+            tv[1][u] = (e1 && okj) ? ldg_c64(e1 + idx) : c64{0.f, 0.f};
+            tv[2][u] = (e2 && okj) ? ldg_c64(e2 + idx) : c64{0.f, 0.f};
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int jj = j0 + u;
+            if (jj >= jn) continue;
+            const size_t idx = size_t(jt * RJ + jj) * size_t(P.ng) + size_t(r);
+            c64 o{acc[2 * jj], acc[2 * jj + 1]};
+            o = o + cmul(P.c[0], tv[0][u]) + cmul(P.c[1], tv[1][u]) + cmul(P.c[2], tv[2][u]);
+            op[idx] = o;
+          }
         }
       }
     }
