@@ -101,7 +101,8 @@ __global__ void __launch_bounds__(THREADS, 2)
   if (tid < G) tw[tid] = c_tw64[tid];
   if (tid == 0) {
     mbar_init(bar, 1);
-    mbar_init(bar + 8, 1);  // second tile of the two-item roles B and C
+    mbar_init(bar + 8, 1);   // second tile of the two-item roles B and C
+    mbar_init(bar + 16, 1);  // third contribution slot of role D
     fence_mbar_init();
   }
   __syncthreads();
@@ -249,42 +250,56 @@ __global__ void __launch_bounds__(THREADS, 2)
     // ---------------- pass D (half a plane per CTA) ----------------
     // plane-major order: all targets of the batch at one z run together, so the two targets of a
     // symmetric pair read its v_ij plane close in time (the second read hits L2), as do the
-    // partner planes shared by a tile row
+    // partner planes shared by a tile row.  The v_ij and partner half-planes (16 KB each, one
+    // contiguous range apiece) stream through a ring of DS shared-memory slots by bulk copies,
+    // DS contributions ahead of the arithmetic, so the loads overlap without holding registers.
     const int nt = L.nD / (2 * G);
     const int z = (bid >> 1) / nt, half = bid & 1;
     const TargetDesc td = L.td[(bid >> 1) % nt];
     constexpr int EPT = G * G / (2 * THREADS);
+    constexpr uint32_t HB = G * G / 2 * sizeof(c64);  // bytes of a half plane
+    constexpr int DS = 3;                             // 3 x 32 KB below the twiddle table
     const int e0 = half * (G * G / 2) + tid;
     const size_t zoff = size_t(z) * G * G;
+    const size_t hoff = zoff + size_t(half) * (G * G / 2);
+    const int nc = td.cend - td.cbeg;
+    auto issue = [&](int i) {  // one thread
+      const Contrib cc = L.cd[td.cbeg + i - L.d_cbeg];
+      const int sl = i % DS;
+      const uint32_t dst = base + uint32_t(sl) * 2u * HB;
+      fence_proxy_async_smem();  // the slot's previous contents were read through the generic proxy
+      mbar_arrive_expect_tx(bar + 8u * sl, 2u * HB);
+      bulk_load(dst, scratch + (size_t(L.slotD) * L.max_pairs + cc.slot) * ng + hoff, HB, bar + 8u * sl);
+      bulk_load(dst + HB, src + size_t(cc.partner) * ng + hoff, HB, bar + 8u * sl);
+    };
+    if (tid == 0)
+      for (int i = 0; i < min(DS, nc); ++i) issue(i);
     c64 acc[EPT];
 #pragma unroll
     for (int u = 0; u < EPT; ++u) acc[u] = czero<float>();
-    for (int c = td.cbeg; c < td.cend; c += 2) {
-      const bool two = c + 1 < td.cend;
-      const Contrib c0 = L.cd[c - L.d_cbeg];
-      const Contrib c1 = L.cd[(two ? c + 1 : c) - L.d_cbeg];
-      const float f0 = float(occ[c0.occ]);
-      const float f1 = two ? float(occ[c1.occ]) : 0.f;
-      const c64* v0 = scratch + (size_t(L.slotD) * L.max_pairs + c0.slot) * ng + zoff + e0;
-      const c64* v1 = scratch + (size_t(L.slotD) * L.max_pairs + c1.slot) * ng + zoff + e0;
-      const c64* q0 = src + size_t(c0.partner) * ng + zoff + e0;
-      const c64* q1 = src + size_t(c1.partner) * ng + zoff + e0;
-      c64 a0[EPT], b0[EPT], a1[EPT], b1[EPT];
+    for (int i = 0; i < nc; ++i) {
+      const int sl = i % DS;
+      const Contrib cc = L.cd[td.cbeg + i - L.d_cbeg];
+      const float f = float(occ[cc.occ]);
+      const bool ok = mbar_wait(bar + 8u * sl, (i / DS) & 1, TIMEOUT_NS);
+      // a skipped pair (d = 0) left its scratch slot unwritten: never multiply stale data by 0
+      if (ok && f != 0.f) {
+        const c64* sv = reinterpret_cast<const c64*>(sm + sl * 2 * HB);
+        const c64* sq = sv + G * G / 2;
 #pragma unroll
-      for (int u = 0; u < EPT; ++u) {
-        a0[u] = v0[u * THREADS];
-        b0[u] = q0[u * THREADS];
-        a1[u] = v1[u * THREADS];
-        b1[u] = q1[u * THREADS];
+        for (int u = 0; u < EPT; ++u) {
+          c64 a = sv[tid + u * THREADS];
+          if (cc.conj) a.im = -a.im;
+          acc[u] = acc[u] + cmul(sq[tid + u * THREADS], a) * f;
+        }
       }
-#pragma unroll
-      for (int u = 0; u < EPT; ++u) {
-        if (c0.conj) a0[u].im = -a0[u].im;
-        if (c1.conj) a1[u].im = -a1[u].im;
-        // a skipped pair (d = 0) left its scratch slot unwritten: never multiply stale data by 0
-        if (f0 != 0.f) acc[u] = acc[u] + cmul(b0[u], a0[u]) * f0;
-        if (f1 != 0.f) acc[u] = acc[u] + cmul(b1[u], a1[u]) * f1;
+      // every thread is done with slot sl before it is refilled; an expired wait ends the CTA
+      // uniformly
+      if (!__syncthreads_and(ok)) {
+        if (tid == 0) atomicOr(err, 8);
+        return;
       }
+      if (tid == 0 && i + DS < nc) issue(i + DS);
     }
     c64* o = out + size_t(td.t) * ng + zoff + e0;
 #pragma unroll
