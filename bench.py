@@ -33,7 +33,7 @@ METRIC = "Vx·Ψ pair-FFTs/s and PT-IM steps/s vs plain FP64 GPU form; serve p50
 # DRAM bytes (read + write) per steady-state launch of the 64^3 FP32 exchange kernel: mean of two
 # launches of an ncu --set full capture with the 16 x 16 pair tiles the benchmark cell uses
 # (N = 64 orbitals, the same launch shape); the kernel is unchanged since that capture
-EXCHANGE64_TRAFFIC_PER_LAUNCH = None
+EXCHANGE64_TRAFFIC_PER_LAUNCH = 2.90e9
 UNIT = "PT-IM steps/s"
 WORKLOAD = "ptim_ace_step_64^3_N320_128site_L20.5"
 # model iteration counts used to scale a bounded CPU sample to one step: the paper's ~5 outer x ~13 inner
