@@ -514,7 +514,7 @@ def ptim_step(phi_n: np.ndarray, sigma_n: np.ndarray, vloc: np.ndarray, g: Grid,
         if not p.use_ace and inner_converged:
             stats.converged = True
             break
-    # Final orthonormalisation and conjugate symmetrisation (Alg. 1, last line)
+    # Final orthonormalisation and conjugate symmetrisation (Algorithm 1, end of the step)
     S = overlap(phi, phi, dV)
     stats.orth_error = float(np.abs(S - overlap(phi_n, phi_n, dV)).max())
     S = 0.5 * (S + S.conj().T)
