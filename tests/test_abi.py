@@ -42,3 +42,58 @@ def test_version_string(lib):
     from paper_2501_03061_gb300 import _lib
     l = _lib.load()
     assert b"sm_103a" in l.pt_version()
+
+
+STRUCTS = ("pt_grid", "pt_kernel", "pt_exchange_item", "pt_ptim_params", "pt_ptim_stats")
+
+
+def header_struct_fields():
+    text = open(os.path.join(ROOT, "include", "ptim.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    out = {}
+    for m in re.finditer(r"typedef struct \{(.*?)\}\s*(\w+);", text, flags=re.S):
+        fields = []
+        for decl in m.group(1).split(";"):
+            decl = re.sub(r"\s+", " ", decl.strip())
+            if not decl:
+                continue
+            parts = decl.split(",")
+            fields.append(re.match(r"(.*?)(\w+)(\[\d+\])?$", parts[0].strip()).group(2))
+            fields += [re.match(r"\s*\**\s*(\w+)", e).group(1) for e in parts[1:]]
+        out[m.group(2)] = fields
+    return out
+
+
+def test_binding_structs_match_the_header_field_by_field():
+    from paper_2501_03061_gb300 import _lib
+    hdr = header_struct_fields()
+    for name in STRUCTS:
+        assert [f[0] for f in getattr(_lib, name)._fields_] == hdr[name], name
+
+
+def test_binding_struct_layout_matches_the_c_compiler(tmp_path):
+    """sizeof and every field offset as gcc lays the header's structs out, against ctypes."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    from paper_2501_03061_gb300 import _lib
+    hdr = header_struct_fields()
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "ptim.h"', "int main(void) {"]
+    for name in STRUCTS:
+        offs = " ".join("%zu" for _ in hdr[name])
+        args = ", ".join(f"offsetof({name}, {f})" for f in hdr[name])
+        lines.append(f'  printf("{name} %zu {offs}\\n", sizeof({name}), {args});')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        name, *vals = line.split()
+        got[name] = [int(v) for v in vals]
+    for name in STRUCTS:
+        cls = getattr(_lib, name)
+        want = [ctypes.sizeof(cls)] + [getattr(cls, f[0]).offset for f in cls._fields_]
+        assert got[name] == want, (name, got[name], want)
