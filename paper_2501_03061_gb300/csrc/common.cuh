@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -70,6 +71,27 @@ struct Error {
 void check_cuda(cudaError_t e, const char* what);
 
 #define PT_CUDA_CHECK(expr) ::pt::check_cuda((expr), #expr)
+
+// Runs a set-up action (kernel attributes, constant-memory tables) once per CUDA device: both are
+// per-device state, and the serving loop calls the library from several threads.
+class DeviceOnce {
+ public:
+  template <class F>
+  void operator()(F&& f) {
+    int dev = 0;
+    check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev < 0 || dev >= 64) fail(PT_CUDA, "device index out of range");
+    const uint64_t bit = uint64_t(1) << dev;
+    std::lock_guard<std::mutex> lock(m_);
+    if (done_ & bit) return;
+    f();
+    done_ |= bit;
+  }
+
+ private:
+  std::mutex m_;
+  uint64_t done_ = 0;
+};
 // Launch a kernel, count it, and surface launch-configuration errors immediately.
 #define PT_LAUNCH(kernel, grid, block, smem, stream, ...)                          \
   do {                                                                            \

@@ -529,11 +529,8 @@ void gram_bf16(pt_ctx* ctx, const c64* A, const c64* B, int N1, int N2, size_t n
     PT_CUDA_CHECK(cudaMemsetAsync(err, 0, sizeof(int), st));
     ctx->tc_err_clean = true;
   }
-  static bool attr = false;
-  if (!attr) {
-    PT_CUDA_CHECK(cudaFuncSetAttribute(k_gram_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, G_SMEM));
-    attr = true;
-  }
+  static DeviceOnce once;
+  once([] { PT_CUDA_CHECK(cudaFuncSetAttribute(k_gram_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, G_SMEM)); });
   CUtensorMap ta, tb;
   const uint64_t da[4] = {kpad, uint64_t(ti) * 128, 1, 1}, db[4] = {kpad, uint64_t(tj) * 64, 1, 1};
   const uint64_t sa[3] = {kpad * 2, kpad * 2 * ti * 128, kpad * 2 * ti * 128};
@@ -565,11 +562,8 @@ void rotate_bf16(pt_ctx* ctx, const c64* A, const c128* Bm, int ldb, int N1, int
     PT_CUDA_CHECK(cudaMemsetAsync(err, 0, sizeof(int), st));
     ctx->tc_err_clean = true;
   }
-  static bool attr = false;
-  if (!attr) {
-    PT_CUDA_CHECK(cudaFuncSetAttribute(k_rotate_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, R_SMEM));
-    attr = true;
-  }
+  static DeviceOnce once;
+  once([] { PT_CUDA_CHECK(cudaFuncSetAttribute(k_rotate_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, R_SMEM)); });
   CUtensorMap ta, tb;
   const uint64_t da[4] = {uint64_t(kpad), ngpad, 1, 1}, db[4] = {uint64_t(kpad), uint64_t(npad), 1, 1};
   const uint64_t sa[3] = {uint64_t(kpad) * 2, uint64_t(kpad) * 2 * ngpad, uint64_t(kpad) * 2 * ngpad};

@@ -245,13 +245,13 @@ size_t tile_smem_bytes(size_t esize) { return (3 * kMaxDim + size_t(kMaxDim) * (
 
 template <class T>
 void set_smem_attrs() {
-  static bool done = false;
-  if (done) return;
-  const int bytes = int(tile_smem_bytes(sizeof(cx<T>)));
-  PT_CUDA_CHECK(cudaFuncSetAttribute(k_pair_fwd_plane<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  PT_CUDA_CHECK(cudaFuncSetAttribute(k_pair_column<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  PT_CUDA_CHECK(cudaFuncSetAttribute(k_pair_inv_acc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  done = true;
+  static DeviceOnce once;
+  once([] {
+    const int bytes = int(tile_smem_bytes(sizeof(cx<T>)));
+    PT_CUDA_CHECK(cudaFuncSetAttribute(k_pair_fwd_plane<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    PT_CUDA_CHECK(cudaFuncSetAttribute(k_pair_column<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    PT_CUDA_CHECK(cudaFuncSetAttribute(k_pair_inv_acc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  });
 }
 
 template <class T>

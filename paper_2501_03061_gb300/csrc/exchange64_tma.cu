@@ -365,8 +365,8 @@ void exchange64_tma(pt_ctx* ctx, const ScheduleImpl& sch, const c64* src, const 
   c64* scratch = static_cast<c64*>(ctx->get("exchange64_scratch", 4 * size_t(maxp) * ng * sizeof(c64)));
   int* err = static_cast<int*>(ctx->get("exchange_err", sizeof(int)));
   if (!ctx->defer_checks) PT_CUDA_CHECK(cudaMemsetAsync(err, 0, sizeof(int), st));  // else zeroed once per batch
-  static bool init = false;
-  if (!init) {
+  static DeviceOnce once;  // kernel attribute and the constant twiddle table are per device
+  once([] {
     PT_CUDA_CHECK(cudaFuncSetAttribute(k_exchange64_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
     c64 h[G];
     for (int i = 0; i < G; ++i) {
@@ -374,8 +374,7 @@ void exchange64_tma(pt_ctx* ctx, const ScheduleImpl& sch, const c64* src, const 
       h[i] = c64{float(std::cos(ang)), float(std::sin(ang))};
     }
     PT_CUDA_CHECK(cudaMemcpyToSymbol(c_tw64, h, sizeof(h)));
-    init = true;
-  }
+  });
   (void)tw;
   const uint64_t strides[3] = {G * 8, G * G * 8, ng * 8};
   const uint32_t plane_box[4] = {16, 64, 1, 1};

@@ -160,13 +160,13 @@ __global__ void __launch_bounds__(AT) k_fx_accumulate(const cx<T>* __restrict__ 
 
 template <int N, class T>
 void set_fx_attrs() {
-  static bool done = false;
-  if (done) return;
-  const int bytes = int(tile_smem<N, T>());
-  PT_CUDA_CHECK(cudaFuncSetAttribute(k_fx_fwd_plane<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  PT_CUDA_CHECK(cudaFuncSetAttribute(k_fx_column<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  PT_CUDA_CHECK(cudaFuncSetAttribute(k_fx_inv_plane<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  done = true;
+  static DeviceOnce once;
+  once([] {
+    const int bytes = int(tile_smem<N, T>());
+    PT_CUDA_CHECK(cudaFuncSetAttribute(k_fx_fwd_plane<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    PT_CUDA_CHECK(cudaFuncSetAttribute(k_fx_column<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    PT_CUDA_CHECK(cudaFuncSetAttribute(k_fx_inv_plane<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  });
 }
 
 template <int N, class T>

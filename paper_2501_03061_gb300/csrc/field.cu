@@ -114,12 +114,11 @@ void current_t(pt_ctx* ctx, const cx<T>* phi, const c128* sigma, int N, const pt
   const size_t tile = size_t(kMaxDim) * (kMaxDim + 1) * sizeof(cx<T>);
   const size_t one = 3 * kMaxDim * sizeof(cx<T>) + tile;
   const size_t two = one + tile;
-  static bool attr = false;
-  if (!attr) {
+  static DeviceOnce once;
+  once([&] {
     PT_CUDA_CHECK(cudaFuncSetAttribute(k_cur_fwd_plane<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(one)));
     PT_CUDA_CHECK(cudaFuncSetAttribute(k_cur_column<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(two)));
-    attr = true;
-  }
+  });
   const double two_pi = 6.283185307179586476925286766559;
   const double3 gstep = make_double3(two_pi / g.L[0], two_pi / g.L[1], two_pi / g.L[2]);
   const double3 av = A ? make_double3(A[0], A[1], A[2]) : make_double3(0.0, 0.0, 0.0);

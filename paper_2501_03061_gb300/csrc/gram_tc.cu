@@ -378,11 +378,8 @@ void gram_tc(pt_ctx* ctx, const c64* A, const c64* B, int N1, int N2, size_t ng,
     PT_CUDA_CHECK(cudaMemsetAsync(err, 0, sizeof(int), st));
     ctx->tc_err_clean = true;
   }
-  static bool attr = false;
-  if (!attr) {
-    PT_CUDA_CHECK(cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-    attr = true;
-  }
+  static DeviceOnce once;
+  once([] { PT_CUDA_CHECK(cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES)); });
   // 2-D views (as 4-D maps with unit outer dims): K' = 2 Ng floats per orbital row
   CUtensorMap ta, tb;
   const uint64_t da[4] = {2 * ng, uint64_t(N1), 1, 1}, db[4] = {2 * ng, uint64_t(N2), 1, 1};

@@ -143,14 +143,14 @@ size_t tile_bytes(size_t esize) { return size_t(kMaxDim) * (kMaxDim + 1) * esize
 
 template <class T>
 void set_attrs() {
-  static bool done = false;
-  if (done) return;
-  const int one = int(3 * kMaxDim * sizeof(cx<T>) + tile_bytes(sizeof(cx<T>)));
-  const int two = int(3 * kMaxDim * sizeof(cx<T>) + 2 * tile_bytes(sizeof(cx<T>)));
-  PT_CUDA_CHECK(cudaFuncSetAttribute(k_h_fwd_plane<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, one));
-  PT_CUDA_CHECK(cudaFuncSetAttribute(k_h_inv_plane<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, one));
-  PT_CUDA_CHECK(cudaFuncSetAttribute(k_h_column<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, two));
-  done = true;
+  static DeviceOnce once;
+  once([] {
+    const int one = int(3 * kMaxDim * sizeof(cx<T>) + tile_bytes(sizeof(cx<T>)));
+    const int two = int(3 * kMaxDim * sizeof(cx<T>) + 2 * tile_bytes(sizeof(cx<T>)));
+    PT_CUDA_CHECK(cudaFuncSetAttribute(k_h_fwd_plane<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, one));
+    PT_CUDA_CHECK(cudaFuncSetAttribute(k_h_inv_plane<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, one));
+    PT_CUDA_CHECK(cudaFuncSetAttribute(k_h_column<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, two));
+  });
 }
 
 template <class T>

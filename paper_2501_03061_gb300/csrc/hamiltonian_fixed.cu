@@ -138,15 +138,14 @@ __global__ void __launch_bounds__(FT) k_hx_inv_plane(const cx<T>* __restrict__ s
 template <int N, class T>
 void h_batch_n(const cx<T>* psi, const double* vloc, const cx<T>* X, T alpha, int j0, int nb, cx<T>* scratch,
                const double* g2d, double ecut, KinField kf, const cx<T>* tw, cx<T>* out, cudaStream_t st) {
-  static bool done = false;
+  static DeviceOnce once;
   const size_t one = tile_bytes_n<N, T>() + N * sizeof(cx<T>);
   const size_t two = 2 * tile_bytes_n<N, T>() + N * sizeof(cx<T>);
-  if (!done) {
+  once([&] {
     PT_CUDA_CHECK(cudaFuncSetAttribute(k_hx_fwd_plane<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(one)));
     PT_CUDA_CHECK(cudaFuncSetAttribute(k_hx_inv_plane<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(one)));
     PT_CUDA_CHECK(cudaFuncSetAttribute(k_hx_column<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(two)));
-    done = true;
-  }
+  });
   constexpr double ng = double(N) * N * N;
   PT_LAUNCH((k_hx_fwd_plane<N, T>), dim3(N, 2 * nb), FT, one, st, psi, vloc, X, alpha, j0, scratch, tw);
   PT_LAUNCH((k_hx_column<N, T>), dim3(N, nb), FT, two, st, scratch, g2d, ecut, kf, T(1.0 / ng), tw);

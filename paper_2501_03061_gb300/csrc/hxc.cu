@@ -190,13 +190,13 @@ __global__ void __launch_bounds__(NT) k_hxc_inv_plane(GridPlan gp, const c128* _
 size_t tile_bytes() { return size_t(kMaxDim) * (kMaxDim + 1) * sizeof(c128) + 3 * kMaxDim * sizeof(c128); }
 
 void set_attrs() {
-  static bool done = false;
-  if (done) return;
-  const int b = int(tile_bytes());
-  PT_CUDA_CHECK(cudaFuncSetAttribute(k_hxc_fwd_plane, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
-  PT_CUDA_CHECK(cudaFuncSetAttribute(k_hxc_column, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
-  PT_CUDA_CHECK(cudaFuncSetAttribute(k_hxc_inv_plane, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
-  done = true;
+  static DeviceOnce once;
+  once([] {
+    const int b = int(tile_bytes());
+    PT_CUDA_CHECK(cudaFuncSetAttribute(k_hxc_fwd_plane, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+    PT_CUDA_CHECK(cudaFuncSetAttribute(k_hxc_column, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+    PT_CUDA_CHECK(cudaFuncSetAttribute(k_hxc_inv_plane, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+  });
 }
 
 }  // namespace

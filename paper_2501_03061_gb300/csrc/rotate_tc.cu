@@ -412,11 +412,8 @@ void rotate_tc(pt_ctx* ctx, const c64* A, const c128* Bm, int ldb, int N1, int N
   }
   const size_t nb = size_t(npad) * kpad;
   PT_LAUNCH(k_rot_prep_b, unsigned((nb + 255) / 256), 256, 0, st, Bm, ldb, N1, N2, alpha, npad, kpad, bhi, blo);
-  static bool attr = false;
-  if (!attr) {
-    PT_CUDA_CHECK(cudaFuncSetAttribute(k_rotate_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-    attr = true;
-  }
+  static DeviceOnce once;
+  once([] { PT_CUDA_CHECK(cudaFuncSetAttribute(k_rotate_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES)); });
   // A as a [N1][Ng] array of 8-byte elements; box = 128 points x 16 orbitals, no swizzle
   CUtensorMap ta, tbh, tbl;
   const uint64_t da[4] = {ng, uint64_t(N1), 1, 1};
