@@ -14,7 +14,10 @@
  *    j, point (x,y,z) sits at element j*Ng + (z*ny + y)*nx + x.  The element
  *    type is double2 (complex128) for PT_FP64 and float2 (complex64) for the
  *    FP32 precisions.  Buffers start on a 16-byte boundary.
- *  - N x N matrices (sigma, Q, ...) are complex128, row-major: a[i*N + j].
+ *  - N x N matrices (sigma, Q, ...) are complex128, row-major: a[i*N + j],
+ *    also on a 16-byte boundary.
+ *  - Orbital counts (N, M, N1, N2) are 1..PT_MAX_ORBITALS; others return
+ *    PT_INVALID_ARG.
  *  - Inner product <a|b> = dV * sum_r conj(a(r)) b(r).
  *  - All pointers passed in are DEVICE pointers unless stated otherwise.  The
  *    caller owns every buffer it passes; the library never frees caller memory
@@ -46,6 +49,9 @@ enum {
   PT_CUDA = 7,           /* a CUDA runtime error; see pt_last_error */
   PT_UNSUPPORTED = 8     /* valid request that this build does not implement */
 };
+
+/* Largest orbital count a call accepts (N x N matrices are indexed with 32-bit products). */
+#define PT_MAX_ORBITALS 32768
 
 /* Orthorhombic periodic cell sampled on an nx*ny*nz grid. */
 typedef struct {

@@ -11,6 +11,7 @@ PT_OK, PT_INVALID_ARG, PT_OOM, PT_NOT_PD, PT_NOT_CONVERGED, PT_NONFINITE, PT_TIM
 STATUS_NAMES = {0: "PT_OK", 1: "PT_INVALID_ARG", 2: "PT_OOM", 3: "PT_NOT_PD", 4: "PT_NOT_CONVERGED",
                 5: "PT_NONFINITE", 6: "PT_TIMEOUT", 7: "PT_CUDA", 8: "PT_UNSUPPORTED"}
 PRECISIONS = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3}
+PT_MAX_ORBITALS = 32768  # largest orbital count a call accepts
 
 
 class pt_grid(C.Structure):

@@ -95,6 +95,12 @@ void check_common(pt_ctx* ctx, const pt_grid* grid, pt_precision prec) {
   if (prec < PT_FP64 || prec > PT_FP32_TC_BF16) pt::fail(PT_INVALID_ARG, "unknown precision");
 }
 
+// orbital counts: positive and small enough that N*N fits the kernels' 32-bit indices
+void check_count(int n, const char* what) {
+  if (n <= 0 || n > PT_MAX_ORBITALS)
+    pt::fail(PT_INVALID_ARG, std::string(what) + " must be in 1.." + std::to_string(PT_MAX_ORBITALS));
+}
+
 void check_kernel(const pt_kernel* k) {
   if (!k) pt::fail(PT_INVALID_ARG, "kernel is NULL");
   if (k->type != 0 && k->type != 1) pt::fail(PT_INVALID_ARG, "kernel type must be 0 or 1");
@@ -200,9 +206,9 @@ pt_status pt_apply_exchange(pt_ctx* ctx, const void* src, const double* occ, int
   return guarded(ctx, [&]() -> pt_status {
     check_common(ctx, grid, prec);
     check_kernel(kernel);
-    if (N <= 0) pt::fail(PT_INVALID_ARG, "N must be positive");
+    check_count(N, "N");
     if (tgt == nullptr) M = N;
-    if (M <= 0) pt::fail(PT_INVALID_ARG, "M must be positive");
+    check_count(M, "M");
     pt::require_aligned(src, "src");
     pt::require_aligned(out, "out");
     if (!occ) pt::fail(PT_INVALID_ARG, "occ is NULL");
@@ -230,7 +236,8 @@ pt_status pt_apply_exchange_batched(pt_ctx* ctx, const pt_exchange_item* items, 
       } catch (const pt::Error& e) {
         pt::fail(e.code, w + e.msg);
       }
-      if (it.N <= 0 || (it.tgt && it.M <= 0)) pt::fail(PT_INVALID_ARG, w + "N and M must be positive");
+      if (it.N <= 0 || it.N > PT_MAX_ORBITALS || (it.tgt && (it.M <= 0 || it.M > PT_MAX_ORBITALS)))
+        pt::fail(PT_INVALID_ARG, w + "N and M must be in 1.." + std::to_string(PT_MAX_ORBITALS));
       if (!it.occ) pt::fail(PT_INVALID_ARG, w + "occ is NULL");
       pt::require_aligned(it.src, "src");
       pt::require_aligned(it.out, "out");
@@ -251,7 +258,7 @@ pt_status pt_build_ace_from(pt_ctx* ctx, const void* W, const void* phi, int N, 
     check_common(ctx, grid, prec);
     if (!ace) pt::fail(PT_INVALID_ARG, "ace is NULL");
     *ace = nullptr;
-    if (N <= 0) pt::fail(PT_INVALID_ARG, "N must be positive");
+    check_count(N, "N");
     pt::require_aligned(W, "W");
     pt::require_aligned(phi, "phi");
     set_device(ctx);
@@ -287,7 +294,7 @@ pt_status pt_build_ace(pt_ctx* ctx, const void* phi, const double* occ, int N, c
     check_common(ctx, grid, prec);
     check_kernel(kernel);
     if (!ace) pt::fail(PT_INVALID_ARG, "ace is NULL");
-    if (N <= 0) pt::fail(PT_INVALID_ARG, "N must be positive");
+    check_count(N, "N");
     pt::require_aligned(phi, "phi");
     if (!occ) pt::fail(PT_INVALID_ARG, "occ is NULL");
     set_device(ctx);
@@ -304,7 +311,8 @@ pt_status pt_overlap(pt_ctx* ctx, const void* A, int N1, const void* B, int N2, 
                      pt_precision prec, void* C, void* stream) {
   return guarded(ctx, [&]() -> pt_status {
     check_common(ctx, grid, prec);
-    if (N1 <= 0 || N2 <= 0) pt::fail(PT_INVALID_ARG, "N1 and N2 must be positive");
+    check_count(N1, "N1");
+    check_count(N2, "N2");
     pt::require_aligned(A, "A");
     pt::require_aligned(B, "B");
     pt::require_aligned(C, "C");
@@ -328,7 +336,8 @@ pt_status pt_rotate(pt_ctx* ctx, const void* A, int N1, const void* B, int N2, c
                     pt_precision prec, void* out, void* stream) {
   return guarded(ctx, [&]() -> pt_status {
     check_common(ctx, grid, prec);
-    if (N1 <= 0 || N2 <= 0) pt::fail(PT_INVALID_ARG, "N1 and N2 must be positive");
+    check_count(N1, "N1");
+    check_count(N2, "N2");
     pt::require_aligned(A, "A");
     pt::require_aligned(B, "B");
     pt::require_aligned(out, "out");
@@ -354,7 +363,7 @@ pt_status pt_rotate(pt_ctx* ctx, const void* A, int N1, const void* B, int N2, c
 pt_status pt_apply_ace(pt_ctx* ctx, const pt_ace* ace, const void* psi, int M, void* out, void* stream) {
   return guarded(ctx, [&]() -> pt_status {
     if (!ctx || !ace) pt::fail(PT_INVALID_ARG, "context or ACE is NULL");
-    if (M <= 0) pt::fail(PT_INVALID_ARG, "M must be positive");
+    check_count(M, "M");
     pt::require_aligned(psi, "psi");
     pt::require_aligned(out, "out");
     if (out == psi) pt::fail(PT_INVALID_ARG, "out must not alias psi");
@@ -384,7 +393,7 @@ pt_status pt_apply_H(pt_ctx* ctx, const void* psi, int M, void* out, const doubl
                      void* stream) {
   return guarded(ctx, [&]() -> pt_status {
     check_common(ctx, grid, prec);
-    if (M <= 0) pt::fail(PT_INVALID_ARG, "M must be positive");
+    check_count(M, "M");
     pt::require_aligned(psi, "psi");
     pt::require_aligned(out, "out");
     if (!vloc) pt::fail(PT_INVALID_ARG, "vloc is NULL");
@@ -410,9 +419,10 @@ pt_status pt_current(pt_ctx* ctx, const void* phi, const void* sigma, int N, con
                      const double* A, double spin, double* J, void* stream) {
   return guarded(ctx, [&]() -> pt_status {
     check_common(ctx, grid, prec);
-    if (N <= 0) pt::fail(PT_INVALID_ARG, "N must be positive");
+    check_count(N, "N");
     if (!phi || !sigma || !J) pt::fail(PT_INVALID_ARG, "NULL buffer");
     pt::require_aligned(phi, "phi");
+    pt::require_aligned(sigma, "sigma");
     set_device(ctx);
     set_engine(ctx, prec);
     auto st = static_cast<cudaStream_t>(stream);
@@ -426,10 +436,11 @@ pt_status pt_density(pt_ctx* ctx, const void* phi, const void* sigma, int N, con
                      double spin, double* rho, void* stream) {
   return guarded(ctx, [&]() -> pt_status {
     check_common(ctx, grid, prec);
-    if (N <= 0) pt::fail(PT_INVALID_ARG, "N must be positive");
+    check_count(N, "N");
     if (!phi || !sigma || !rho) pt::fail(PT_INVALID_ARG, "NULL buffer");
     if (!(spin > 0.0)) pt::fail(PT_INVALID_ARG, "spin must be positive");
     pt::require_aligned(phi, "phi");
+    pt::require_aligned(sigma, "sigma");
     set_device(ctx);
     set_engine(ctx, prec);
     auto st = static_cast<cudaStream_t>(stream);
@@ -478,8 +489,10 @@ pt_status pt_hxc_potential(pt_ctx* ctx, const double* rho, const double* vloc, c
 pt_status pt_diag_occupations(pt_ctx* ctx, const void* sigma, int N, void* Q, double* d, void* stream) {
   return guarded(ctx, [&]() -> pt_status {
     if (!ctx) pt::fail(PT_INVALID_ARG, "context is NULL");
-    if (N <= 0) pt::fail(PT_INVALID_ARG, "N must be positive");
+    check_count(N, "N");
     if (!sigma || !Q || !d) pt::fail(PT_INVALID_ARG, "NULL buffer");
+    pt::require_aligned(sigma, "sigma");
+    pt::require_aligned(Q, "Q");
     set_device(ctx);
     pt::heev(ctx, static_cast<const c128*>(sigma), N, static_cast<c128*>(Q), d, static_cast<cudaStream_t>(stream));
     return PT_OK;
@@ -493,7 +506,7 @@ pt_status pt_ptim_step(pt_ctx* ctx, void* phi, void* sigma, int N, const double*
     check_common(ctx, grid, prec);
     check_kernel(kernel);
     if (!params) pt::fail(PT_INVALID_ARG, "params is NULL");
-    if (N <= 0) pt::fail(PT_INVALID_ARG, "N must be positive");
+    check_count(N, "N");
     pt::require_aligned(phi, "phi");
     pt::require_aligned(sigma, "sigma");
     if (!vloc) pt::fail(PT_INVALID_ARG, "vloc is NULL");
@@ -511,7 +524,7 @@ pt_status pt_ptim_step(pt_ctx* ctx, void* phi, void* sigma, int N, const double*
 }
 
 size_t pt_ptim_footprint(int N, const pt_grid* grid, pt_precision prec, int anderson_depth) {
-  if (!grid || N <= 0) return 0;
+  if (!grid || N <= 0 || N > PT_MAX_ORBITALS) return 0;
   const size_t ng = pt::ng_of(*grid);
   const size_t es = pt::elem_bytes(prec);
   const size_t field = ng * es;

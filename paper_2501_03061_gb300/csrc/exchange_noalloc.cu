@@ -218,7 +218,8 @@ extern "C" pt_status pt_apply_exchange_noalloc(const void* src, const double* oc
     if (!kernel || (kernel->type != 0 && kernel->type != 1) || (kernel->type == 1 && !(kernel->mu > 0)))
       pt::fail(PT_INVALID_ARG, "bad kernel");
     if (prec < PT_FP64 || prec > PT_FP32_TC_BF16) pt::fail(PT_INVALID_ARG, "unknown precision");
-    if (N <= 0 || (tgt && M <= 0) || !occ) pt::fail(PT_INVALID_ARG, "bad sizes or NULL occupations");
+    if (N <= 0 || N > PT_MAX_ORBITALS || (tgt && (M <= 0 || M > PT_MAX_ORBITALS)) || !occ)
+      pt::fail(PT_INVALID_ARG, "bad sizes or NULL occupations");
     pt::require_aligned(src, "src");
     pt::require_aligned(out, "out");
     if (tgt) pt::require_aligned(tgt, "tgt");

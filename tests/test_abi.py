@@ -97,3 +97,73 @@ def test_binding_struct_layout_matches_the_c_compiler(tmp_path):
         cls = getattr(_lib, name)
         want = [ctypes.sizeof(cls)] + [getattr(cls, f[0]).offset for f in cls._fields_]
         assert got[name] == want, (name, got[name], want)
+
+
+def test_header_bound_on_orbital_counts_matches_the_binding():
+    from paper_2501_03061_gb300 import _lib
+    text = open(os.path.join(ROOT, "include", "ptim.h")).read()
+    m = re.search(r"#define\s+PT_MAX_ORBITALS\s+(\d+)", text)
+    assert m and int(m.group(1)) == _lib.PT_MAX_ORBITALS
+    # N x N matrices are indexed with 32-bit products inside the kernels
+    assert _lib.PT_MAX_ORBITALS ** 2 < 2 ** 31
+
+
+def test_context_free_entry_rejects_invalid_arguments_on_the_host():
+    """pt_apply_exchange_noalloc takes no context, and every argument check it makes runs on the
+    host before any CUDA call, so the C ABI's error contract is testable without a GPU: each
+    invalid request returns PT_INVALID_ARG.  The pointers are 16-byte-aligned placeholders that
+    these rejected calls never dereference."""
+    from paper_2501_03061_gb300 import _lib
+    from paper_2501_03061_gb300 import build
+    lib = _lib.load(build.build())
+    P = ctypes.c_void_p
+    src, occ, out, tgt = P(0x10000), P(0x20000), P(0x30000), P(0x40000)
+
+    def grid(n=(8, 8, 8), L=(5.0, 5.0, 5.0)):
+        g = _lib.pt_grid()
+        g.nx, g.ny, g.nz = n
+        for a in range(3):
+            g.L[a] = L[a]
+        return g
+
+    def kern(t=1, mu=0.106):
+        k = _lib.pt_kernel()
+        k.type, k.mu, k.g0 = t, mu, float("nan")
+        return k
+
+    def call(src=src, occ=occ, N=4, tgt=None, M=0, out=out, g=None, k=None, prec=0):
+        g = grid() if g is None else g
+        k = kern() if k is None else k
+        return lib.pt_apply_exchange_noalloc(src, occ, N, tgt, M, out, ctypes.byref(g), ctypes.byref(k), prec, None)
+
+    cases = {
+        "N = 0": call(N=0),
+        "N above PT_MAX_ORBITALS": call(N=_lib.PT_MAX_ORBITALS + 1),
+        "N above the static scratch's 1024": call(N=1025),
+        "M = 0 with separate targets": call(tgt=tgt, M=0),
+        "M above PT_MAX_ORBITALS": call(tgt=tgt, M=_lib.PT_MAX_ORBITALS + 1),
+        "NULL occupations": call(occ=None),
+        "NULL source block": call(src=None),
+        "source not on a 16-byte boundary": call(src=P(0x10008)),
+        "output not on a 16-byte boundary": call(out=P(0x30004)),
+        "targets not on a 16-byte boundary": call(tgt=P(0x40008), M=2),
+        "output aliasing the sources": call(out=src),
+        "output aliasing the targets": call(tgt=tgt, M=2, out=tgt),
+        "unknown precision": call(prec=7),
+        "negative precision": call(prec=-1),
+        "unknown kernel type": call(k=kern(t=2)),
+        "screened kernel with mu = 0": call(k=kern(mu=0.0)),
+        "screened kernel with mu = NaN": call(k=kern(mu=float("nan"))),
+        "grid side 14 (not 2,3,5-smooth)": call(g=grid((14, 8, 8))),
+        "grid side 128 (above 64)": call(g=grid((8, 128, 8))),
+        "grid side 1": call(g=grid((8, 8, 1))),
+        "non-positive cell length": call(g=grid(L=(5.0, -1.0, 5.0))),
+        "infinite cell length": call(g=grid(L=(5.0, 5.0, float("inf")))),
+    }
+    bad = {k: _lib.STATUS_NAMES.get(v, v) for k, v in cases.items() if v != _lib.PT_INVALID_ARG}
+    assert not bad, bad
+    # a NULL grid or kernel is rejected too
+    k = kern()
+    assert lib.pt_apply_exchange_noalloc(src, occ, 4, None, 0, out, None, ctypes.byref(k), 0, None) == _lib.PT_INVALID_ARG
+    g = grid()
+    assert lib.pt_apply_exchange_noalloc(src, occ, 4, None, 0, out, ctypes.byref(g), None, 0, None) == _lib.PT_INVALID_ARG
