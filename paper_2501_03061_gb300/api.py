@@ -50,6 +50,31 @@ def _ptr(t: torch.Tensor):
     return C.c_void_p(t.data_ptr())
 
 
+def _points(cell) -> int:
+    return int(cell.n[0]) * int(cell.n[1]) * int(cell.n[2])
+
+
+def _sized(t: torch.Tensor, count: int, what: str, where: str = "", how: str = ""):
+    """Buffers the C ABI reads or writes by pointer must hold exactly what the call addresses
+    (the library cannot see tensor sizes; a short buffer would be read or written past its end)."""
+    if t.numel() != count:
+        raise PtimError(L.PT_INVALID_ARG,
+                        f"{where}{what} holds {t.numel()} elements where the call addresses {count}{how}")
+
+
+def _block(t: torch.Tensor, cell, what: str, where: str = ""):
+    """An (N, nz, ny, nx) orbital block on the cell's grid."""
+    n = _points(cell)
+    _sized(t, t.shape[0] * n, what, where, f" ({t.shape[0]} orbitals x {n} grid points of the cell)")
+
+
+def _result(out: torch.Tensor, count: int, dtype, device, what: str = "out", where: str = ""):
+    """A caller-supplied output: contiguous, of the call's type and device, `count` elements."""
+    if out.device != device or out.dtype != dtype or not out.is_contiguous():
+        raise ValueError(f"{where}{what} must be a contiguous {dtype} tensor on {device}")
+    _sized(out, count, what, where)
+
+
 def _vec3(A):
     """A host double[3] for an optional 3-vector argument (None -> NULL)."""
     if A is None:
@@ -137,8 +162,14 @@ class Context:
             self._orb(tgt, precision, "tgt")
         occ = occ.to(device=self.device, dtype=torch.float64).contiguous()
         ref = src if tgt is None else tgt
+        _block(src, cell, "src")
+        if tgt is not None:
+            _block(tgt, cell, "tgt")
+        if occ.numel() < src.shape[0]:
+            raise PtimError(L.PT_INVALID_ARG, f"occ holds {occ.numel()} occupations for {src.shape[0]} orbitals")
         if out is None:
             out = torch.empty_like(ref)
+        _result(out, ref.numel(), ref.dtype, self.device)
         g, k = _grid(cell), _kernel(kernel)
         st = self.lib.pt_apply_exchange(self.h, _ptr(src), _ptr(occ), src.shape[0],
                                         None if tgt is None else _ptr(tgt), ref.shape[0], _ptr(out),
@@ -157,9 +188,17 @@ class Context:
             if tgt is not None:
                 self._orb(tgt, precision, "tgt")
             occ = it["occ"].to(device=self.device, dtype=torch.float64).contiguous()
+            ref = src if tgt is None else tgt
+            where = f"item {k}: "
+            _block(src, it["cell"], "src", where)
+            if tgt is not None:
+                _block(tgt, it["cell"], "tgt", where)
+            if occ.numel() < src.shape[0]:
+                raise PtimError(L.PT_INVALID_ARG, f"{where}occ holds {occ.numel()} occupations for {src.shape[0]} orbitals")
             out = it.get("out")
             if out is None:
-                out = torch.empty_like(src if tgt is None else tgt)
+                out = torch.empty_like(ref)
+            _result(out, ref.numel(), ref.dtype, self.device, where=where)
             keep.append(occ)
             outs.append(out)
             a = arr[k]
@@ -176,7 +215,10 @@ class Context:
     # ---- ACE --------------------------------------------------------------------------------
     def build_ace(self, phi, occ, *, cell, kernel=None, precision="fp64", stream=None) -> Ace:
         self._orb(phi, precision, "phi")
+        _block(phi, cell, "phi")
         occ = occ.to(device=self.device, dtype=torch.float64).contiguous()
+        if occ.numel() < phi.shape[0]:
+            raise PtimError(L.PT_INVALID_ARG, f"occ holds {occ.numel()} occupations for {phi.shape[0]} orbitals")
         g, k = _grid(cell), _kernel(kernel)
         h = C.c_void_p()
         st = self.lib.pt_build_ace(self.h, _ptr(phi), _ptr(occ), phi.shape[0], C.byref(g), C.byref(k),
@@ -187,6 +229,8 @@ class Context:
     def build_ace_from(self, W, phi, *, cell, precision="fp64", stream=None) -> Ace:
         self._orb(W, precision, "W")
         self._orb(phi, precision, "phi")
+        _block(phi, cell, "phi")
+        _sized(W, phi.numel(), "W")
         g = _grid(cell)
         h = C.c_void_p()
         st = self.lib.pt_build_ace_from(self.h, _ptr(W), _ptr(phi), phi.shape[0], C.byref(g),
@@ -196,8 +240,10 @@ class Context:
 
     def apply_ace(self, ace: Ace, psi, out=None, stream=None):
         self._orb(psi, ace.precision, "psi")
+        _block(psi, ace.cell, "psi")
         if out is None:
             out = torch.empty_like(psi)
+        _result(out, psi.numel(), psi.dtype, self.device)
         st = self.lib.pt_apply_ace(self.h, ace.handle, _ptr(psi), psi.shape[0], _ptr(out), _stream(stream))
         self._check(st, "pt_apply_ace")
         return out
@@ -208,8 +254,11 @@ class Context:
         self._orb(A, precision, "A")
         B = A if B is None else B
         self._orb(B, precision, "B")
+        _block(A, cell, "A")
+        _block(B, cell, "B")
         if out is None:
             out = torch.empty((A.shape[0], B.shape[0]), dtype=torch.complex128, device=self.device)
+        _result(out, A.shape[0] * B.shape[0], torch.complex128, self.device)
         g = _grid(cell)
         st = self.lib.pt_overlap(self.h, _ptr(A), A.shape[0], _ptr(B), B.shape[0], C.byref(g),
                                  L.PRECISIONS[precision], _ptr(out), _stream(stream))
@@ -222,8 +271,10 @@ class Context:
         B = B.to(device=self.device, dtype=torch.complex128).contiguous()
         if B.dim() != 2 or B.shape[0] != A.shape[0]:
             raise ValueError("B must be (N1, N2) with N1 = A.shape[0]")
+        _block(A, cell, "A")
         if out is None:
             out = torch.empty((B.shape[1],) + tuple(A.shape[1:]), dtype=A.dtype, device=self.device)
+        _result(out, B.shape[1] * _points(cell), A.dtype, self.device)
         g = _grid(cell)
         st = self.lib.pt_rotate(self.h, _ptr(A), A.shape[0], _ptr(B), B.shape[1], C.byref(g),
                                 L.PRECISIONS[precision], _ptr(out), _stream(stream))
@@ -235,9 +286,12 @@ class Context:
                 A=None, out=None, stream=None):
         """H psi with the velocity-gauge vector potential A (3 floats, or None for no field)."""
         self._orb(psi, precision, "psi")
+        _block(psi, cell, "psi")
         vloc = vloc.to(device=self.device, dtype=torch.float64).contiguous()
+        _sized(vloc, _points(cell), "vloc")
         if out is None:
             out = torch.empty_like(psi)
+        _result(out, psi.numel(), psi.dtype, self.device)
         g = _grid(cell)
         st = self.lib.pt_apply_H(self.h, _ptr(psi), psi.shape[0], _ptr(out), _ptr(vloc),
                                  None if ace is None else ace.handle, float(alpha), float(ecut), _vec3(A),
@@ -248,7 +302,9 @@ class Context:
     def current(self, phi, sigma, *, cell, precision="fp64", A=None, spin=2.0, stream=None):
         """J = spin/Omega Re Tr[P (-i grad + A)] as a (3,) numpy array (synchronises the stream)."""
         self._orb(phi, precision, "phi")
+        _block(phi, cell, "phi")
         sigma = sigma.to(device=self.device, dtype=torch.complex128).contiguous()
+        _sized(sigma, phi.shape[0] ** 2, "sigma")
         g = _grid(cell)
         J = (C.c_double * 3)()
         st = self.lib.pt_current(self.h, _ptr(phi), _ptr(sigma), phi.shape[0], C.byref(g), L.PRECISIONS[precision],
@@ -260,9 +316,12 @@ class Context:
     def density(self, phi, sigma, *, cell, precision="fp64", spin=2.0, out=None, stream=None):
         """rho = spin * P(r, r), P = Phi sigma Phi^* (float64 tensor shaped like one orbital)."""
         self._orb(phi, precision, "phi")
+        _block(phi, cell, "phi")
         sigma = sigma.to(device=self.device, dtype=torch.complex128).contiguous()
+        _sized(sigma, phi.shape[0] ** 2, "sigma")
         if out is None:
             out = torch.empty(phi.shape[1:], dtype=torch.float64, device=self.device)
+        _result(out, _points(cell), torch.float64, self.device)
         g = _grid(cell)
         st = self.lib.pt_density(self.h, _ptr(phi), _ptr(sigma), phi.shape[0], C.byref(g), L.PRECISIONS[precision],
                                  float(spin), _ptr(out), _stream(stream))
@@ -272,10 +331,13 @@ class Context:
     def hxc_potential(self, rho, vloc=None, *, cell, energies=False, out=None, stream=None):
         """vloc + V_H[rho] + v_xc(rho) (FP64); with energies=True also returns (E_H, E_xc)."""
         rho = rho.to(device=self.device, dtype=torch.float64).contiguous()
+        _sized(rho, _points(cell), "rho")
         if vloc is not None:
             vloc = vloc.to(device=self.device, dtype=torch.float64).contiguous()
+            _sized(vloc, _points(cell), "vloc")
         if out is None:
             out = torch.empty_like(rho)
+        _result(out, rho.numel(), torch.float64, self.device)
         g = _grid(cell)
         e = (C.c_double * 2)()
         st = self.lib.pt_hxc_potential(self.h, _ptr(rho), None if vloc is None else _ptr(vloc), C.byref(g),
@@ -286,6 +348,8 @@ class Context:
     # ---- occupations ----------------------------------------------------------------------
     def diag_occupations(self, sigma, stream=None):
         sigma = sigma.to(device=self.device, dtype=torch.complex128).contiguous()
+        if sigma.dim() != 2 or sigma.shape[0] != sigma.shape[1]:
+            raise PtimError(L.PT_INVALID_ARG, "sigma must be a square (N, N) matrix")
         N = sigma.shape[0]
         Q = torch.empty_like(sigma)
         d = torch.empty(N, dtype=torch.float64, device=self.device)
@@ -301,7 +365,10 @@ class Context:
         self._orb(phi, precision, "phi")
         if sigma.dtype != torch.complex128 or not sigma.is_contiguous() or sigma.device != self.device:
             raise ValueError("sigma must be a contiguous complex128 tensor on the device")
+        _block(phi, cell, "phi")
+        _sized(sigma, phi.shape[0] ** 2, "sigma")
         vloc = vloc.to(device=self.device, dtype=torch.float64).contiguous()
+        _sized(vloc, _points(cell), "vloc")
         p = L.pt_ptim_params(dt, alpha, ecut, tol, max_outer, max_inner, anderson_depth, anderson_beta,
                              int(bool(use_ace)), spin, int(bool(hxc)),
                              (C.c_double * 3)(*(A if A is not None else (0.0, 0.0, 0.0))))
