@@ -301,6 +301,9 @@ typedef struct {
      11 V_Hxc (midpoint density, Hartree FFT, LDA; params.hxc = 1) */
   double phase_ms[12];
   int eig_sweeps;           /* Jacobi sweeps of the sigma eigensolves (phase 6) */
+  double total_energy;      /* E(t_n) of the input state (Ha): spin Tr[P_n (-Lap/2 + V_loc)] + E_x
+                               (+ E_H + E_xc with params.hxc; the kinetic term carries params.A),
+                               from the first iteration, where the midpoint is (Phi_n, sigma_n) */
 } pt_ptim_stats;
 
 /* One PT-IM(-ACE) step from (phi, sigma) = (Phi_n, sigma_n) to (Phi_{n+1}, sigma_{n+1}),

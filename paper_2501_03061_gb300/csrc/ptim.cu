@@ -206,6 +206,13 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
   // self-consistent V_Hxc: midpoint density and the total local potential V_loc + V_Hxc[rho_h]
   double* rho = P.hxc ? static_cast<double*>(S.buf("ptim_rho", S.ng * sizeof(double))) : nullptr;
   double* vtot = P.hxc ? static_cast<double*>(S.buf("ptim_vtot", S.ng * sizeof(double))) : nullptr;
+  double* hxc_part = P.hxc ? static_cast<double*>(S.buf("ptim_hxc_part", 2 * size_t(g.nz) * sizeof(double))) : nullptr;
+  // E(t_n) from the first inner iteration, whose midpoint is (Phi_n, sigma_n) and whose exchange
+  // operator is exact on it: spin Re Tr[sigma_n A_0] holds the exchange energy twice and, with
+  // V_Hxc, int rho V_Hxc in place of E_H + E_xc (host copies of A_0, sigma_n and the V_Hxc fields)
+  std::vector<c128> e_A, e_sig;
+  std::vector<double> e_rho, e_vt, e_vl, e_part;
+  double ex0 = NAN;
 
   PT_CUDA_CHECK(cudaMemcpyAsync(phin, phi, fb, cudaMemcpyDeviceToDevice, st));
   PT_CUDA_CHECK(cudaMemcpyAsync(sign, sig, mb, cudaMemcpyDeviceToDevice, st));
@@ -324,6 +331,7 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
     std::vector<int> order;  // active history slots, oldest first
     for (int inner = 0; inner < P.max_inner; ++inner) {
       stv.inner++;
+      const bool first = stv.inner == 1;
       cx<T>* rphi = rphi_buf[inner & 1];
       c128* rsig = rsig_buf[inner & 1];
       S.midpoint(phih, sigh, phi, phin, sig, sign);
@@ -333,7 +341,7 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
         // exchange term below, so it holds chi = Phi_h sigma_h
         tm.begin(PH_HXC);
         density<T>(ctx, phih, sigh, N, S.ng, P.spin, X, rho, st);
-        hxc_potential(ctx, rho, vloc, g, vtot, nullptr, st);
+        hxc_potential(ctx, rho, vloc, g, vtot, first ? hxc_part : nullptr, st);
         tm.end();
         vh = vtot;
       }
@@ -344,6 +352,7 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
       } else {
         exchange_on_midpoint(X, inner == 0);
       }
+      if (first) ex0 = stv.exch_energy;
       tm.begin(PH_H);
       apply_h(ctx, phih, N, Hphi, vh, X, P.alpha, P.ecut, g, prec, st, P.A);
       tm.end();
@@ -351,6 +360,23 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
       // A = <Phi_h|H Phi_h> and S = <Phi_h|Phi_h> are Hermitian: upper tiles only, mirrored
       gram<T>(ctx, phih, Hphi, N, N, S.ng, S.dV, A, st, true);
       gram<T>(ctx, phih, phih, N, N, S.ng, S.dV, Sm, st, true);
+      if (first) {
+        e_A.resize(S.n2);
+        e_sig.resize(S.n2);
+        PT_CUDA_CHECK(cudaMemcpyAsync(e_A.data(), A, mb, cudaMemcpyDeviceToHost, st));
+        PT_CUDA_CHECK(cudaMemcpyAsync(e_sig.data(), sign, mb, cudaMemcpyDeviceToHost, st));
+        if (P.hxc) {
+          e_rho.resize(S.ng);
+          e_vt.resize(S.ng);
+          e_vl.resize(S.ng);
+          e_part.resize(2 * size_t(g.nz));
+          PT_CUDA_CHECK(cudaMemcpyAsync(e_rho.data(), rho, S.ng * sizeof(double), cudaMemcpyDeviceToHost, st));
+          PT_CUDA_CHECK(cudaMemcpyAsync(e_vt.data(), vtot, S.ng * sizeof(double), cudaMemcpyDeviceToHost, st));
+          PT_CUDA_CHECK(cudaMemcpyAsync(e_vl.data(), vloc, S.ng * sizeof(double), cudaMemcpyDeviceToHost, st));
+          PT_CUDA_CHECK(cudaMemcpyAsync(e_part.data(), hxc_part, e_part.size() * sizeof(double),
+                                        cudaMemcpyDeviceToHost, st));
+        }
+      }
       tm.end();
       tm.begin(PH_SUBNN);
       // S^{-1} A = L^{-*} (L^{-1} A)
@@ -376,6 +402,25 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
       PT_CUDA_CHECK(cudaMemcpyAsync(&h_info, info, sizeof(int), cudaMemcpyDeviceToHost, st));
       double rr = 0, xx = 0;
       S.norm2_pair(rphi, rsig, phi, sig, &rr, &xx);  // synchronises st
+      if (first) {
+        double tr = 0.0;  // Re Tr[sigma_n A_0] = Re sum_ij sigma_ij A_ji
+        for (int i = 0; i < N; ++i)
+          for (int j = 0; j < N; ++j) {
+            const c128 sv = e_sig[size_t(i) * N + j], av = e_A[size_t(j) * N + i];
+            tr += sv.re * av.re - sv.im * av.im;
+          }
+        double e = P.spin * tr - ex0;
+        if (P.hxc) {
+          double eh = 0.0, exc = 0.0, rv = 0.0;
+          for (int z = 0; z < g.nz; ++z) {
+            eh += e_part[2 * size_t(z)];
+            exc += e_part[2 * size_t(z) + 1];
+          }
+          for (size_t r = 0; r < S.ng; ++r) rv += e_rho[r] * (e_vt[r] - e_vl[r]);
+          e += S.dV * (eh + exc - rv);
+        }
+        stv.total_energy = e;
+      }
       if (h_info) fail(PT_NOT_PD, "PT-IM: overlap of the midpoint orbitals is not positive definite");
       const double res = std::sqrt(rr / xx);
       stv.residual = res;
