@@ -62,10 +62,11 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 form comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--mode", default="step",
-                    choices=["step", "exchange", "serve", "batched", "precision", "contractions"],
+                    choices=["step", "exchange", "serve", "batched", "precision", "contractions", "library"],
                     help="step: PT-IM steps (the benchmark); exchange: only V_x applications on the same cell "
                          "(profiler captures of the exchange kernel); serve / batched: configs 5 / 4 alone; "
-                         "precision: config 3 per-result errors; contractions: Gram/rotation engines at 64^3")
+                         "precision: config 3 per-result errors; contractions: Gram/rotation engines at 64^3; "
+                         "library: cuFFT exchange and cuBLAS contractions timed beside the library (comparison)")
     ap.add_argument("--serve-window", type=float, default=15.0, help="seconds of arrivals per serving phase")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement in step mode")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
@@ -319,6 +320,112 @@ def contraction_measurement() -> dict:
         ctx.set_option("tc_gram", 0)
         ctx.close()
     return {"workload": "64^3 grid, N = 320 (random complex fields), B = N x N", "results": res}
+
+
+def screened_kernel_table(cell, mu, dtype, device):
+    """K(G) = 4 pi/|G|^2 (1 - exp(-|G|^2/(4 mu^2))), K(0) = pi/mu^2, on the (nz, ny, nx) grid (for the
+    library comparison only; the library builds its own table)."""
+    import torch
+    axes = []
+    for n, L in zip(cell.n, cell.L):
+        m = torch.arange(n, dtype=torch.float64)
+        m = torch.where(m < (n + 1) // 2, m, m - n)
+        axes.append(2 * math.pi * m / L)
+    gx, gy, gz = axes
+    g2 = gz[:, None, None] ** 2 + gy[None, :, None] ** 2 + gx[None, None, :] ** 2
+    K = torch.where(g2 > 0, 4 * math.pi / g2.clamp_min(1e-300) * (1 - torch.exp(-g2 / (4 * mu * mu))),
+                    torch.full_like(g2, math.pi / (mu * mu)))
+    return K.to(device=device, dtype=dtype)
+
+
+def library_exchange(phi, occ, K, batch: int = 64):
+    """V_x phi from cuFFT (torch.fft) and elementwise torch ops, for comparison with the fused
+    kernels: symmetric pairs i <= j in batches of targets; v_ji = conj(v_ij) for the real, even
+    kernel feeds the i-side of each pair."""
+    import torch
+    N = phi.shape[0]
+    W = torch.zeros_like(phi)
+    d = occ.to(device=phi.device, dtype=phi.real.dtype)
+    dims = (1, 2, 3)
+    for i in range(N):
+        for j0 in range(i, N, batch):
+            j1 = min(N, j0 + batch)
+            v = torch.fft.ifftn(K * torch.fft.fftn(phi[i].conj()[None] * phi[j0:j1], dim=dims), dim=dims)
+            W[j0:j1] -= d[i] * phi[i][None] * v
+            o = 1 if j0 == i else 0  # the diagonal pair feeds W_i once, above
+            if o < j1 - j0:
+                W[i] -= (d[j0 + o:j1, None, None, None] * phi[j0 + o:j1] * v[o:].conj()).sum(0)
+    return W
+
+
+def library_comparison() -> dict:
+    """cuFFT and cuBLAS timed beside the library on the benchmark cell (64^3, N = 320): one V_x
+    application through torch.fft (C2C and Z2Z) against pt_apply_exchange, and the N x N Gram
+    and the rotation through torch.matmul (cuBLAS CGEMM / ZGEMM) against pt_overlap / pt_rotate.
+    Comparisons only: none of these library calls is on the library's path."""
+    import numpy as np
+    import torch
+
+    from paper_2501_03061_gb300 import api, synth
+
+    w = synth.ptim_cell128()
+    N = w.phi.shape[0]
+    npairs = N * (N + 1) // 2
+    ctx = api.Context(0)
+    res = {"workload": "64^3 grid, N = 320, screened kernel mu = 0.106 (the benchmark cell)"}
+
+    def timed(f, reps=1):
+        f()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            out = f()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps, out
+
+    try:
+        occ = torch.from_numpy(w.occ).cuda()
+        for prec, cdt, rdt in (("fp32", np.complex64, torch.float32), ("fp64", np.complex128, torch.float64)):
+            phi = torch.from_numpy(w.phi.astype(cdt)).cuda()
+            K = screened_kernel_table(w.cell, w.kernel["mu"], rdt, "cuda")
+            t_lib, ref = timed(lambda: ctx.apply_exchange(phi, occ, cell=w.cell, kernel=w.kernel, precision=prec))
+            t_fft, out = timed(lambda: library_exchange(phi, occ, K))
+            res[f"exchange_{prec}"] = {
+                "library_ms": t_lib, "cufft_ms": t_fft, "library_pair_ffts_per_s": npairs / (t_lib / 1e3),
+                "cufft_pair_ffts_per_s": npairs / (t_fft / 1e3), "speedup_vs_cufft": t_fft / t_lib,
+                "rel_difference": float((out - ref).norm() / ref.norm())}
+            del phi, ref, out
+            torch.cuda.empty_cache()
+        cell = w.cell
+        a = torch.from_numpy(w.phi.astype(np.complex64)).cuda()
+        Q = torch.linalg.qr(torch.randn((N, N), dtype=torch.complex128, device="cuda"))[0]
+        dV = cell.volume / cell.ng
+        A2 = a.reshape(N, -1)
+        ctx.set_option("tc_gram", 1)
+        t_lib, S_lib = timed(lambda: ctx.overlap(a, a, cell=cell, precision="fp32"), 5)
+        t_rl, R_lib = timed(lambda: ctx.rotate(a, Q, cell=cell, precision="fp32"), 5)
+        ctx.set_option("tc_gram", 0)
+        t_cb, S_cb = timed(lambda: dV * (A2.conj() @ A2.T), 5)
+        Q64 = Q.to(torch.complex64)
+        t_rc, R_cb = timed(lambda: Q64.T @ A2, 5)
+        res["gram_fp32"] = {"library_tcgen05_3xTF32_ms": t_lib, "cublas_cgemm_ms": t_cb,
+                            "rel_difference": float((S_lib.to(torch.complex128) - S_cb.to(torch.complex128)).norm()
+                                                    / S_cb.to(torch.complex128).norm())}
+        res["rotate_fp32"] = {"library_tcgen05_3xTF32_ms": t_rl, "cublas_cgemm_ms": t_rc,
+                              "rel_difference": float((R_lib.reshape(N, -1) - R_cb).norm() / R_cb.norm())}
+        del a, A2, S_lib, R_lib, S_cb, R_cb
+        torch.cuda.empty_cache()
+        a64 = torch.from_numpy(w.phi).cuda()
+        A64 = a64.reshape(N, -1)
+        t_lib, S_lib = timed(lambda: ctx.overlap(a64, a64, cell=cell, precision="fp64"), 3)
+        t_cb, S_cb = timed(lambda: dV * (A64.conj() @ A64.T), 3)
+        res["gram_fp64"] = {"library_ms": t_lib, "cublas_zgemm_ms": t_cb,
+                            "rel_difference": float((S_lib - S_cb).norm() / S_cb.norm())}
+    finally:
+        ctx.close()
+    return res
 
 
 def serve_measurement(window_s: float, slots: int = 6) -> dict:
@@ -712,6 +819,8 @@ def main():
         print(json.dumps({"mode": "precision", "precision_forms": precision_forms()}), flush=True)
     elif args.mode == "contractions":
         print(json.dumps({"mode": "contractions", "contractions": contraction_measurement()}), flush=True)
+    elif args.mode == "library":
+        print(json.dumps({"mode": "library", "library": library_comparison()}), flush=True)
     elif args.mode == "batched":
         import torch
         torch.cuda.set_device(0)
