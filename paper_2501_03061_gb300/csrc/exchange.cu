@@ -164,72 +164,22 @@ __global__ void __launch_bounds__(NT) k_pair_inv_acc(GridPlan gp, const cx<T>* _
 
 std::shared_ptr<ScheduleImpl> build_schedule(int N, int M, bool sym, int B) {
   auto s = std::make_shared<ScheduleImpl>();
+  PairPlan plan = plan_pairs(N, M, sym, B);
   s->N = N;
   s->M = M;
   s->B = B;
   s->sym = sym;
-  std::vector<PairDesc> pairs;
-  std::vector<TargetDesc> tgts;
-  std::vector<Contrib> cons;
-  std::vector<char> touched(sym ? N : M, 0);
-  s->pair_off.push_back(0);
-  s->tgt_off.push_back(0);
-  auto finish_batch = [&](std::map<int, std::vector<Contrib>>& per_t) {
-    for (auto& kv : per_t) {
-      TargetDesc td;
-      td.t = kv.first;
-      td.cbeg = int(cons.size());
-      for (auto& c : kv.second) cons.push_back(c);
-      td.cend = int(cons.size());
-      td.first = touched[kv.first] ? 0 : 1;
-      touched[kv.first] = 1;
-      tgts.push_back(td);
-    }
-    s->max_pairs = std::max(s->max_pairs, int(pairs.size()) - s->pair_off.back());
-    s->max_tgts = std::max(s->max_tgts, int(tgts.size()) - s->tgt_off.back());
-    s->pair_off.push_back(int(pairs.size()));
-    s->tgt_off.push_back(int(tgts.size()));
-  };
-  if (sym) {
-    const int nb = (N + B - 1) / B;
-    for (int J = 0; J < nb; ++J) {
-      for (int I = 0; I <= J; ++I) {
-        std::map<int, std::vector<Contrib>> per_t;
-        const int base = int(pairs.size());
-        const int i0 = I * B, i1 = std::min(N, i0 + B), j0 = J * B, j1 = std::min(N, j0 + B);
-        for (int i = i0; i < i1; ++i) {
-          for (int j = (I == J ? i : j0); j < j1; ++j) {
-            const int slot = int(pairs.size()) - base;
-            pairs.push_back({i, j, i, i == j ? -1 : j});
-            per_t[j].push_back({slot, i, i, 0});
-            if (i != j) per_t[i].push_back({slot, j, j, 1});
-          }
-        }
-        finish_batch(per_t);
-      }
-    }
-  } else {
-    const int nbi = (N + B - 1) / B, nbj = (M + B - 1) / B;
-    for (int J = 0; J < nbj; ++J) {
-      for (int I = 0; I < nbi; ++I) {
-        std::map<int, std::vector<Contrib>> per_t;
-        const int base = int(pairs.size());
-        const int i0 = I * B, i1 = std::min(N, i0 + B), j0 = J * B, j1 = std::min(M, j0 + B);
-        for (int j = j0; j < j1; ++j) {
-          for (int i = i0; i < i1; ++i) {
-            const int slot = int(pairs.size()) - base;
-            pairs.push_back({i, j, i, -1});
-            per_t[j].push_back({slot, i, i, 0});
-          }
-        }
-        finish_batch(per_t);
-      }
-    }
-  }
-  s->total_pairs = (long long)pairs.size();
-  s->h_pairs = pairs;
-  s->h_tgts = tgts;
-  s->h_contribs = cons;
+  s->pair_off = std::move(plan.pair_off);
+  s->tgt_off = std::move(plan.tgt_off);
+  s->max_pairs = plan.max_pairs;
+  s->max_tgts = plan.max_tgts;
+  s->total_pairs = (long long)plan.pairs.size();
+  s->h_pairs = std::move(plan.pairs);
+  s->h_tgts = std::move(plan.tgts);
+  s->h_contribs = std::move(plan.contribs);
+  const auto& pairs = s->h_pairs;
+  const auto& tgts = s->h_tgts;
+  const auto& cons = s->h_contribs;
   PT_CUDA_CHECK(cudaMalloc(&s->d_pairs, pairs.size() * sizeof(PairDesc)));
   PT_CUDA_CHECK(cudaMalloc(&s->d_tgts, tgts.size() * sizeof(TargetDesc)));
   PT_CUDA_CHECK(cudaMalloc(&s->d_contribs, cons.size() * sizeof(Contrib)));

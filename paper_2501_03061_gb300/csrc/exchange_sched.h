@@ -7,20 +7,10 @@
 #include <vector>
 
 #include "common.cuh"
+#include "exchange_plan.h"
 #include "fft.cuh"
 
 namespace pt {
-
-struct PairDesc {
-  int i, j;    // source index, target index
-  int o1, o2;  // occupation indices of its contributions (o2 < 0: a single one)
-};
-struct TargetDesc {
-  int t, cbeg, cend, first;
-};
-struct Contrib {
-  int slot, partner, occ, conj;
-};
 
 __device__ __forceinline__ bool pair_skipped(const PairDesc& pd, const double* occ) {
   return occ[pd.o1] == 0.0 && (pd.o2 < 0 || occ[pd.o2] == 0.0);
@@ -45,7 +35,7 @@ struct ScheduleImpl {
   }
 };
 
-// tiles of B x B orbitals; symmetric: I <= J tiles with i <= j inside diagonal tiles
+// plan_pairs (tiles of B x B orbitals) with its tables copied to the device
 std::shared_ptr<ScheduleImpl> build_schedule(int N, int M, bool sym, int B);
 
 // the three generic tile passes for one pair batch on caller-provided device buffers
