@@ -327,6 +327,15 @@ const char* pt_version(void);
 /* Number of this library's kernel launches issued so far by the calling process. */
 long long pt_kernel_launches(void);
 
+/* Self-test of the bounded device waits (no counterpart in the paper).  One CTA waits on a
+ * shared-memory mbarrier through the same deadline-bounded wait the TMA and tensor-core
+ * pipelines use.  arrive = 1: the barrier completes and the call returns PT_OK.  arrive = 0:
+ * nothing ever arrives, the wait gives up after timeout_s (0 < timeout_s <= 2), the kernel
+ * records the expiry and returns, and the call returns PT_TIMEOUT with the context still usable
+ * (the path every pipeline takes when a copy or a peer role never completes).  Synchronises the
+ * stream.  PT_INVALID_ARG for a NULL context, arrive not 0 or 1, or timeout_s out of range. */
+pt_status pt_selftest_wait(pt_ctx* ctx, int arrive, double timeout_s, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

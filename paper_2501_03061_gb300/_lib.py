@@ -76,6 +76,7 @@ PROTOTYPES = {
     "pt_ptim_footprint": (C.c_size_t, [i32, C.POINTER(pt_grid), i32, i32]),
     "pt_version": (C.c_char_p, []),
     "pt_kernel_launches": (C.c_longlong, []),
+    "pt_selftest_wait": (i32, [vp, i32, C.c_double, vp]),
 }
 
 _lib = None

@@ -145,6 +145,14 @@ class Context:
             raise ValueError(f"{what} must be a contiguous {_CDTYPE[precision]} (N, nz, ny, nx) tensor on {self.device}")
         return t
 
+    def selftest_wait(self, arrive: bool, timeout_s: float = 0.05, stream=None) -> str:
+        """Bounded device-wait self-test: the status name, "PT_TIMEOUT" when nothing arrives
+        (the expected outcome with arrive=False), "PT_OK" when the barrier completes."""
+        st = self.lib.pt_selftest_wait(self.h, int(bool(arrive)), float(timeout_s), _stream(stream))
+        if st not in (L.PT_OK, L.PT_TIMEOUT):
+            self._check(st, "pt_selftest_wait")
+        return L.STATUS_NAMES[st]
+
     def workspace_bytes(self) -> int:
         return int(self.lib.pt_workspace_bytes(self.h))
 

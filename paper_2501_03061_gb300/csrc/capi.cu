@@ -552,4 +552,15 @@ const char* pt_version(void) { return "ptim-gb300 0.1 (sm_103a)"; }
 
 long long pt_kernel_launches(void) { return pt::g_launches.load(); }
 
+pt_status pt_selftest_wait(pt_ctx* ctx, int arrive, double timeout_s, void* stream) {
+  return guarded(ctx, [&]() -> pt_status {
+    if (!ctx) pt::fail(PT_INVALID_ARG, "context is NULL");
+    if (arrive != 0 && arrive != 1) pt::fail(PT_INVALID_ARG, "arrive must be 0 or 1");
+    if (!(timeout_s > 0.0) || timeout_s > 2.0) pt::fail(PT_INVALID_ARG, "timeout_s must be in (0, 2]");
+    set_device(ctx);
+    pt::wait_selftest(ctx, arrive, timeout_s, static_cast<cudaStream_t>(stream));
+    return PT_OK;
+  });
+}
+
 }  // extern "C"

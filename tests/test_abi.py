@@ -167,3 +167,11 @@ def test_context_free_entry_rejects_invalid_arguments_on_the_host():
     assert lib.pt_apply_exchange_noalloc(src, occ, 4, None, 0, out, None, ctypes.byref(k), 0, None) == _lib.PT_INVALID_ARG
     g = grid()
     assert lib.pt_apply_exchange_noalloc(src, occ, 4, None, 0, out, ctypes.byref(g), None, 0, None) == _lib.PT_INVALID_ARG
+
+
+def test_selftest_wait_checks_its_arguments_on_the_host():
+    """pt_selftest_wait rejects a NULL context before any CUDA call."""
+    from paper_2501_03061_gb300 import _lib
+    from paper_2501_03061_gb300 import build
+    lib = _lib.load(build.build())
+    assert lib.pt_selftest_wait(None, 0, 0.05, None) == _lib.PT_INVALID_ARG
