@@ -150,6 +150,15 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
                       const pt_kernel& kern, const pt_ptim_params& P, pt_precision prec, pt_ptim_stats* stats,
                       cudaStream_t st) {
   Step<T> S{ctx, N, ng_of(g), ng_of(g) * N, size_t(N) * N, dv_of(g), g, kern, prec, P, st, 0};
+  // a step that fails part-way (non-finite input, a failed factorisation) may leave a basis that is
+  // not unitary in "ptim_Q": the context's next step must not warm-start its eigensolves from it
+  struct WarmStartGuard {
+    pt_ctx* c;
+    bool done;
+    ~WarmStartGuard() {
+      if (!done) c->ptim_q_n = 0;
+    }
+  } warm_guard{ctx, false};
   const size_t fb = S.n1 * sizeof(cx<T>);
   const size_t mb = S.n2 * sizeof(c128);
   const int depth = std::max(1, std::min(P.anderson_depth, kMaxDepth));
@@ -536,6 +545,7 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
   }
   stv.converged = converged ? 1 : 0;
   if (stats) *stats = stv;
+  warm_guard.done = true;
   return converged ? PT_OK : PT_NOT_CONVERGED;
 }
 
