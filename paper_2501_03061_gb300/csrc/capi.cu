@@ -5,6 +5,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "trace.h"
 
 namespace pt {
 
@@ -64,8 +65,10 @@ void pt_ctx::release_all() {
 
 namespace {
 
+// every entry point: an NVTX range named after it, C++ errors turned into status codes
 template <class F>
-pt_status guarded(pt_ctx* ctx, F&& f) {
+pt_status guarded(const char* entry, pt_ctx* ctx, F&& f) {
+  pt::TraceRange range(entry);
   try {
     pt_status s = f();
     if (ctx && s == PT_OK) ctx->err.clear();
@@ -115,7 +118,7 @@ pt_status pt_create(pt_ctx** out, int device, size_t hbm_budget) {
   if (!out) return PT_INVALID_ARG;
   *out = nullptr;
   auto* ctx = new pt_ctx();
-  pt_status s = guarded(ctx, [&]() -> pt_status {
+  pt_status s = guarded(__func__, ctx, [&]() -> pt_status {
     int n = 0;
     pt::check_cuda(cudaGetDeviceCount(&n), "cudaGetDeviceCount");
     if (device < 0 || device >= n) pt::fail(PT_INVALID_ARG, "no such CUDA device");
@@ -153,7 +156,7 @@ const char* pt_last_error(const pt_ctx* ctx) { return ctx ? ctx->err.c_str() : "
 size_t pt_workspace_bytes(const pt_ctx* ctx) { return ctx ? ctx->held : 0; }
 
 pt_status pt_trim(pt_ctx* ctx) {
-  return guarded(ctx, [&]() -> pt_status {
+  return guarded(__func__, ctx, [&]() -> pt_status {
     if (!ctx) pt::fail(PT_INVALID_ARG, "context is NULL");
     set_device(ctx);
     ctx->release_all();
@@ -162,7 +165,7 @@ pt_status pt_trim(pt_ctx* ctx) {
 }
 
 pt_status pt_set_option(pt_ctx* ctx, const char* key, double value) {
-  return guarded(ctx, [&]() -> pt_status {
+  return guarded(__func__, ctx, [&]() -> pt_status {
     if (!ctx || !key) pt::fail(PT_INVALID_ARG, "context or key is NULL");
     if (std::string(key) == "graphs" || std::string(key) == "autotune") {
       (std::string(key) == "graphs" ? ctx->use_graphs : ctx->autotune) = value != 0.0 ? 1 : 0;
@@ -203,7 +206,7 @@ pt_status pt_set_option(pt_ctx* ctx, const char* key, double value) {
 pt_status pt_apply_exchange(pt_ctx* ctx, const void* src, const double* occ, int N, const void* tgt, int M,
                             void* out, const pt_grid* grid, const pt_kernel* kernel, pt_precision prec,
                             void* stream) {
-  return guarded(ctx, [&]() -> pt_status {
+  return guarded(__func__, ctx, [&]() -> pt_status {
     check_common(ctx, grid, prec);
     check_kernel(kernel);
     check_count(N, "N");
@@ -223,7 +226,7 @@ pt_status pt_apply_exchange(pt_ctx* ctx, const void* src, const double* occ, int
 
 pt_status pt_apply_exchange_batched(pt_ctx* ctx, const pt_exchange_item* items, int count, pt_precision prec,
                                     long long* pair_ffts, size_t* graph_nodes, void* stream) {
-  return guarded(ctx, [&]() -> pt_status {
+  return guarded(__func__, ctx, [&]() -> pt_status {
     if (!ctx) pt::fail(PT_INVALID_ARG, "context is NULL");
     if (count <= 0 || !items) pt::fail(PT_INVALID_ARG, "no items");
     if (prec < PT_FP64 || prec > PT_FP32_TC_BF16) pt::fail(PT_INVALID_ARG, "unknown precision");
@@ -254,7 +257,7 @@ pt_status pt_apply_exchange_batched(pt_ctx* ctx, const pt_exchange_item* items, 
 
 pt_status pt_build_ace_from(pt_ctx* ctx, const void* W, const void* phi, int N, const pt_grid* grid,
                             pt_precision prec, pt_ace** ace, void* stream) {
-  return guarded(ctx, [&]() -> pt_status {
+  return guarded(__func__, ctx, [&]() -> pt_status {
     check_common(ctx, grid, prec);
     if (!ace) pt::fail(PT_INVALID_ARG, "ace is NULL");
     *ace = nullptr;
@@ -290,7 +293,7 @@ pt_status pt_build_ace_from(pt_ctx* ctx, const void* W, const void* phi, int N, 
 
 pt_status pt_build_ace(pt_ctx* ctx, const void* phi, const double* occ, int N, const pt_grid* grid,
                        const pt_kernel* kernel, pt_precision prec, pt_ace** ace, void* stream) {
-  return guarded(ctx, [&]() -> pt_status {
+  return guarded(__func__, ctx, [&]() -> pt_status {
     check_common(ctx, grid, prec);
     check_kernel(kernel);
     if (!ace) pt::fail(PT_INVALID_ARG, "ace is NULL");
@@ -309,7 +312,7 @@ pt_status pt_build_ace(pt_ctx* ctx, const void* phi, const double* occ, int N, c
 
 pt_status pt_overlap(pt_ctx* ctx, const void* A, int N1, const void* B, int N2, const pt_grid* grid,
                      pt_precision prec, void* C, void* stream) {
-  return guarded(ctx, [&]() -> pt_status {
+  return guarded(__func__, ctx, [&]() -> pt_status {
     check_common(ctx, grid, prec);
     check_count(N1, "N1");
     check_count(N2, "N2");
@@ -334,7 +337,7 @@ pt_status pt_overlap(pt_ctx* ctx, const void* A, int N1, const void* B, int N2, 
 
 pt_status pt_rotate(pt_ctx* ctx, const void* A, int N1, const void* B, int N2, const pt_grid* grid,
                     pt_precision prec, void* out, void* stream) {
-  return guarded(ctx, [&]() -> pt_status {
+  return guarded(__func__, ctx, [&]() -> pt_status {
     check_common(ctx, grid, prec);
     check_count(N1, "N1");
     check_count(N2, "N2");
@@ -361,7 +364,7 @@ pt_status pt_rotate(pt_ctx* ctx, const void* A, int N1, const void* B, int N2, c
 }
 
 pt_status pt_apply_ace(pt_ctx* ctx, const pt_ace* ace, const void* psi, int M, void* out, void* stream) {
-  return guarded(ctx, [&]() -> pt_status {
+  return guarded(__func__, ctx, [&]() -> pt_status {
     if (!ctx || !ace) pt::fail(PT_INVALID_ARG, "context or ACE is NULL");
     check_count(M, "M");
     pt::require_aligned(psi, "psi");
@@ -391,7 +394,7 @@ void pt_ace_destroy(pt_ace* ace) {
 pt_status pt_apply_H(pt_ctx* ctx, const void* psi, int M, void* out, const double* vloc, const pt_ace* ace,
                      double alpha, double ecut, const double* A, const pt_grid* grid, pt_precision prec,
                      void* stream) {
-  return guarded(ctx, [&]() -> pt_status {
+  return guarded(__func__, ctx, [&]() -> pt_status {
     check_common(ctx, grid, prec);
     check_count(M, "M");
     pt::require_aligned(psi, "psi");
@@ -417,7 +420,7 @@ pt_status pt_apply_H(pt_ctx* ctx, const void* psi, int M, void* out, const doubl
 
 pt_status pt_current(pt_ctx* ctx, const void* phi, const void* sigma, int N, const pt_grid* grid, pt_precision prec,
                      const double* A, double spin, double* J, void* stream) {
-  return guarded(ctx, [&]() -> pt_status {
+  return guarded(__func__, ctx, [&]() -> pt_status {
     check_common(ctx, grid, prec);
     check_count(N, "N");
     if (!phi || !sigma || !J) pt::fail(PT_INVALID_ARG, "NULL buffer");
@@ -434,7 +437,7 @@ pt_status pt_current(pt_ctx* ctx, const void* phi, const void* sigma, int N, con
 
 pt_status pt_density(pt_ctx* ctx, const void* phi, const void* sigma, int N, const pt_grid* grid, pt_precision prec,
                      double spin, double* rho, void* stream) {
-  return guarded(ctx, [&]() -> pt_status {
+  return guarded(__func__, ctx, [&]() -> pt_status {
     check_common(ctx, grid, prec);
     check_count(N, "N");
     if (!phi || !sigma || !rho) pt::fail(PT_INVALID_ARG, "NULL buffer");
@@ -459,7 +462,7 @@ pt_status pt_density(pt_ctx* ctx, const void* phi, const void* sigma, int N, con
 
 pt_status pt_hxc_potential(pt_ctx* ctx, const double* rho, const double* vloc, const pt_grid* grid, double* v,
                            double* energies, void* stream) {
-  return guarded(ctx, [&]() -> pt_status {
+  return guarded(__func__, ctx, [&]() -> pt_status {
     if (!ctx) pt::fail(PT_INVALID_ARG, "context is NULL");
     pt::validate_grid(grid);
     if (!rho || !v) pt::fail(PT_INVALID_ARG, "NULL buffer");
@@ -487,7 +490,7 @@ pt_status pt_hxc_potential(pt_ctx* ctx, const double* rho, const double* vloc, c
 }
 
 pt_status pt_diag_occupations(pt_ctx* ctx, const void* sigma, int N, void* Q, double* d, void* stream) {
-  return guarded(ctx, [&]() -> pt_status {
+  return guarded(__func__, ctx, [&]() -> pt_status {
     if (!ctx) pt::fail(PT_INVALID_ARG, "context is NULL");
     check_count(N, "N");
     if (!sigma || !Q || !d) pt::fail(PT_INVALID_ARG, "NULL buffer");
@@ -502,7 +505,7 @@ pt_status pt_diag_occupations(pt_ctx* ctx, const void* sigma, int N, void* Q, do
 pt_status pt_ptim_step(pt_ctx* ctx, void* phi, void* sigma, int N, const double* vloc, const pt_grid* grid,
                        const pt_kernel* kernel, const pt_ptim_params* params, pt_precision prec,
                        pt_ptim_stats* stats, void* stream) {
-  return guarded(ctx, [&]() -> pt_status {
+  return guarded(__func__, ctx, [&]() -> pt_status {
     check_common(ctx, grid, prec);
     check_kernel(kernel);
     if (!params) pt::fail(PT_INVALID_ARG, "params is NULL");
@@ -553,7 +556,7 @@ const char* pt_version(void) { return "ptim-gb300 0.1 (sm_103a)"; }
 long long pt_kernel_launches(void) { return pt::g_launches.load(); }
 
 pt_status pt_selftest_wait(pt_ctx* ctx, int arrive, double timeout_s, void* stream) {
-  return guarded(ctx, [&]() -> pt_status {
+  return guarded(__func__, ctx, [&]() -> pt_status {
     if (!ctx) pt::fail(PT_INVALID_ARG, "context is NULL");
     if (arrive != 0 && arrive != 1) pt::fail(PT_INVALID_ARG, "arrive must be 0 or 1");
     if (!(timeout_s > 0.0) || timeout_s > 2.0) pt::fail(PT_INVALID_ARG, "timeout_s must be in (0, 2]");

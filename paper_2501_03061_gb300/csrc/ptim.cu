@@ -15,6 +15,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "trace.h"
 
 namespace pt {
 
@@ -22,11 +23,18 @@ namespace {
 
 constexpr int kMaxDepth = 20;
 
-// CUDA events around the phases of a step, summed per phase once the step has synchronised.
+// names of the phases (the order of pt_ptim_stats.phase_ms), also the NVTX range names
+const char* const kPhaseNames[12] = {"ptim/exchange",      "ptim/ace_build", "ptim/ace_apply", "ptim/apply_H",
+                                     "ptim/subspace_gemm", "ptim/subspace_nxn", "ptim/sigma_eig", "ptim/sigma_rot",
+                                     "ptim/commutator",    "ptim/anderson",  "ptim/loewdin",   "ptim/hxc"};
+
+// CUDA events around the phases of a step, summed per phase once the step has synchronised; each
+// phase is also an NVTX range on the host thread
 class PhaseTimer {
  public:
   explicit PhaseTimer(cudaStream_t st) : st_(st) {}
   ~PhaseTimer() {
+    if (open_) trace_pop();  // a phase left by an error
     for (auto& r : recs_) {
       cudaEventDestroy(r.a);
       cudaEventDestroy(r.b);
@@ -38,8 +46,14 @@ class PhaseTimer {
     check_cuda(cudaEventCreate(&r.b), "cudaEventCreate");
     check_cuda(cudaEventRecord(r.a, st_), "cudaEventRecord");
     recs_.push_back(r);
+    trace_push(kPhaseNames[phase]);
+    open_ = true;
   }
-  void end() { check_cuda(cudaEventRecord(recs_.back().b, st_), "cudaEventRecord"); }
+  void end() {
+    check_cuda(cudaEventRecord(recs_.back().b, st_), "cudaEventRecord");
+    if (open_) trace_pop();
+    open_ = false;
+  }
   // the stream must have been synchronised
   void sum(double* ms) const {
     for (const auto& r : recs_) {
@@ -56,6 +70,7 @@ class PhaseTimer {
   };
   cudaStream_t st_;
   std::vector<Rec> recs_;
+  bool open_ = false;
 };
 enum { PH_EXCH = 0, PH_ACE_BUILD, PH_ACE_APPLY, PH_H, PH_SUB, PH_SUBNN, PH_EIG, PH_ROT, PH_COMM, PH_AND, PH_LOEW, PH_HXC };
 
