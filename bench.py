@@ -62,11 +62,13 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 form comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--mode", default="step",
-                    choices=["step", "exchange", "serve", "batched", "precision", "contractions", "library"],
+                    choices=["step", "exchange", "serve", "batched", "precision", "contractions", "library",
+                             "peaks"],
                     help="step: PT-IM steps (the benchmark); exchange: only V_x applications on the same cell "
                          "(profiler captures of the exchange kernel); serve / batched: configs 5 / 4 alone; "
                          "precision: config 3 per-result errors; contractions: Gram/rotation engines at 64^3; "
-                         "library: cuFFT exchange and cuBLAS contractions timed beside the library (comparison)")
+                         "library: cuFFT exchange and cuBLAS contractions timed beside the library (comparison); "
+                         "peaks: FP32/FP64 FMA throughput of the device (CUDA-core roofline denominators)")
     ap.add_argument("--serve-window", type=float, default=15.0, help="seconds of arrivals per serving phase")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement in step mode")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
@@ -821,6 +823,15 @@ def main():
         print(json.dumps({"mode": "contractions", "contractions": contraction_measurement()}), flush=True)
     elif args.mode == "library":
         print(json.dumps({"mode": "library", "library": library_comparison()}), flush=True)
+    elif args.mode == "peaks":
+        from paper_2501_03061_gb300 import api
+        ctx = api.Context(0)
+        try:
+            runs = [ctx.alu_peaks() for _ in range(3)]
+        finally:
+            ctx.close()
+        print(json.dumps({"mode": "peaks", "best_of_3": {k: max(r[k] for r in runs) for k in runs[0]},
+                          "runs": runs}), flush=True)
     elif args.mode == "batched":
         import torch
         torch.cuda.set_device(0)

@@ -327,6 +327,12 @@ const char* pt_version(void);
 /* Number of this library's kernel launches issued so far by the calling process. */
 long long pt_kernel_launches(void);
 
+/* FP32 and FP64 FMA throughput of the context's device in TFLOP/s (host outputs): every SM runs
+ * eight CTAs of 256 threads, each thread eight independent register FMA chains, timed with CUDA
+ * events on `stream` after a warm-up (tens of ms).  The CUDA-core roofline denominators for
+ * kernels bound by FP32 or FP64 arithmetic.  Synchronises the stream. */
+pt_status pt_alu_peaks(pt_ctx* ctx, double* fp32_tflops, double* fp64_tflops, void* stream);
+
 /* Self-test of the bounded device waits (no counterpart in the paper).  One CTA waits on a
  * shared-memory mbarrier through the same deadline-bounded wait the TMA and tensor-core
  * pipelines use.  arrive = 1: the barrier completes and the call returns PT_OK.  arrive = 0:

@@ -77,6 +77,7 @@ PROTOTYPES = {
     "pt_version": (C.c_char_p, []),
     "pt_kernel_launches": (C.c_longlong, []),
     "pt_selftest_wait": (i32, [vp, i32, C.c_double, vp]),
+    "pt_alu_peaks": (i32, [vp, C.POINTER(C.c_double), C.POINTER(C.c_double), vp]),
 }
 
 _lib = None

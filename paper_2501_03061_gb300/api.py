@@ -145,6 +145,12 @@ class Context:
             raise ValueError(f"{what} must be a contiguous {_CDTYPE[precision]} (N, nz, ny, nx) tensor on {self.device}")
         return t
 
+    def alu_peaks(self, stream=None) -> dict:
+        """FP32 and FP64 FMA throughput of the device, TFLOP/s (synchronises the stream)."""
+        f32, f64 = C.c_double(0.0), C.c_double(0.0)
+        self._check(self.lib.pt_alu_peaks(self.h, C.byref(f32), C.byref(f64), _stream(stream)), "pt_alu_peaks")
+        return {"fp32_tflops": f32.value, "fp64_tflops": f64.value}
+
     def selftest_wait(self, arrive: bool, timeout_s: float = 0.05, stream=None) -> str:
         """Bounded device-wait self-test: the status name, "PT_TIMEOUT" when nothing arrives
         (the expected outcome with arrive=False), "PT_OK" when the barrier completes."""

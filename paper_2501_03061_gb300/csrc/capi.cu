@@ -555,6 +555,15 @@ const char* pt_version(void) { return "ptim-gb300 0.1 (sm_103a)"; }
 
 long long pt_kernel_launches(void) { return pt::g_launches.load(); }
 
+pt_status pt_alu_peaks(pt_ctx* ctx, double* fp32_tflops, double* fp64_tflops, void* stream) {
+  return guarded(__func__, ctx, [&]() -> pt_status {
+    if (!ctx || !fp32_tflops || !fp64_tflops) pt::fail(PT_INVALID_ARG, "context or output is NULL");
+    set_device(ctx);
+    pt::alu_peaks(ctx, fp32_tflops, fp64_tflops, static_cast<cudaStream_t>(stream));
+    return PT_OK;
+  });
+}
+
 pt_status pt_selftest_wait(pt_ctx* ctx, int arrive, double timeout_s, void* stream) {
   return guarded(__func__, ctx, [&]() -> pt_status {
     if (!ctx) pt::fail(PT_INVALID_ARG, "context is NULL");

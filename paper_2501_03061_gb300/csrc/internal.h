@@ -135,6 +135,9 @@ void ace_from_w(pt_ctx* ctx, const void* W, const void* phi, int N, const pt_gri
 void ace_apply(pt_ctx* ctx, const void* xi, int N, const void* psi, int M, void* out, const pt_grid& g,
                pt_precision prec, cudaStream_t st);
 
+// ---- FMA throughput of the device (peaks.cu), TFLOP/s; synchronises st ----
+void alu_peaks(pt_ctx* ctx, double* fp32_tflops, double* fp64_tflops, cudaStream_t st);
+
 // ---- bounded-wait self-test (selftest.cu): PT_TIMEOUT when arrive = 0; synchronises st ----
 void wait_selftest(pt_ctx* ctx, int arrive, double timeout_s, cudaStream_t st);
 
