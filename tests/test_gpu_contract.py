@@ -4,7 +4,6 @@ usable afterwards.  Calls go straight through ctypes with raw pointers so the li
 (not the Python binding's) are what is tested."""
 import ctypes as C
 
-import numpy as np
 import pytest
 
 from paper_2501_03061_gb300 import synth

@@ -3,7 +3,6 @@
 Tolerances: FP64 form ||dV_x Psi||_F/||V_x Psi||_F <= 1e-11; FP32 form <= 1e-5 on V_x Psi and
 <= 1e-6 Ha/atom on the exchange energy, both against FP64.
 """
-import math
 
 import numpy as np
 import pytest
