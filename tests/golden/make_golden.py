@@ -174,7 +174,35 @@ def write_ptim(path):
     out.close()
 
 
+FIELD_A = (0.3, -0.2, 0.1)  # bohr^-1, a uniform vector potential
+
+
+def write_field(path):
+    w, sig = ptim_case()
+    g = O.grid_of(w.cell)
+    K = O.exchange_kernel(g, 1, synth.SCREENED_MU)
+    A = np.array(FIELD_A)
+    hdr = f"""
+    Velocity-gauge field (Eq. 1's V_ext(t) as a uniform vector potential A = {FIELD_A} bohr^-1) on the
+    step fixture's input: current = (spin/Omega) Re Tr[P (-i grad + A)] with spin 2 (current0 before the
+    step, current1 after), and one PT-IM-ACE step with A at the midpoint time (Sec. II-A), dt 0.5 au,
+    tol 1e-12: sigma1, proj[i, j] = <phi_n,i|phi_{{n+1}},j>, energy0 / energy1 with A in the kinetic term.
+    """
+    out = Writer(path, hdr)
+    out.array("current0", O.current(w.phi, sig, g, A))
+    phi1, sig1, st = O.ptim_step(w.phi, sig, w.vloc, g, K, O.PtimParams(tol=1e-12, ecut=6.0, A=FIELD_A))
+    if not st.converged:
+        raise RuntimeError("oracle PT-IM step did not converge")
+    out.array("current1", O.current(phi1, sig1, g, A))
+    out.array("sigma1", sig1)
+    out.array("proj", O.overlap(w.phi, phi1, g.dV))
+    out.scalar("energy0", O.total_energy(w.phi, sig, w.vloc, g, K, 6.0, A=A))
+    out.scalar("energy1", O.total_energy(phi1, sig1, w.vloc, g, K, 6.0, A=A))
+    out.close()
+
+
 def main():
+    write_field(os.path.join(HERE, "field_12cubed_N6.txt"))
     write_exchange(os.path.join(HERE, "exchange_12cubed_N6.txt"))
     write_ace(os.path.join(HERE, "ace_12cubed_N6.txt"))
     write_hxc(os.path.join(HERE, "hxc_12cubed_N6.txt"))

@@ -7,7 +7,9 @@ oracle) against the oracle recomputed through a different route where it has one
   compressed operator itself (<xi|Phi> = -L^*) with W from the diagonalised exchange;
 * density: rho = 2 sum_i d_i |phit_i|^2 from the eigenpairs of sigma instead of the double sum;
 * PT-IM step: the fixtures hold the PT-IM-ACE fixed point; here the step runs with the exchange
-  applied exactly in every inner iteration (same fixed point, different iteration).
+  applied exactly in every inner iteration (same fixed point, different iteration);
+* field: the stored current against the field derivative of the total energy, and the stored step
+  with a vector potential against the exact-exchange iteration.
 
 A failing fixture means the oracle's arithmetic changed; the generating script is rerun only with
 a commit that names the passage of the paper justifying the change.
@@ -77,7 +79,7 @@ def exchange_input():
 
 def test_every_fixture_is_cited():
     names = sorted(n for n in os.listdir(GOLDEN) if n.endswith(".txt"))
-    assert names == ["ace_12cubed_N6.txt", "exchange_12cubed_N6.txt", "hxc_12cubed_N6.txt",
+    assert names == ["ace_12cubed_N6.txt", "exchange_12cubed_N6.txt", "field_12cubed_N6.txt", "hxc_12cubed_N6.txt",
                      "ptim_step_12cubed_N6.txt"]
     for n in names:
         data, header = load(n)
@@ -150,3 +152,31 @@ def test_ptim_fixture_by_exact_exchange_iteration(suffix, hxc):
     assert np.trace(s1).real == pytest.approx(np.trace(sig).real, rel=1e-11)
     sv = np.linalg.svd(ref["proj" + suffix], compute_uv=False)
     assert sv.max() <= 1 + 1e-12 and sv.min() > 0.5
+
+
+def test_field_fixture_by_energy_derivative_and_exact_exchange_iteration():
+    """The stored current against Omega J_a = dE/dA_a by central differences of the total energy, and
+    the stored field step against the step with the exchange applied exactly in every iteration."""
+    w = synth.small_cell(23, 12, 8.0, 6, kT=0.05, ecut=6.0)
+    sig = mixed_sigma(w.occ)
+    g = O.grid_of(w.cell)
+    K = O.exchange_kernel(g, 1, synth.SCREENED_MU)
+    A = np.array([0.3, -0.2, 0.1])
+    ref, header = load("field_12cubed_N6.txt")
+    assert any("0.3, -0.2, 0.1" in h for h in header)
+    h = 1e-4
+    dE = []
+    for a in range(3):
+        e = np.zeros(3)
+        e[a] = h
+        dE.append((O.total_energy(w.phi, sig, w.vloc, g, K, 6.0, A=A + e)
+                   - O.total_energy(w.phi, sig, w.vloc, g, K, 6.0, A=A - e)) / (2 * h) / g.volume)
+    close(np.array(dE), ref["current0"], 1e-6)
+    phi1, sig1, st = O.ptim_step(w.phi, sig, w.vloc, g, K,
+                                 O.PtimParams(tol=1e-12, ecut=6.0, A=tuple(A), use_ace=False))
+    assert st.converged
+    close(sig1, ref["sigma1"], 1e-9)
+    close(O.overlap(w.phi, phi1, g.dV), ref["proj"], 1e-9)
+    close(O.current(phi1, sig1, g, A), ref["current1"], 1e-8)
+    assert O.total_energy(w.phi, sig, w.vloc, g, K, 6.0, A=A) == pytest.approx(ref["energy0"], rel=1e-12)
+    assert O.total_energy(phi1, sig1, w.vloc, g, K, 6.0, A=A) == pytest.approx(ref["energy1"], rel=1e-9)
