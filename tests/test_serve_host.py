@@ -102,3 +102,34 @@ def test_footprint_structure():
     f = api.ptim_footprint(320, c64, "fp32", 20)
     assert f >= (12 + 40) * 320 * 64 ** 3 * 8 + 4 * 16 * 16 * 64 ** 3 * 8
     assert f < 60 * 2 ** 30
+
+
+def test_a_failing_request_is_recorded_and_frees_its_worker():
+    """_run: an exception inside a request becomes the request's error; the worker is released with
+    its workspace size re-read, the request is completed and its future resolved (no device: the
+    worker's stream is None and the context is a stub)."""
+    import threading
+    from concurrent.futures import Future
+
+    from paper_2501_03061_gb300.serve import Request
+
+    s = server_stub(100, [])
+    s.cv = threading.Condition()
+    s.completed = []
+    w = types.SimpleNamespace(held=0, reserved=40, busy=True, stream=None,
+                              ctx=types.SimpleNamespace(workspace_bytes=lambda: 17))
+    s.workers = [w]
+
+    def boom(worker, req):
+        raise ValueError("PT_INVALID_ARG: phi holds 1536 elements where the call addresses 1152")
+
+    s._execute = boom
+    req = Request(phi=np.zeros((1, 2, 2, 2), np.complex64), sigma=None, occ=None, vloc=None,
+                  cell=synth.cubic(8, 5.0), kernel={})
+    fut = Future()
+    s._run(w, req, fut)
+    assert fut.done() and fut.result() is req
+    assert "PT_INVALID_ARG" in req.error and req.result is None
+    assert req.t_end >= req.t_start > 0
+    assert (w.busy, w.reserved, w.held) == (False, 0, 17)
+    assert s.completed == [req]
