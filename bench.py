@@ -40,6 +40,11 @@ WORKLOAD = "ptim_ace_step_64^3_N320_128site_L20.5"
 MODEL_OUTER, MODEL_INNER = 5, 65
 
 
+def _finite(x):
+    """A float for the JSON line, or None where it is absent or not finite (strict JSON has no NaN)."""
+    return float(x) if x is not None and math.isfinite(float(x)) else None
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -751,8 +756,10 @@ def run_gb300(args):
             "exchange": {"pair_ffts": pair_ffts, "calls": ex_calls, "ms": ex_ms,
                          "pair_ffts_per_s": pair_ffts / (ex_ms / 1e3) if ex_ms else None,
                          "share_of_step": ex_ms / ms if ms else None},
-            "iterations": [{"outer": s["outer"], "inner": s["inner"], "residual": s["residual"],
-                            "converged": s["converged"], "eig_sweeps": s["eig_sweeps"]} for s in stats],
+            "iterations": [{"outer": s["outer"], "inner": s["inner"], "residual": _finite(s["residual"]),
+                            "converged": s["converged"], "eig_sweeps": s["eig_sweeps"],
+                            "total_energy_in": _finite(s.get("total_energy")),
+                            "orth_error": _finite(s.get("orth_error"))} for s in stats],
             "phases_ms_per_step": {k: sum(s["phase_ms"][k] for s in stats) / len(stats)
                                    for k in stats[0]["phase_ms"]},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
