@@ -205,6 +205,29 @@ def exchange_energy(phi: np.ndarray, sigma: np.ndarray, K: np.ndarray, dV: float
     return float(spin * 0.5 * alpha * np.real(np.sum(d * np.diag(overlap(phit, vx, dV)))))
 
 
+def exchange_energy_pairs(phit: np.ndarray, d: np.ndarray, K: np.ndarray, dV: float, rows=None) -> float:
+    """Sum over pairs of E_x / (spin alpha/2) = sum_i d_i <phit_i|V_x phit_i>, by Parseval.
+
+    With rho_ij = conj(phit_i) phit_j, <phit_i|V_x phit_i> = -sum_j d_j dV sum_r conj(rho_ji) v_ji, and
+    sum_r conj(rho) ifftn(K fftn(rho)) = (1/Ng) sum_G K(G) |fftn(rho)(G)|^2, so
+        sum_i d_i <phit_i|V_x phit_i> = -(dV/Ng) sum_{i,j} d_i d_j sum_G K(G) |fftn(rho_ij)(G)|^2,
+    one forward FFT per unordered pair (|rho_ji^| and |rho_ij^| sum the same K-weighted squares, K
+    being even).  `rows` restricts i to a subset (the pairs i <= j with i in rows), so that callers
+    can split the sum; the full sum is rows = all i.  Same value as exchange_energy / (spin alpha/2)
+    for sigma = diag(d) in the basis phit (Sec. IV-A1, Eq. vxdiag; the energy of Sec. II-B).
+    """
+    N = phit.shape[0]
+    ng = int(np.prod(phit.shape[1:]))
+    rows = range(N) if rows is None else rows
+    s = 0.0
+    for i in rows:
+        for j in range(i, N):
+            rh = np.fft.fftn(np.conj(phit[i]) * phit[j])
+            w = 1.0 if i == j else 2.0
+            s += w * d[i] * d[j] * float(np.sum(K * (rh.real ** 2 + rh.imag ** 2)))
+    return -dV / ng * s
+
+
 # ----------------------------------------------------------------------------------------
 # Adaptively compressed exchange (Sec. IV-A2, Eq. vx_ace; construction of Lin 2016)
 # ----------------------------------------------------------------------------------------

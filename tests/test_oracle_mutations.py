@@ -81,6 +81,12 @@ CASES = [
      [P.test_ptim_quadratic_invariants, P.test_ptim_free_electron_cayley_closed_form]),
     ("exchange energy without the 1/2", "exchange_energy", "spin * 0.5 * alpha", "spin * alpha", 1,
      [functools.partial(pw, 1)]),
+    ("pair energy counts off-diagonal pairs once", "exchange_energy_pairs", "1.0 if i == j else 2.0", "1.0", 1,
+     [functools.partial(P.test_exchange_energy_by_pairs_plane_waves_closed_form, 1)]),
+    ("pair energy weights one occupation twice", "exchange_energy_pairs", "d[i] * d[j]", "d[i] * d[i]", 1,
+     [P.test_exchange_energy_by_pairs_matches_the_exchange_route]),
+    ("pair energy without the 1/Ng of Parseval", "exchange_energy_pairs", "-dV / ng * s", "-dV * s", 1,
+     [functools.partial(P.test_exchange_energy_by_pairs_plane_waves_closed_form, 0)]),
     # ACE
     ("ACE factor without the conjugate of L^-1", "build_ace", "(Linv.conj() @ Wm)", "(Linv @ Wm)", 1,
      [P.test_ace_reproduces_exchange_on_its_orbitals]),

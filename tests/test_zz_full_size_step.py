@@ -83,16 +83,28 @@ def test_full_size_fp32_step_satisfies_its_fixed_point_and_invariants():
     assert st["converged"]
     del phi, sigma
     # invariants of the implicit midpoint step (quadratic invariants, exact at the fixed point):
-    # sigma Hermitian with its trace and tr sigma^2; an orthonormal orbital block
-    assert np.abs(sig1 - sig1.conj().T).max() <= 1e-12
-    assert abs(np.trace(sig1) - np.trace(sig_n)) <= 1e-4 * abs(np.trace(sig_n))
-    assert abs(np.trace(sig1 @ sig1) - np.trace(sig_n @ sig_n)) <= 1e-4 * abs(np.trace(sig_n @ sig_n))
+    # sigma Hermitian with its trace and tr sigma^2; an orthonormal orbital block.  Bounds: the
+    # step stops at a relative residual of tol = 1e-6 on x = (Phi, sigma), which bounds the drift
+    # of the traces to a few tol; the orbitals are stored in FP32 (unit roundoff 6e-8), whose
+    # rounding after the final orthonormalisation leaves max |Phi^*Phi - I| near 1e-6.
+    tr_drift = abs(np.trace(sig1) - np.trace(sig_n)) / abs(np.trace(sig_n))
+    tr2_drift = abs(np.trace(sig1 @ sig1) - np.trace(sig_n @ sig_n)) / abs(np.trace(sig_n @ sig_n))
     G = O.overlap(phi1, phi1, g.dV)
-    assert np.abs(G - np.eye(N)).max() <= 5e-5
-    # the step moved the state (a no-op would pass the invariants)
-    assert np.abs(sig1 - sig_n).max() > 1e-4
+    orth = float(np.abs(G - np.eye(N)).max())
     # the orbital equation of the fixed point for sampled orbitals, through the oracle
     K = O.exchange_kernel(g, 1, synth.SCREENED_MU)
     defect = fixed_point_defect(phi_n.astype(np.complex128), sig_n, phi1, sig1, w.vloc, g, K, 0.5, 10.0, 0.25,
                                 (0, 177, 319))
-    assert defect <= 5e-4, defect
+    print(f"full-size FP32 step: outer {st['outer']} inner {st['inner']} residual {st['residual']:.3e}; "
+          f"tr sigma drift {tr_drift:.3e}, tr sigma^2 drift {tr2_drift:.3e}, max|Phi*Phi - I| {orth:.3e}, "
+          f"fixed-point defect {defect:.3e}")
+    assert np.abs(sig1 - sig1.conj().T).max() <= 1e-12
+    assert tr_drift <= 1e-5, tr_drift
+    assert tr2_drift <= 1e-5, tr2_drift
+    assert orth <= 1e-5, orth
+    # the step moved the state (a no-op would pass the invariants)
+    assert np.abs(sig1 - sig_n).max() > 1e-4
+    # the defect of the fixed-point equation: the inner residual (tol), the ACE operator's distance
+    # from the exact V_x at the final midpoint (the anchor moved less than tol) and the final
+    # orthonormalisation (~1e-6) each enter at the 1e-6 level, FP32 rounding of the orbitals at 1e-7
+    assert defect <= 1e-5, defect
