@@ -142,10 +142,14 @@ pt_status pt_apply_exchange(pt_ctx* ctx, const void* src, const double* occ, int
  * in static device arrays of this library (32 MiB pair scratch, a 64^3 kernel table, small
  * schedule tables) that every GPU loading the library holds until the process exits.  Limits:
  * N, M <= 1024 and grids of at most 64^3 points (the regular grid rules apply); larger requests
- * return PT_INVALID_ARG.  The first call on a device (with that device current) looks up the
- * device addresses of those arrays; make it before any stream capture.  All calls share the
- * arrays: calls that overlap on the GPU (other streams or host threads) race.  Uses the generic
- * (non-TMA) exchange kernels.  Other status codes as pt_apply_exchange. */
+ * return PT_INVALID_ARG.  The arrays (about 34 MiB) become resident when the CUDA runtime loads
+ * this library's device code on a GPU, which under lazy module loading can happen inside the
+ * first call: a caller that hands all free device memory to its own pool should make one call
+ * before doing so.  The first call on a device (with that device current) also looks up the
+ * device addresses of those arrays; make that first call before any stream capture begins.  All
+ * calls share the arrays and the last call's contents stay in them: calls that overlap on the
+ * GPU (other streams or host threads) race.  Uses the generic (non-TMA) exchange kernels.  Other
+ * status codes as pt_apply_exchange. */
 pt_status pt_apply_exchange_noalloc(const void* src, const double* occ, int N, const void* tgt, int M, void* out,
                                     const pt_grid* grid, const pt_kernel* kernel, pt_precision prec, void* stream);
 
@@ -309,7 +313,10 @@ typedef struct {
 /* One PT-IM(-ACE) step from (phi, sigma) = (Phi_n, sigma_n) to (Phi_{n+1}, sigma_{n+1}),
  * both updated in place.  phi: Ng x N (precision prec); sigma: N x N complex128;
  * vloc: Ng doubles.  Returns PT_NOT_CONVERGED (with the last iterate stored) when the
- * caps are reached.  Synchronises the stream once per inner iteration (residual test). */
+ * caps are reached.  On any other error status (a non-finite residual, a failed factorisation,
+ * an expired device wait) phi and sigma are restored to their input values before the call
+ * returns, unless the CUDA context itself has failed (PT_CUDA), after which their contents are
+ * unspecified.  Synchronises the stream once per inner iteration (residual test). */
 pt_status pt_ptim_step(pt_ctx* ctx, void* phi, void* sigma, int N, const double* vloc,
                        const pt_grid* grid, const pt_kernel* kernel, const pt_ptim_params* params,
                        pt_precision prec, pt_ptim_stats* stats, void* stream);

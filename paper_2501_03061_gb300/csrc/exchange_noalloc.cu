@@ -12,6 +12,9 @@
 //   pair-field scratch  NOALLOC_SCRATCH_BYTES (32 MiB)
 //   K(G)/Ng table       64^3 doubles (2 MiB)
 //   twiddles, one batch's pair/target/contribution lists (a few tens of KiB)
+// The arrays become resident when the CUDA runtime loads this library's device code on a GPU;
+// under lazy module loading that can be inside the first call, so a caller that gives all free
+// device memory to its own pool makes one call first.
 // In host code the names of these arrays are host-side stand-ins, not device addresses, so the
 // first call on each device (with that device current) fetches their device addresses with
 // cudaGetSymbolAddress and keeps them; make that first call before any stream capture.

@@ -240,6 +240,21 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
 
   PT_CUDA_CHECK(cudaMemcpyAsync(phin, phi, fb, cudaMemcpyDeviceToDevice, st));
   PT_CUDA_CHECK(cudaMemcpyAsync(sign, sig, mb, cudaMemcpyDeviceToDevice, st));
+  // the iteration updates (phi, sig) in place: a step that ends in an error (not PT_NOT_CONVERGED,
+  // which returns normally with its last iterate) copies the input state back from (phin, sign)
+  struct RestoreGuard {
+    void *phi, *sig;
+    const void *phin, *sign;
+    size_t fb, mb;
+    cudaStream_t st;
+    bool armed;
+    ~RestoreGuard() {
+      if (!armed) return;
+      cudaMemcpyAsync(phi, phin, fb, cudaMemcpyDeviceToDevice, st);
+      cudaMemcpyAsync(sig, sign, mb, cudaMemcpyDeviceToDevice, st);
+      cudaStreamSynchronize(st);
+    }
+  } restore{phi, sig, phin, sign, fb, mb, st, true};
   gram<T>(ctx, phin, phin, N, N, S.ng, S.dV, Sn, st);
 
   pt_ptim_stats stv;
@@ -532,13 +547,20 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
     if (Z != A) PT_CUDA_CHECK(cudaMemcpyAsync(A, Z, mb, cudaMemcpyDeviceToDevice, st));
     if (Y != Lc) PT_CUDA_CHECK(cudaMemcpyAsync(Lc, Y, mb, cudaMemcpyDeviceToDevice, st));
   } else {
+    // Q receives the eigenvectors of S, not of sigma: ptim_q_n stays 0 so that the next step's
+    // sigma eigensolve starts cold instead of from this unrelated basis
     ctx->ptim_q_n = 0;
     heev(ctx, Sm, N, Q, d, st);
-    ctx->ptim_q_n = N;
     scale_cols_pow(Q, d, N, -0.5, T1, info, st);
     zgemm('N', 'C', N, N, N, c128{1, 0}, T1, N, Q, N, c128{0, 0}, A, N, st);   // S^{-1/2}
     scale_cols_pow(Q, d, N, 0.5, T1, info, st);
     zgemm('N', 'C', N, N, N, c128{1, 0}, T1, N, Q, N, c128{0, 0}, Lc, N, st);  // S^{1/2}
+    // a non-positive eigenvalue of S is reported before phi and sigma are overwritten, so a step
+    // that fails here leaves the caller's (Phi_n, sigma_n) as they were
+    int s_info = 0;
+    PT_CUDA_CHECK(cudaMemcpyAsync(&s_info, info, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PT_CUDA_CHECK(cudaStreamSynchronize(st));
+    if (s_info) fail(PT_NOT_PD, "PT-IM: final overlap matrix is not positive definite");
   }
   rotate<T>(ctx, phi, A, N, N, N, S.ng, c128{1, 0}, nullptr, 0, rphi_buf[0], st);
   PT_CUDA_CHECK(cudaMemcpyAsync(phi, rphi_buf[0], fb, cudaMemcpyDeviceToDevice, st));
@@ -561,6 +583,7 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
   stv.converged = converged ? 1 : 0;
   if (stats) *stats = stv;
   warm_guard.done = true;
+  restore.armed = false;
   return converged ? PT_OK : PT_NOT_CONVERGED;
 }
 

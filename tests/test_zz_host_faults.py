@@ -1,8 +1,9 @@
 """Faults injected on the host, none of which faults, traps or hangs the GPU: an impossible
 tolerance (PT_NOT_CONVERGED, with the statistics and the last iterate), and a non-finite entry in
 the orbitals or in the occupation matrix (an error status, PT_NONFINITE or PT_NOT_PD from the first
-check or factorisation the NaN reaches).  After each, the same context takes a valid step that
-matches the oracle: a failed step leaves nothing behind that the next one starts from."""
+check or factorisation the NaN reaches; the caller's orbitals and occupation matrix come back
+unchanged).  After each, the same context takes a valid step that matches the oracle: a failed step
+leaves nothing behind that the next one starts from."""
 import numpy as np
 import pytest
 
@@ -86,4 +87,7 @@ def test_non_finite_input_is_an_error_and_the_context_recovers(ctx, ref, where, 
         ctx.ptim_step(phi, sigma, torch.from_numpy(w.vloc).cuda(), cell=w.cell, kernel=w.kernel,
                       precision=precision, dt=0.5, ecut=6.0, tol=1e-10)
     assert ei.value.status in (L.PT_NONFINITE, L.PT_NOT_PD), str(ei.value)
+    # the failed step hands the caller's input back unchanged (NaN entries compared as NaN)
+    np.testing.assert_array_equal(phi.cpu().numpy(), ph)
+    np.testing.assert_array_equal(sigma.cpu().numpy(), sig)
     valid_step(ctx, ref, precision)

@@ -4,7 +4,9 @@ pt_apply_exchange_noalloc serves callers that cannot allocate device memory whil
 host application whose pool allocator owns all device memory, or a loop that cannot take the
 device synchronisation of cudaMalloc).  It keeps its scratch in static device arrays, so it must
 give the same V_x tgt as pt_apply_exchange — on every call, including a second call that finds
-the previous call's data still in those arrays.  This file is collected last on purpose.
+the previous call's data still in those arrays — and it must not allocate: after warm-up calls
+(which also let lazy module loading bring in the kernels), further calls leave the device's free
+memory and torch's allocated bytes unchanged.  This file is collected last on purpose.
 """
 import ctypes as C
 
@@ -37,7 +39,12 @@ CASES = [
     (24, 10.0, 9, 5, "fp32", 1e-6),
     (64, 20.5, 6, None, "fp32", 1e-6),   # several batches of the 32 MiB scratch
     (30, 9.6, 7, 4, "fp64", 1e-12),
+    ((24, 30, 20), (7.5, 9.4, 6.3), 6, None, "fp32", 1e-6),  # non-cubic: table key and twiddle layout
 ]
+
+
+def _cell(n, L):
+    return synth.cubic(n, L) if isinstance(n, int) else synth.Cell(n, L)
 
 
 @pytest.mark.parametrize("n,L,N,M,precision,tol", CASES)
@@ -49,8 +56,8 @@ def test_noalloc_matches_regular_exchange_twice(n, L, N, M, precision, tol):
     lib = _lib.load()
     ctx = api.Context(0)
     try:
-        rng = np.random.default_rng(n * 100 + N)
-        cell = synth.cubic(n, L)
+        rng = np.random.default_rng((n if isinstance(n, int) else sum(n)) * 100 + N)
+        cell = _cell(n, L)
         dt = np.complex128 if precision == "fp64" else np.complex64
         kernel = {"type": 1, "mu": synth.SCREENED_MU}
         for call in range(2):  # the second call reuses the static arrays the first one filled
@@ -82,3 +89,37 @@ def test_noalloc_rejects_oversize_requests():
                                        C.c_void_p(out.data_ptr()), C.byref(_grid(cell)), C.byref(_kernel(None)), 1,
                                        None)
     assert st == _lib.PT_INVALID_ARG
+
+
+def test_noalloc_calls_allocate_nothing():
+    """Two warm-up calls (a 64^3 symmetric FP32 request and a 24x30x20 FP64 request with separate
+    targets), then the same two requests with other data: the device's free memory and torch's
+    allocated bytes are the same before and after the second pair of calls."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2501_03061_gb300 import _lib
+
+    lib = _lib.load()
+    rng = np.random.default_rng(77)
+    kernel = {"type": 1, "mu": synth.SCREENED_MU}
+    reqs = []
+    for cell, N, M, precision in ((synth.cubic(64, 20.5), 5, None, "fp32"),
+                                  (synth.Cell((24, 30, 20), (7.5, 9.4, 6.3)), 4, 3, "fp64")):
+        dt = np.complex128 if precision == "fp64" else np.complex64
+        for _ in range(2):
+            src = torch.from_numpy(synth.random_orbitals(rng, cell, N, ecut=5.0).astype(dt)).cuda()
+            tgt = None if M is None else torch.from_numpy(synth.random_orbitals(rng, cell, M, ecut=5.0).astype(dt)).cuda()
+            occ = torch.from_numpy(rng.uniform(0.1, 1.0, N)).cuda()
+            out = torch.empty_like(src if tgt is None else tgt)
+            reqs.append((src, occ, tgt, out, cell, precision))
+    for r in reqs[0::2]:  # warm-up: one call of each kind
+        _noalloc(lib, r[0], r[1], r[2], r[3], r[4], kernel, r[5])
+    torch.cuda.synchronize()
+    free0, alloc0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+    for r in reqs[1::2]:
+        _noalloc(lib, r[0], r[1], r[2], r[3], r[4], kernel, r[5])
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_allocated() == alloc0
+    for r in reqs:
+        assert bool(torch.isfinite(torch.view_as_real(r[3])).all())
