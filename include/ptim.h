@@ -106,6 +106,13 @@ pt_status pt_trim(pt_ctx* ctx);
  *                    iteration); the step still converges only when the midpoint has settled to
  *                    tol and the last inner loop met tol.  Defaults 0.1 and 1e-2; kappa = 0 uses
  *                    tol throughout.
+ *   "ptim_precond"   1: the inner Anderson iteration of pt_ptim_step works on the kinetically
+ *                    preconditioned map x -> x + M (T(x) - x), M acting on each orbital column j of
+ *                    the residual as 1/(1 + i dt/2 (|G + A|^2/2 - Re <phi_j|H phi_j>)) in Fourier space
+ *                    inside the basis sphere (identity outside, sigma untouched).  M is invertible, so
+ *                    the fixed point (the step's result) is unchanged; the iteration needs fewer
+ *                    steps (64^3 grid, N = 320: 39 inner iterations per step against 46-47).
+ *                    Default 1; 0: plain Anderson on T(x) - x.
  *   "scratch_bytes"  bytes of pair/orbital fields one FFT batch may hold (default 512 MiB: the
  *                    cost per pair falls with the pair tile even past L2 residency, 4-10% from
  *                    48 MiB to 512 MiB; smaller values give more, smaller batches).

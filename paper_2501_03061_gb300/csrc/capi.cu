@@ -176,8 +176,21 @@ pt_status pt_set_option(pt_ctx* ctx, const char* key, double value) {
       (std::string(key) == "ptim_inner_kappa" ? ctx->ptim_inner_kappa : ctx->ptim_inner_cap) = value;
       return PT_OK;
     }
+    if (std::string(key) == "ptim_precond") {
+      ctx->ptim_precond = value != 0.0 ? 1 : 0;
+      return PT_OK;
+    }
     if (std::string(key) == "exchange64_engine") {
-      ctx->exchange64_engine = value != 0.0 ? 1 : 0;
+      if (!(value == 0.0 || value == 1.0 || value == 2.0)) pt::fail(PT_INVALID_ARG, "exchange64_engine is 0, 1 or 2");
+      ctx->exchange64_engine = int(value);
+      return PT_OK;
+    }
+    if (std::string(key) == "exchange64p_tile" || std::string(key) == "exchange64p_ring" ||
+        std::string(key) == "exchange64p_lag") {
+      if (!(value >= 1.0 && value <= 1024.0)) pt::fail(PT_INVALID_ARG, std::string(key) + " must be in [1, 1024]");
+      (std::string(key) == "exchange64p_tile" ? ctx->x64p_tile
+                                              : (std::string(key) == "exchange64p_ring" ? ctx->x64p_ring
+                                                                                        : ctx->x64p_lag)) = int(value);
       return PT_OK;
     }
     if (std::string(key) == "tc_period") {

@@ -132,8 +132,14 @@ struct pt_ctx {
   bool bf16_requested = false;  // per call: the BF16 form, whose contractions are not built
   double ptim_inner_kappa = 0.1;  // option: inner tolerance = max(tol, min(cap, kappa * midpoint move))
   double ptim_inner_cap = 1e-2;   // option: loosest inner tolerance (also that of the first outer iteration)
+  int ptim_precond = 1;        // option: Anderson on the kinetically preconditioned inner map when 1
   int ptim_q_n = 0;            // the "ptim_Q" buffer holds a complete unitary ptim_q_n x ptim_q_n basis
-  int exchange64_engine = 0;  // option: 64^3 exchange on the TMA pipeline (0) or the compile-time tile kernels (1)
+  // option: 64^3 FP32 exchange engine: 0 the launch-pipelined TMA kernel, 1 the compile-time tile
+  // kernels, 2 one persistent cooperative launch per application (exchange64_persist.cu)
+  int exchange64_engine = 0;
+  int x64p_tile = 4;   // option: pair-tile side of the persistent engine's schedule
+  int x64p_ring = 24;  // option: pair-field ring slots of the persistent engine (raised to tile pairs + 3 lag + 1)
+  int x64p_lag = 2;    // option: waves between the A, B, C and D stages of a pair in the persistent engine
   int tc_period = 2;   // option: K stages (32 floats each) accumulated in TMEM between readouts
   bool tc_err_clean = false;  // the tensor-core Gram's device error word exists and has been zeroed
   // batched exchange (batched.cu)

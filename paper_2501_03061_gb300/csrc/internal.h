@@ -116,6 +116,11 @@ void anderson_update(pt_ctx* ctx, cx<T>* x, const cx<T>* r, const cx<T>* const* 
 // A: vector potential of the velocity-gauge field (host double[3]; null = no field)
 void apply_h(pt_ctx* ctx, const void* psi, int M, void* out, const double* vloc, const void* X, double alpha,
              double ecut, const pt_grid& g, pt_precision prec, cudaStream_t st, const double* A = nullptr);
+// in place on the orbital residual r (Ng x N): r_j <- IFFT[m_j(G) FFT(r_j)] with
+// m_j = 1/(1 + i dt/2 (|G + A|^2/2 - Re A_jj)) inside the sphere |G|^2/2 <= ecut, 1 outside;
+// A: N x N device matrix <Phi_h|H Phi_h>; Avec: vector potential (host double[3] or null)
+void precondition_residual(pt_ctx* ctx, void* r, int N, const c128* A, double dt, double ecut, const pt_grid& g,
+                           pt_precision prec, cudaStream_t st, const double* Avec);
 // J_a = spin/Omega Re sum_ij sigma_ij <phi_j|(-i d_a + A_a) phi_i> (host J[3]; synchronises st)
 void current(pt_ctx* ctx, const void* phi, const c128* sigma, int N, const pt_grid& g, pt_precision prec,
              const double* A, double spin, double* J, cudaStream_t st);

@@ -469,6 +469,8 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
         inner_conv = res < P.tol;
         break;
       }
+      // kinetic preconditioning: Anderson then solves x = x + M (T(x) - x), same fixed point
+      if (ctx->ptim_precond) precondition_residual(ctx, rphi, N, A, P.dt, P.ecut, g, prec, st, P.A);
       // ---- Anderson (type II, real coefficients) ----
       int m = 0;
       if (inner > 0) {
