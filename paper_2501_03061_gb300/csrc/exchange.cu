@@ -214,6 +214,14 @@ long long exchange_t(pt_ctx* ctx, const cx<T>* src, const double* occ, int N, co
   }
   const FftTables& ft = fft_tables(ctx, g, prec);
   const T* ktab = static_cast<const T*>(kernel_table(ctx, g, k, prec));
+  if constexpr (sizeof(T) == 4) {
+    if (exchange64_applies(g) && ctx->exchange64_engine == 2) {
+      const long long np = exchange64_persist(ctx, src, occ, N, tgt, M, sym, out, ktab,
+                                              static_cast<const cx<T>*>(ft.tw), st);
+      if (!ctx->defer_checks) exchange_check(ctx, st);
+      return np;
+    }
+  }
   const size_t ng = ng_of(g);
   const size_t field = ng * sizeof(cx<T>);
   // Pair batch: as many pair fields as fit a budget that keeps them L2-resident (the 64^3 TMA
