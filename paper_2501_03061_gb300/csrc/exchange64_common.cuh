@@ -30,6 +30,14 @@ __device__ __forceinline__ uint32_t sw_off(int x, int r) {
          uint32_t((xx & 1) << 3);
 }
 
+// element (row, col) of the 64 x 64 plane-transpose buffer: col XOR-swizzled by
+// ((row & 7) << 1) ^ ((row & 1) << 3), a bijection of [0, 4096) under which both access patterns of
+// the plane passes — column writes (lane t of group g at row t + 8k, column g) and row reads
+// (row g, column t + 8q) — reach 16 distinct 8-byte bank slots in every half-warp
+__device__ __forceinline__ int pidx(int row, int col) {
+  return row * G + (col ^ (((row & 7) << 1) ^ ((row & 1) << 3)));
+}
+
 // 64-point transform of the line held by an 8-lane group (lane t holds x[t + 8a]): radix 8,
 // twiddles w^{tk} derived in registers, a swizzled group transpose through gs (element e at
 // e ^ (8 (g & 1))), radix 8; on return lane t holds X[t + 8k]

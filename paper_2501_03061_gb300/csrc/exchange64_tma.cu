@@ -99,11 +99,11 @@ __global__ void __launch_bounds__(THREADS, 2)
     c64* gs = reinterpret_cast<c64*>(sm + OFF_A) + grp * 64;
     fft64_tma(v, t, gs, gpar, tw, false);  // along y: lane t holds ky = t + 8k
 #pragma unroll
-    for (int k = 0; k < 8; ++k) P[(t + 8 * k) * PITCH + x] = v[k];
+    for (int k = 0; k < 8; ++k) P[pidx(t + 8 * k, x)] = v[k];
     __syncthreads();
     const int ky = grp;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] = P[ky * PITCH + t + 8 * q];
+    for (int q = 0; q < 8; ++q) v[q] = P[pidx(ky, t + 8 * q)];
     fft64_tma(v, t, gs, gpar, tw, false);  // along x: lane t holds kx = t + 8k
     c64* o = scratch + (size_t(L.slotA) * L.max_pairs + p) * ng + size_t(z) * G * G + ky * G;
 #pragma unroll
@@ -193,11 +193,11 @@ __global__ void __launch_bounds__(THREADS, 2)
       __syncthreads();
       fft64_tma(v, t, gs, gpar, tw, true);  // inverse along y: lane t holds y = t + 8k
 #pragma unroll
-      for (int k = 0; k < 8; ++k) P[(t + 8 * k) * PITCH + kx] = v[k];
+      for (int k = 0; k < 8; ++k) P[pidx(t + 8 * k, kx)] = v[k];
       __syncthreads();
       const int y = grp;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) v[q] = P[y * PITCH + t + 8 * q];
+      for (int q = 0; q < 8; ++q) v[q] = P[pidx(y, t + 8 * q)];
       fft64_tma(v, t, gs, gpar, tw, true);  // inverse along x: lane t holds x = t + 8k
       c64* o = scratch + size_t(orb) * ng + size_t(z) * G * G + y * G;
 #pragma unroll
