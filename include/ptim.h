@@ -141,6 +141,21 @@ pt_status pt_apply_exchange(pt_ctx* ctx, const void* src, const double* occ, int
                             const pt_grid* grid, const pt_kernel* kernel,
                             pt_precision prec, void* stream);
 
+/* The same operator for a general (non-diagonal) occupation matrix, evaluated as Algorithm 2's
+ * undiagonalised triple loop (Sec. III-B; Sec. II-B Eq. mixed_vx):
+ *   out_j = - sum_{k,i} sigma[i][k] phi_i(r) * IFFT[ K(G) * FFT[ conj(phi_k) tgt_j ] ](r)
+ * for j < M, i, k < N, with the pair FFT of (k, j) recomputed for every i (N*N*M pair FFTs, the
+ * baseline that the diagonalisation of Sec. IV-A1 replaces by N*M).  Kept as the comparison
+ * form: pt_apply_exchange on phit = phi Q with d = eig(sigma) gives the same result.
+ *   phi    Ng x N orbitals (any basis); sigma: N x N complex128 device matrix, row-major, used as
+ *          given (not symmetrised, no entry skipped)
+ *   tgt    Ng x M orbitals or NULL (tgt = phi, M = N); out: Ng x M, overwritten, no aliasing.
+ * *pair_ffts (optional, host) receives N*N*M.  Precisions: PT_FP64 or any FP32 form (the pair
+ * products and FFTs in FP32).  Asynchronous on `stream`. */
+pt_status pt_apply_exchange_mixed(pt_ctx* ctx, const void* phi, const void* sigma, int N, const void* tgt, int M,
+                                  void* out, const pt_grid* grid, const pt_kernel* kernel, pt_precision prec,
+                                  long long* pair_ffts, void* stream);
+
 /* Allocation-free variant of pt_apply_exchange (no counterpart in the paper: it exists for
  * callers that cannot allocate device memory while they run — an application whose own pool
  * allocator owns the whole device memory, or a latency-critical loop that cannot afford the
@@ -315,6 +330,8 @@ typedef struct {
   double total_energy;      /* E(t_n) of the input state (Ha): spin Tr[P_n (-Lap/2 + V_loc)] + E_x
                                (+ E_H + E_xc with params.hxc; the kinetic term carries params.A),
                                from the first iteration, where the midpoint is (Phi_n, sigma_n) */
+  int pure_state;           /* 1 when sigma_n = c I exactly (c real): the pure-state path ran (Eq.
+                               pure_vx: no sigma eigensolve, rotation or commutator; sigma_{n+1} = c I) */
 } pt_ptim_stats;
 
 /* One PT-IM(-ACE) step from (phi, sigma) = (Phi_n, sigma_n) to (Phi_{n+1}, sigma_{n+1}),

@@ -38,7 +38,7 @@ class pt_ptim_stats(C.Structure):
     _fields_ = [("outer", C.c_int), ("inner", C.c_int), ("residual", C.c_double), ("exch_energy", C.c_double),
                 ("orth_error", C.c_double), ("converged", C.c_int), ("pair_ffts", C.c_longlong),
                 ("exchange_calls", C.c_int), ("exchange_ms", C.c_double), ("phase_ms", C.c_double * 12),
-                ("eig_sweeps", C.c_int), ("total_energy", C.c_double)]
+                ("eig_sweeps", C.c_int), ("total_energy", C.c_double), ("pure_state", C.c_int)]
 
 PHASES = ("exchange", "ace_build", "ace_apply", "apply_H", "subspace_gemm", "subspace_nxn", "sigma_eig",
           "sigma_rot", "commutator", "anderson", "loewdin", "hxc")
@@ -54,6 +54,8 @@ PROTOTYPES = {
     "pt_trim": (i32, [vp]),
     "pt_set_option": (i32, [vp, C.c_char_p, C.c_double]),
     "pt_apply_exchange": (i32, [vp, vp, vp, i32, vp, i32, vp, C.POINTER(pt_grid), C.POINTER(pt_kernel), i32, vp]),
+    "pt_apply_exchange_mixed": (i32, [vp, vp, vp, i32, vp, i32, vp, C.POINTER(pt_grid), C.POINTER(pt_kernel), i32,
+                                      C.POINTER(C.c_longlong), vp]),
     "pt_apply_exchange_noalloc": (i32, [vp, vp, i32, vp, i32, vp, C.POINTER(pt_grid), C.POINTER(pt_kernel), i32, vp]),
     "pt_apply_exchange_batched": (i32, [vp, C.POINTER(pt_exchange_item), i32, i32, C.POINTER(C.c_longlong),
                                         C.POINTER(C.c_size_t), vp]),

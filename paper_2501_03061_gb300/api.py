@@ -191,6 +191,32 @@ class Context:
         self._check(st, "pt_apply_exchange")
         return out
 
+    def apply_exchange_mixed(self, phi, sigma, tgt=None, out=None, *, cell, kernel=None, precision="fp64",
+                             stream=None):
+        """out_j = -sum_ik sigma_ik phi_i IFFT[K FFT[conj(phi_k) tgt_j]] by the undiagonalised triple loop
+        (N*N*M pair FFTs; tgt None: tgt = phi).  Returns (out, pair_ffts)."""
+        self._orb(phi, precision, "phi")
+        if tgt is not None:
+            self._orb(tgt, precision, "tgt")
+        _block(phi, cell, "phi")
+        if tgt is not None:
+            _block(tgt, cell, "tgt")
+        if sigma.dtype != torch.complex128 or not sigma.is_contiguous() or sigma.device != self.device:
+            raise ValueError("sigma must be a contiguous complex128 tensor on the device")
+        _sized(sigma, phi.shape[0] ** 2, "sigma")
+        ref = phi if tgt is None else tgt
+        if out is None:
+            out = torch.empty_like(ref)
+        _result(out, ref.numel(), ref.dtype, self.device)
+        g, k = _grid(cell), _kernel(kernel)
+        n = C.c_longlong(0)
+        st = self.lib.pt_apply_exchange_mixed(self.h, _ptr(phi), _ptr(sigma), phi.shape[0],
+                                              None if tgt is None else _ptr(tgt), ref.shape[0], _ptr(out),
+                                              C.byref(g), C.byref(k), L.PRECISIONS[precision], C.byref(n),
+                                              _stream(stream))
+        self._check(st, "pt_apply_exchange_mixed")
+        return out, int(n.value)
+
     def apply_exchange_batched(self, items, *, precision="fp32", stream=None):
         """Batched V_x applications.  items: list of dicts with keys src, occ, cell and optional
         tgt, out, kernel (as apply_exchange).  Returns (outs, pair_ffts, graph_nodes)."""
@@ -396,7 +422,7 @@ class Context:
                 "exch_energy": s.exch_energy, "orth_error": s.orth_error, "converged": bool(s.converged),
                 "pair_ffts": int(s.pair_ffts), "exchange_calls": int(s.exchange_calls),
                 "exchange_ms": float(s.exchange_ms), "eig_sweeps": int(s.eig_sweeps),
-                "total_energy": float(s.total_energy),
+                "total_energy": float(s.total_energy), "pure_state": bool(s.pure_state),
                 "phase_ms": {n: float(s.phase_ms[i]) for i, n in enumerate(L.PHASES)}}
 
 

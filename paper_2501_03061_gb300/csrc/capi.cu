@@ -237,6 +237,29 @@ pt_status pt_apply_exchange(pt_ctx* ctx, const void* src, const double* occ, int
   });
 }
 
+pt_status pt_apply_exchange_mixed(pt_ctx* ctx, const void* phi, const void* sigma, int N, const void* tgt, int M,
+                                  void* out, const pt_grid* grid, const pt_kernel* kernel, pt_precision prec,
+                                  long long* pair_ffts, void* stream) {
+  return guarded(__func__, ctx, [&]() -> pt_status {
+    check_common(ctx, grid, prec);
+    check_kernel(kernel);
+    check_count(N, "N");
+    if (tgt == nullptr) M = N;
+    check_count(M, "M");
+    pt::require_aligned(phi, "phi");
+    pt::require_aligned(sigma, "sigma");
+    pt::require_aligned(out, "out");
+    if (tgt) pt::require_aligned(tgt, "tgt");
+    if (out == phi || (tgt && out == tgt)) pt::fail(PT_INVALID_ARG, "out must not alias phi or tgt");
+    set_device(ctx);
+    set_engine(ctx, prec);
+    const long long n = pt::exchange_mixed(ctx, phi, static_cast<const c128*>(sigma), N, tgt, M, out, *grid, *kernel,
+                                           prec, static_cast<cudaStream_t>(stream));
+    if (pair_ffts) *pair_ffts = n;
+    return PT_OK;
+  });
+}
+
 pt_status pt_apply_exchange_batched(pt_ctx* ctx, const pt_exchange_item* items, int count, pt_precision prec,
                                     long long* pair_ffts, size_t* graph_nodes, void* stream) {
   return guarded(__func__, ctx, [&]() -> pt_status {

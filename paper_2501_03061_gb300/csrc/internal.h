@@ -19,6 +19,9 @@ size_t exchange_scratch_budget(const pt_ctx* ctx);
 // W = V_x tgt (tgt == nullptr: tgt = src, symmetric pairs).  Returns the number of pair FFTs.
 long long exchange(pt_ctx* ctx, const void* src, const double* occ, int N, const void* tgt, int M, void* out,
                    const pt_grid& g, const pt_kernel& k, pt_precision prec, cudaStream_t st);
+// Algorithm 2's undiagonalised triple loop (N * N * M pair FFTs): out_j = -sum_ik sigma_ik phi_i v_kj
+long long exchange_mixed(pt_ctx* ctx, const void* phi, const c128* sigma, int N, const void* tgt, int M, void* out,
+                         const pt_grid& g, const pt_kernel& k, pt_precision prec, cudaStream_t st);
 
 // ---- batched exchange (batched.cu): autotuned pair tiles, replay from captured CUDA graphs ----
 long long exchange_batched(pt_ctx* ctx, const pt_exchange_item* items, int count, pt_precision prec,
