@@ -91,6 +91,33 @@ __global__ void k_maxabs_diff(const c128* __restrict__ A, const c128* __restrict
   }
 }
 
+// out[0] = max over entries of |sigma_ij - sigma_00 delta_ij| + |Im sigma_00|: zero exactly when
+// sigma = c I with c real (a pure state up to normalisation); out[1] = Re sigma_00
+__global__ void k_pure_check(const c128* __restrict__ sig, int N, double* __restrict__ out) {
+  const c128 c = sig[0];
+  double m = fabs(c.im);
+  const int n2 = N * N;
+  for (int e = threadIdx.x; e < n2; e += blockDim.x) {
+    const int i = e / N, j = e - i * N;
+    const double dr = sig[e].re - (i == j ? c.re : 0.0), di = sig[e].im - (i == j ? c.im : 0.0);
+    m = fmax(m, fabs(dr) + fabs(di));
+  }
+  for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+  __shared__ double s[32];
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) r = fmax(r, s[w]);
+    out[0] = r;
+    out[1] = c.re;
+  }
+}
+
+__global__ void k_fill(double* __restrict__ d, int n, const double* __restrict__ v) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) d[e] = v[0];
+}
+
 // sum_i d_i Re <phit_i|V phit_i> * dV   (one block per orbital, FP64 block reduction)
 template <class T>
 __global__ void k_weighted_diag(const cx<T>* __restrict__ a, const cx<T>* __restrict__ b, const double* __restrict__ d,
@@ -256,6 +283,20 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
     }
   } restore{phi, sig, phin, sign, fb, mb, st, true};
   gram<T>(ctx, phin, phin, N, N, S.ng, S.dV, Sn, st);
+  // Pure state (sigma_n = c I, Eq. pure_vx): sigma_h stays c I, its eigenbasis is any basis, the
+  // commutator [A, c I] vanishes, so the eigensolve, the rotations into and out of the eigenbasis
+  // and the commutator are skipped; Algorithm 1's final step then orthonormalises Phi and keeps
+  // sigma = c I (the general step's S^{1/2} sigma S^{1/2} differs from c I by c (S - I), at the
+  // level of the orthonormality error)
+  bool pure = false;
+  {
+    PT_LAUNCH(k_pure_check, 1, 1024, 0, st, sign, N, dsc);
+    double h[2] = {1.0, 0.0};
+    PT_CUDA_CHECK(cudaMemcpyAsync(h, dsc, sizeof(h), cudaMemcpyDeviceToHost, st));
+    PT_CUDA_CHECK(cudaStreamSynchronize(st));
+    pure = h[0] == 0.0;
+    if (pure) PT_LAUNCH(k_fill, std::max(1, (N + 255) / 256), 256, 0, st, d, N, dsc + 1);  // d_i = c
+  }
 
   pt_ptim_stats stv;
   std::memset(&stv, 0, sizeof(stv));
@@ -281,6 +322,28 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
   // sigma_h changes little between outer iterations and between steps: eigensolves start from the
   // last basis the context holds (any unitary start is correct; a near one converges in a sweep or two)
   auto exchange_on_midpoint = [&](cx<T>* out, bool energy) {
+    if (pure) {  // phit = Phi_h, d_i = c: V_x Phi_h directly, no eigenbasis
+      tm.begin(PH_EXCH);
+      std::pair<cudaEvent_t, cudaEvent_t> e;
+      PT_CUDA_CHECK(cudaEventCreate(&e.first));
+      PT_CUDA_CHECK(cudaEventCreate(&e.second));
+      ev.push_back(e);
+      PT_CUDA_CHECK(cudaEventRecord(e.first, st));
+      stv.pair_ffts += exchange(ctx, phih, d, N, nullptr, N, out, g, kern, prec, st);
+      PT_CUDA_CHECK(cudaEventRecord(e.second, st));
+      tm.end();
+      stv.exchange_calls++;
+      if (energy) {
+        PT_LAUNCH(k_weighted_diag<T>, N, 256, 0, st, phih, out, d, S.ng, S.dV, dsc);
+        std::vector<double> h(N);
+        PT_CUDA_CHECK(cudaMemcpyAsync(h.data(), dsc, N * sizeof(double), cudaMemcpyDeviceToHost, st));
+        PT_CUDA_CHECK(cudaStreamSynchronize(st));
+        double en = 0;
+        for (double v : h) en += v;
+        stv.exch_energy = P.spin * 0.5 * P.alpha * en;
+      }
+      return;
+    }
     tm.begin(PH_EIG);
     const bool warm = ctx->ptim_q_n == N;
     ctx->ptim_q_n = 0;  // Q is being rewritten
@@ -430,9 +493,13 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
       rotate<T>(ctx, phih, SinvA, N, N, N, S.ng, c128{0, P.dt}, tr, 3, rphi, st);
       tm.end();
       tm.begin(PH_COMM);
-      // r_sigma = sigma_n - i dt (A sigma_h - sigma_h A) - sigma
-      zgemm('N', 'N', N, N, N, c128{1, 0}, A, N, sigh, N, c128{0, 0}, T1, N, st);
-      zgemm('N', 'N', N, N, N, c128{-1, 0}, sigh, N, A, N, c128{1, 0}, T1, N, st);
+      // r_sigma = sigma_n - i dt (A sigma_h - sigma_h A) - sigma  (the commutator is 0 in a pure state)
+      if (pure) {
+        PT_CUDA_CHECK(cudaMemsetAsync(T1, 0, mb, st));
+      } else {
+        zgemm('N', 'N', N, N, N, c128{1, 0}, A, N, sigh, N, c128{0, 0}, T1, N, st);
+        zgemm('N', 'N', N, N, N, c128{-1, 0}, sigh, N, A, N, c128{1, 0}, T1, N, st);
+      }
       Term ts[3] = {{sign, c128{1, 0}}, {T1, c128{0, -P.dt}}, {sig, c128{-1, 0}}};
       lincomb<double>(ctx, rsig, S.n2, ts, 3, st);
       tm.end();
@@ -566,11 +633,15 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
   }
   rotate<T>(ctx, phi, A, N, N, N, S.ng, c128{1, 0}, nullptr, 0, rphi_buf[0], st);
   PT_CUDA_CHECK(cudaMemcpyAsync(phi, rphi_buf[0], fb, cudaMemcpyDeviceToDevice, st));
-  zgemm('N', 'N', N, N, N, c128{1, 0}, Lc, N, sig, N, c128{0, 0}, T1, N, st);
-  zgemm('N', 'N', N, N, N, c128{1, 0}, T1, N, Lc, N, c128{0, 0}, sig, N, st);
-  conj_transpose(sig, N, T1, st);
-  Term th[2] = {{sig, c128{0.5, 0}}, {T1, c128{0.5, 0}}};
-  lincomb<double>(ctx, sig, S.n2, th, 2, st);
+  if (pure) {
+    PT_CUDA_CHECK(cudaMemcpyAsync(sig, sign, mb, cudaMemcpyDeviceToDevice, st));  // sigma stays c I
+  } else {
+    zgemm('N', 'N', N, N, N, c128{1, 0}, Lc, N, sig, N, c128{0, 0}, T1, N, st);
+    zgemm('N', 'N', N, N, N, c128{1, 0}, T1, N, Lc, N, c128{0, 0}, sig, N, st);
+    conj_transpose(sig, N, T1, st);
+    Term th[2] = {{sig, c128{0.5, 0}}, {T1, c128{0.5, 0}}};
+    lincomb<double>(ctx, sig, S.n2, th, 2, st);
+  }
   tm.end();
   int h_info = 0;
   PT_CUDA_CHECK(cudaMemcpyAsync(&h_info, info, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -583,6 +654,7 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
     stv.exchange_ms += ms;
   }
   stv.converged = converged ? 1 : 0;
+  stv.pure_state = pure ? 1 : 0;
   if (stats) *stats = stv;
   warm_guard.done = true;
   restore.armed = false;

@@ -1,6 +1,7 @@
 """Degenerate occupation matrices in the PT-IM step, against the oracle: the pure state sigma = I
-(every eigenvalue equal, so the eigenbasis is arbitrary and only basis-independent results are
-compared; the commutator vanishes and sigma must stay I) and a diagonal sigma with exactly empty
+and sigma = I/2 (every eigenvalue equal, so the eigenbasis is arbitrary and only basis-independent
+results are compared; such steps take the pure-state path: no eigensolve or commutator, sigma stays
+c I) and a diagonal sigma with exactly empty
 orbitals (pairs of two empty orbitals are skipped by the exchange)."""
 import numpy as np
 import pytest
@@ -28,6 +29,7 @@ def rel(a, b):
 
 SIGMAS = {
     "pure": np.eye(6, dtype=np.complex128),
+    "pure_half": 0.5 * np.eye(6, dtype=np.complex128),
     "empty_orbitals": np.diag([1.0, 1.0, 0.9, 0.0, 0.0, 0.0]).astype(np.complex128),
 }
 
@@ -68,5 +70,9 @@ def test_degenerate_sigma_step_matches_oracle(ctx, refs, name, precision, tc_gra
     R = np.einsum("ir,ij,js->rs", r, sig1, r.conj())
     assert rel(P, R) <= bar
     assert np.abs(s - sig1).max() <= bar
-    if name == "pure":
-        assert np.abs(s - np.eye(6)).max() <= bar  # [A, I] = 0: sigma does not move
+    if name.startswith("pure"):
+        # sigma_n = c I takes the pure-state path (Eq. pure_vx): no eigensolve, sigma stays c I
+        assert st["pure_state"] and st["eig_sweeps"] == 0 and st["phase_ms"]["sigma_eig"] == 0.0
+        assert np.abs(s - SIGMAS[name]).max() == 0.0
+    else:
+        assert not st["pure_state"]
