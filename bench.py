@@ -80,9 +80,11 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=1,
                     help="timed plain FP64 PT-IM steps (after one FP64 warm-up step); 0 skips the FP64 step")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    ap.add_argument("--no-ablation", action="store_true",
+                    help="skip the triple-loop vs diagonalised exchange and pure-state step measurement")
     ap.add_argument("--mode", default="step",
                     choices=["step", "exchange", "serve", "batched", "precision", "contractions", "library",
-                             "peaks"],
+                             "peaks", "ablation"],
                     help="step: PT-IM steps (the benchmark); exchange: only V_x applications on the same cell "
                          "(profiler captures of the exchange kernel); serve / batched: configs 5 / 4 alone; "
                          "precision: config 3 per-result errors; contractions: Gram/rotation engines at 64^3; "
@@ -520,6 +522,94 @@ def library_comparison() -> dict:
     return res
 
 
+def diag_ablation(cell128=None) -> dict:
+    """The paper's "Diag" step measured on one GPU (Sec. IV-A1 against Algorithm 2): V_x[P] Phi for a
+    general Hermitian sigma by the undiagonalised triple loop (pt_apply_exchange_mixed, N^2 M pair
+    FFTs) and by the diagonalised form (sigma eigensolve, rotation, symmetric pair FFTs, rotation
+    back), on the same inputs, CUDA events, one warm-up call each; plus one PT-IM step in a pure
+    state (sigma = I, the pure-state path) against one with the Fermi-Dirac sigma on the benchmark
+    cell."""
+    import numpy as np
+    import torch
+
+    from paper_2501_03061_gb300 import api, synth
+
+    def herm(rng, f, scale):
+        N = len(f)
+        A = rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))
+        return np.diag(f).astype(np.complex128) + scale * (A + A.conj().T)
+
+    def timed(f):
+        f()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        out = f()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b), out
+
+    ctx = api.Context(0)
+    res = {}
+    try:
+        cases = [("cell_24^3_N16_fp64", synth.exchange_small(), "fp64"),
+                 ("cell_64^3_N32_fp32", synth.small_cell(3032, 64, 20.5, 32, kT=0.02), "fp32"),
+                 ("cell_64^3_N32_fp64", synth.small_cell(3032, 64, 20.5, 32, kT=0.02), "fp64")]
+        for name, w, prec in cases:
+            rng = np.random.default_rng(7)
+            sig = herm(rng, w.occ, 0.02)
+            dt = np.complex128 if prec == "fp64" else np.complex64
+            phi = torch.from_numpy(w.phi.astype(dt)).cuda()
+            sd = torch.from_numpy(sig).cuda()
+            kw = dict(cell=w.cell, kernel=w.kernel, precision=prec)
+
+            def mixed():
+                return ctx.apply_exchange_mixed(phi, sd, **kw)[0]
+
+            def diag():
+                Q, d = ctx.diag_occupations(sd)
+                phit = ctx.rotate(phi, Q, cell=w.cell, precision=prec)
+                wt = ctx.apply_exchange(phit, d, **kw)
+                return ctx.rotate(wt, Q.conj().T.contiguous(), cell=w.cell, precision=prec)
+
+            t_m, a = timed(mixed)
+            t_d, b = timed(diag)
+            N = w.N
+            res[name] = {"N": N, "triple_loop_ms": t_m, "triple_loop_pair_ffts": N ** 3, "diagonalised_ms": t_d,
+                         "diagonalised_pair_ffts": N * (N + 1) // 2, "speedup": t_m / t_d,
+                         "pair_fft_ratio": N ** 3 / (N * (N + 1) / 2),
+                         "rel_difference": float((a.to(torch.complex128) - b.to(torch.complex128)).norm()
+                                                 / b.to(torch.complex128).norm())}
+            del phi, a, b
+        # pure-state path against the general step on the benchmark cell (FP32 form)
+        w = cell128 or synth.ptim_cell128()
+        ctx.set_option("tc_gram", 1)
+        vloc = torch.from_numpy(w.vloc).cuda()
+        kw = dict(cell=w.cell, kernel=w.kernel, precision="fp32", dt=0.5, alpha=0.25, ecut=10.0, tol=1e-6,
+                  max_outer=20, max_inner=100, anderson_depth=20, allow_unconverged=True)
+        steps = {}
+        for name, sig in (("general_fermi_dirac_sigma", w.sigma), ("pure_state_sigma_identity",
+                                                                    np.eye(w.N, dtype=np.complex128))):
+            phi = torch.from_numpy(w.phi.astype(np.complex64)).cuda()
+            sd = torch.from_numpy(sig.copy()).cuda()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            st = ctx.ptim_step(phi, sd, vloc, **kw)
+            b.record()
+            torch.cuda.synchronize()
+            steps[name] = {"ms": a.elapsed_time(b), "pure_state": st["pure_state"], "outer": st["outer"],
+                           "inner": st["inner"], "converged": st["converged"],
+                           "sigma_phases_ms": {k: st["phase_ms"][k] for k in ("sigma_eig", "sigma_rot",
+                                                                              "commutator")}}
+            del phi, sd
+        res["ptim_step_64^3_N320"] = steps
+    finally:
+        ctx.set_option("tc_gram", 0)
+        ctx.close()
+    return res
+
+
 def serve_measurement(window_s: float, slots: int = 6) -> dict:
     """Serving form: Poisson stream of PT-IM step requests (N in 32..320, grids 32^3..64^3, FP32).
 
@@ -840,6 +930,14 @@ def run_gb300(args):
                 "exchange_speedup_fp32_vs_fp64": t64 / t32}
         del pd, p32
 
+    ablation = None
+    if rank == 0 and world == 1 and not args.no_ablation:
+        try:
+            ctx.trim()
+            ablation = diag_ablation(w if N == 320 else None)
+        except Exception as e:  # noqa: BLE001
+            ablation = {"error": str(e)[:300]}
+
     prec_res = None
     if rank == 0 and world == 1 and not args.no_fp64:
         try:
@@ -907,6 +1005,7 @@ def run_gb300(args):
             "clocks": clocks,
             "plain_fp64_step": fp64_step,
             "plain_fp64_form": fp64,
+            "diag_ablation": ablation,
             "precision_forms": prec_res,
             "serve": serve_res,
         }
@@ -982,6 +1081,8 @@ def main():
         print(json.dumps({"mode": "precision", "precision_forms": precision_forms()}), flush=True)
     elif args.mode == "contractions":
         print(json.dumps({"mode": "contractions", "contractions": contraction_measurement()}), flush=True)
+    elif args.mode == "ablation":
+        print(json.dumps({"mode": "ablation", "diag_ablation": diag_ablation()}), flush=True)
     elif args.mode == "library":
         print(json.dumps({"mode": "library", "library": library_comparison()}), flush=True)
     elif args.mode == "peaks":
