@@ -90,7 +90,10 @@ def parse():
                          "precision: config 3 per-result errors; contractions: Gram/rotation engines at 64^3; "
                          "library: cuFFT exchange and cuBLAS contractions timed beside the library (comparison); "
                          "peaks: FP32/FP64 FMA throughput of the device (CUDA-core roofline denominators)")
-    ap.add_argument("--serve-window", type=float, default=15.0, help="seconds of arrivals per serving phase")
+    ap.add_argument("--serve-window", type=float, default=15.0,
+                    help="least seconds of arrivals per serving phase")
+    ap.add_argument("--serve-completions", type=int, default=200,
+                    help="completed requests each serving phase runs until (with at least --serve-window seconds)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement in step mode")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -610,14 +613,18 @@ def diag_ablation(cell128=None) -> dict:
     return res
 
 
-def serve_measurement(window_s: float, slots: int = 6) -> dict:
+def serve_measurement(window_s: float, slots: int = 6, min_completions: int = 200, fp64_burst: int = 8,
+                      session_steps: int = 4, queue_cap: int = 512) -> dict:
     """Serving form: Poisson stream of PT-IM step requests (N in 32..320, grids 32^3..64^3, FP32).
 
     Systems are cut from one generated template per grid size (the first N orbitals of an
     orthonormal set stay orthonormal; occupations are redrawn for N).  Phase 1 measures the
-    saturation throughput with a burst; phase 2 replays the 200 req/s stream for `window_s`
-    seconds of arrivals; phase 3 replays arrivals at 75% of the saturation rate.  Queued
-    requests still waiting when a window closes are counted as backlog, not run.
+    saturation throughput with a burst; phase 2 replays the 200 req/s stream and phase 3 replays
+    arrivals at 75% of the saturation rate, each until `min_completions` requests have completed
+    (at least `window_s` seconds); an arrival that finds `queue_cap` requests waiting is turned
+    away (counted), and requests still queued when arrivals stop are counted as backlog, not run.  Phase 4 runs the stream's first `fp64_burst` requests as one burst in the FP32 form
+    and in the plain FP64 form (latency and throughput of the same requests).  Phase 5 keeps
+    `slots` systems resident as sessions and serves requests of `session_steps` chained steps.
     """
     import numpy as np
 
@@ -654,38 +661,79 @@ def serve_measurement(window_s: float, slots: int = 6) -> dict:
 
         def replay(rate, tag):
             srv.completed.clear()
-            gaps = np.random.default_rng(1005).exponential(1.0 / rate, size=100000)
+            gaps = np.random.default_rng(1005).exponential(1.0 / rate, size=1000000)
             t_start = time.perf_counter()
-            futs, k, t = [], 0, 0.0
+            k, t, dropped = 0, 0.0, 0
             while True:
                 t += gaps[k]
                 if t > window_s:
-                    break
+                    with srv.cv:
+                        enough = sum(1 for r in srv.completed if r.error is None) >= min_completions
+                    if enough:
+                        break
                 now = time.perf_counter() - t_start
                 if t > now:
                     time.sleep(t - now)
-                r = make(stream[(2 * slots + k) % len(stream)])
-                r.t_arrival = t_start + t
-                futs.append(srv.submit(r))
                 k += 1
-            backlog = 0
+                if srv.backlog() >= queue_cap:  # a full queue turns the arrival away
+                    dropped += 1
+                    continue
+                r = make(stream[(2 * slots + k - 1) % len(stream)])
+                r.t_arrival = t_start + t
+                srv.submit(r)
+            t_stop = time.perf_counter() - t_start
             with srv.cv:
                 backlog = len(srv.queue)
                 srv.queue.clear()
-            for f in futs:
-                if f.done():
-                    continue
             while any(w.busy for w in srv.workers):
                 time.sleep(0.05)
             fin = [r for r in srv.completed if r.error is None]
             summ = serve.latency_summary(fin)
-            summ.update({"offered_req_per_s": rate, "arrivals": k, "completed": len(fin), "backlog": backlog,
+            summ.update({"offered_req_per_s": rate, "arrivals": k, "arrival_window_s": t_stop, "completed": len(fin),
+                         "backlog": backlog, "dropped_queue_full": dropped, "queue_cap": queue_cap,
                          "throughput_req_per_s": len(fin) / max(1e-9, time.perf_counter() - t_start)})
             out[tag] = summ
 
         replay(200.0, "at_200_req_per_s")
-        window_s = max(window_s, 40.0)
         replay(0.75 * sat, "at_75pct_saturation")
+
+        # phase 4: the same requests in the FP32 form and in the plain FP64 form, one burst each
+        rows = {}
+        for prec in ("fp32", "fp64"):
+            srv.completed.clear()
+            reqs = [make(sp, prec) for sp in stream[2 * slots:2 * slots + fp64_burst]]
+            t0 = time.perf_counter()
+            futs = [srv.submit(r) for r in reqs]
+            fin = [f.result() for f in futs]
+            dt = time.perf_counter() - t0
+            summ = serve.latency_summary([r for r in fin if r.error is None])
+            summ.update({"requests": len(reqs), "makespan_s": dt, "throughput_req_per_s": len(reqs) / dt,
+                         "errors": sum(1 for r in fin if r.error is not None)})
+            rows[prec] = summ
+        rows["fp32_speedup_throughput"] = rows["fp64"]["makespan_s"] / rows["fp32"]["makespan_s"]
+        rows["note"] = (f"the stream's requests {2 * slots}..{2 * slots + fp64_burst - 1} submitted at once, "
+                        f"in each form")
+        out["fp32_vs_plain_fp64_burst"] = rows
+
+        # phase 5: sessions - state resident across requests of several chained steps
+        srv.completed.clear()
+        sids = []
+        for sp in stream[:slots]:
+            r = make(sp)
+            sids.append(srv.open_session(r.phi, r.sigma, r.vloc, r.cell, r.kernel, "fp32"))
+        t0 = time.perf_counter()
+        futs = [srv.submit(serve.Request(phi=None, sigma=None, occ=None, vloc=None, cell=None, kernel={},
+                                         session=sid, steps=session_steps, params={"tol": 1e-6}))
+                for sid in sids for _ in range(2)]
+        fin = [f.result() for f in futs]
+        dt = time.perf_counter() - t0
+        for sid in sids:
+            srv.close_session(sid)
+        steps = sum(len(r.result["stats"]) for r in fin if r.error is None)
+        summ = serve.latency_summary([r for r in fin if r.error is None])
+        summ.update({"sessions": len(sids), "requests": len(fin), "steps_per_request": session_steps,
+                     "steps": steps, "steps_per_s": steps / dt, "errors": sum(1 for r in fin if r.error)})
+        out["sessions"] = summ
     finally:
         srv.close()
     return out
@@ -949,7 +997,7 @@ def run_gb300(args):
     if rank == 0 and world == 1 and not args.no_serve:
         try:
             ctx.trim()
-            serve_res = serve_measurement(args.serve_window)
+            serve_res = serve_measurement(args.serve_window, min_completions=args.serve_completions)
         except Exception as e:  # noqa: BLE001
             serve_res = {"error": str(e)[:300]}
         try:
@@ -1101,7 +1149,7 @@ def main():
     elif args.mode == "serve":
         import torch
         torch.cuda.set_device(0)
-        res = serve_measurement(args.serve_window)
+        res = serve_measurement(args.serve_window, min_completions=args.serve_completions)
         res["batched"] = batched_measurement()
         print(json.dumps({"mode": "serve", "serve": res}), flush=True)
     else:

@@ -11,6 +11,12 @@ systems are not starved.  Inputs are copied to the device when the request start
 resident on the device while it runs, results are copied back when it ends, and every request
 records its arrival, start and end times for p50/p99 latency.
 
+Sessions keep a system's state on the device between requests: open_session copies (Phi, sigma,
+V_loc) up once, a request with `session` set runs `steps` chained PT-IM steps on that resident
+state in place (no host copies of the orbitals), and close_session hands the state back.  Session
+state counts against the HBM budget while it is open; requests of one session run one at a time,
+in order (a queue head whose session is busy waits, keeping admission FIFO).
+
 All computation runs in libptim.so through `api.Context`; this module only schedules.
 """
 from __future__ import annotations
@@ -40,6 +46,8 @@ class Request:
     kind: str = "ptim"              # "ptim" or "exchange"
     precision: str = "fp32"
     params: dict = dataclasses.field(default_factory=dict)
+    session: int | None = None      # run on the resident state of this session (phi/sigma/vloc unused)
+    steps: int = 1                  # chained PT-IM steps of a session request
     t_arrival: float = 0.0
     t_start: float = 0.0
     t_end: float = 0.0
@@ -49,7 +57,7 @@ class Request:
 
     @property
     def N(self) -> int:
-        return int(self.phi.shape[0])
+        return int(self.phi.shape[0]) if self.phi is not None else 0
 
     @property
     def latency(self) -> float:
@@ -81,6 +89,8 @@ class Server:
         self.running = True
         self.completed: list[Request] = []
         self.rejected: list[Request] = []
+        self.sessions: dict[int, dict] = {}
+        self._next_session = 0
         self._threads = []
         self._sched = threading.Thread(target=self._schedule, daemon=True)
         self._sched.start()
@@ -88,9 +98,42 @@ class Server:
     # ------------------------------------------------------------------ public
     def footprint(self, req: Request) -> int:
         depth = int(req.params.get("anderson_depth", 20))
+        if req.session is not None:
+            ss = self.sessions[req.session]
+            return api.ptim_footprint(ss["N"], ss["cell"], ss["precision"], depth)  # state already resident
         lib = api.ptim_footprint(req.N, req.cell, req.precision, depth if req.kind == "ptim" else 1)
         io = 2 * req.phi.size * (16 if req.precision == "fp64" else 8)  # inputs and outputs on the device
         return lib + io
+
+    def open_session(self, phi: np.ndarray, sigma: np.ndarray, vloc: np.ndarray, cell, kernel: dict,
+                     precision: str = "fp32") -> int:
+        """Copy a system's state to the device once; returns the session id.  The state's bytes
+        count against the HBM budget until close_session."""
+        dev = torch.device("cuda", self.device)
+        cdt = _CDT["fp64" if precision == "fp64" else "fp32"]
+        st = {"phi": torch.from_numpy(np.ascontiguousarray(phi.astype(cdt))).to(dev),
+              "sigma": torch.from_numpy(np.ascontiguousarray(sigma, dtype=np.complex128)).to(dev),
+              "vloc": torch.from_numpy(np.ascontiguousarray(vloc, dtype=np.float64)).to(dev),
+              "cell": cell, "kernel": kernel, "precision": precision, "N": int(phi.shape[0]), "busy": False,
+              "steps_done": 0}
+        st["bytes"] = sum(st[k].numel() * st[k].element_size() for k in ("phi", "sigma", "vloc"))
+        torch.cuda.synchronize(dev)
+        with self.cv:
+            if self._reserved() + st["bytes"] > self.budget:
+                raise RuntimeError("session state does not fit the HBM budget")
+            sid = self._next_session
+            self._next_session += 1
+            self.sessions[sid] = st
+        return sid
+
+    def close_session(self, sid: int) -> dict:
+        """Wait for the session's requests, copy its state back to the host and release it."""
+        with self.cv:
+            while self.sessions[sid]["busy"] or any(r.session == sid for r, _ in self.queue):
+                self.cv.wait(0.05)
+            st = self.sessions.pop(sid)
+            self.cv.notify_all()
+        return {"phi": st["phi"].cpu().numpy(), "sigma": st["sigma"].cpu().numpy(), "steps_done": st["steps_done"]}
 
     def submit(self, req: Request) -> Future:
         req.t_arrival = time.perf_counter() if req.t_arrival == 0.0 else req.t_arrival
@@ -122,7 +165,7 @@ class Server:
 
     # ------------------------------------------------------------------ scheduling
     def _reserved(self) -> int:
-        return sum(max(w.held, w.reserved) for w in self.workers)
+        return sum(max(w.held, w.reserved) for w in self.workers) + sum(s["bytes"] for s in self.sessions.values())
 
     def _schedule(self):
         while True:
@@ -139,6 +182,8 @@ class Server:
                     req, fut = self.queue.popleft()
                     w.busy = True
                     w.reserved = req.footprint
+                    if req.session is not None:
+                        self.sessions[req.session]["busy"] = True
                 else:
                     trim.busy = True  # keep it out of the pool while its workspace is released
             if trim is not None:
@@ -161,6 +206,8 @@ class Server:
         if not free:
             return None, None
         req = self.queue[0][0]
+        if req.session is not None and self.sessions[req.session]["busy"]:
+            return None, None  # the session's previous request is still running: keep FIFO order
         w = max(free, key=lambda x: x.held)  # reuse the largest cached workspace
         if self._reserved() - max(w.held, w.reserved) + max(w.held, req.footprint) <= self.budget:
             return w, None
@@ -181,12 +228,25 @@ class Server:
             w.held = w.ctx.workspace_bytes()
             w.reserved = 0
             w.busy = False
+            if req.session is not None:
+                self.sessions[req.session]["busy"] = False
             self.completed.append(req)
             self.cv.notify_all()
         fut.set_result(req)
 
     def _execute(self, w: _Worker, req: Request) -> dict:
         dev = torch.device("cuda", self.device)
+        if req.session is not None:
+            ss = self.sessions[req.session]
+            p = dict(dt=0.5, alpha=0.25, ecut=10.0, tol=1e-6, max_outer=20, max_inner=100, anderson_depth=20)
+            p.update(req.params)
+            stats = []
+            for _ in range(max(1, req.steps)):
+                stats.append(w.ctx.ptim_step(ss["phi"], ss["sigma"], ss["vloc"], cell=ss["cell"], kernel=ss["kernel"],
+                                             precision=ss["precision"], stream=w.stream, allow_unconverged=True, **p))
+            w.stream.synchronize()
+            ss["steps_done"] += len(stats)
+            return {"stats": stats}
         cdt = _CDT["fp64" if req.precision == "fp64" else "fp32"]
         s = w.stream
         phi = torch.from_numpy(np.ascontiguousarray(req.phi.astype(cdt))).to(dev, non_blocking=True)

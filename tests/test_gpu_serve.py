@@ -72,3 +72,35 @@ def test_admission_rejects_oversize_and_queues_within_budget():
         assert rej.error == "larger than the HBM budget"
     finally:
         srv.close()
+
+
+def test_session_steps_equal_chained_requests():
+    """A session (state resident on the device) serving two requests of two steps each gives the
+    state that four chained ordinary requests give, the state copied through the host in between."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2501_03061_gb300.serve import Request, Server
+    w = synth.small_cell(531, 16, 8.0, 8, kT=0.05, ecut=8.0)
+    # each worker's context warm-starts its sigma eigensolve from its own last basis, so two routes
+    # agree to the order of the tolerance they converge to, not to rounding
+    params = {"ecut": 8.0, "tol": 1e-11}
+    srv = Server(slots=2)
+    try:
+        phi, sig = w.phi, w.sigma
+        for _ in range(4):
+            r = _results(srv, [Request(phi=phi, sigma=sig, occ=None, vloc=w.vloc, cell=w.cell, kernel=w.kernel,
+                                       kind="ptim", precision="fp64", params=params)])[0]
+            assert r.error is None, r.error
+            phi, sig = r.result["phi"], r.result["sigma"]
+        sid = srv.open_session(w.phi, w.sigma, w.vloc, w.cell, w.kernel, "fp64")
+        futs = [srv.submit(Request(phi=None, sigma=None, occ=None, vloc=None, cell=None, kernel={}, session=sid,
+                                   steps=2, params=params)) for _ in range(2)]
+        res = [f.result(timeout=300) for f in futs]
+        assert all(r.error is None for r in res), [r.error for r in res]
+        assert res[0].t_end <= res[1].t_start  # one request of a session at a time, in order
+        st = srv.close_session(sid)
+    finally:
+        srv.close()
+    assert st["steps_done"] == 4
+    assert np.linalg.norm(st["phi"] - phi) <= 1e-9 * np.linalg.norm(phi)
+    assert np.abs(st["sigma"] - sig).max() <= 1e-9

@@ -17,6 +17,7 @@ def server_stub(budget, workers):
     s.budget = budget
     s.workers = workers
     s.queue = collections.deque()
+    s.sessions = {}
     return s
 
 
@@ -24,8 +25,8 @@ def worker(held=0, reserved=0, busy=False):
     return types.SimpleNamespace(held=held, reserved=reserved, busy=busy)
 
 
-def request(footprint):
-    return types.SimpleNamespace(footprint=footprint)
+def request(footprint, session=None):
+    return types.SimpleNamespace(footprint=footprint, session=session)
 
 
 def test_admits_queue_head_on_the_worker_with_the_largest_cache():
@@ -133,3 +134,29 @@ def test_a_failing_request_is_recorded_and_frees_its_worker():
     assert req.t_end >= req.t_start > 0
     assert (w.busy, w.reserved, w.held) == (False, 0, 17)
     assert s.completed == [req]
+
+
+def test_open_session_state_counts_against_the_budget():
+    a = worker()
+    s = server_stub(100, [a])
+    s.sessions[0] = {"bytes": 70, "busy": False}
+    s.queue.append((request(40), None))
+    assert s._reserved() == 70
+    w, trim = s._pick()
+    assert w is None and trim is None  # 70 resident + 40 > 100
+    s.sessions.clear()
+    w, trim = s._pick()
+    assert w is a
+
+
+def test_session_requests_run_one_at_a_time_in_order():
+    a, b = worker(), worker()
+    s = server_stub(1000, [a, b])
+    s.sessions[3] = {"bytes": 10, "busy": True}  # its previous request is still running
+    s.queue.append((request(20, session=3), None))
+    s.queue.append((request(20), None))
+    w, trim = s._pick()
+    assert w is None and trim is None  # the head waits for its session; FIFO keeps the rest behind it
+    s.sessions[3]["busy"] = False
+    w, trim = s._pick()
+    assert w is not None
