@@ -784,9 +784,26 @@ def batched_measurement(reps: int = 3) -> dict:
         torch.cuda.synchronize()
         t_eager = a.elapsed_time(b) / 1e3
         ctx.set_option("graphs", 1)
+        # one branch (items in order on one stream) for comparison
+        ctx.set_option("batch_streams", 1)
+        ctx.apply_exchange_batched(items, precision="fp32")
+        torch.cuda.synchronize()
+        a.record(stream)
+        ctx.apply_exchange_batched(items, precision="fp32")
+        b.record(stream)
+        torch.cuda.synchronize()
+        t_one = a.elapsed_time(b) / 1e3
+        ctx.set_option("batch_streams", 4)
     finally:
         ctx.close()
+    # roofline of the batched form: the 4-field per-pair bytes of every item over the replay time
+    alg_bytes = sum((sp["N"] * (sp["N"] + 1) // 2) * 4 * sp["n"] ** 3 * 8 for sp in specs)
+    peak, peak_src = read_peaks()
     return {"instances": len(items), "pair_ffts": npairs, "seconds": t_graph, "pair_ffts_per_s": npairs / t_graph,
+            "roofline": {"bound": "hbm", "achieved": alg_bytes / t_graph / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": alg_bytes / t_graph / 1e9 / peak, "peak_source": peak_src,
+                         "model": "4 complex64 fields of Ng per pair FFT, summed over the items"},
+            "branches": 4, "one_branch_seconds": t_one, "one_branch_pair_ffts_per_s": npairs / t_one,
             "graph_nodes": nodes, "host_kernel_launches_per_replay": host_launches // reps,
             "eager_seconds": t_eager, "eager_pair_ffts_per_s": npairs / t_eager,
             "first_call_seconds_incl_autotune_and_capture": first_s,

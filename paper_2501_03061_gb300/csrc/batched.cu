@@ -4,9 +4,13 @@
 //
 // Host runtime around the exchange kernels:
 //   * autotuner: the pair-tile size of a grid (how many pair fields one FFT batch holds, which
-//     sets the L2 footprint and the launch count) is picked by timing candidate budgets of
-//     12 MiB to 512 MiB on the first item of that grid (its first min(N, 32) orbitals) and kept
-//     in the context;
+//     sets the L2 footprint and the launch count) and, on 64^3 FP32 grids, the kernel family (the
+//     launch-pipelined TMA kernels or the compile-time tile kernels) are picked by timing
+//     candidates of 12 MiB to 512 MiB on the first item of that grid (its first min(N, 32)
+//     orbitals) and kept in the context;
+//   * concurrent branches: items are dealt to `batch_streams` streams (longest first, by pair
+//     FFTs x grid points), each with its own scratch buffers, forked from and joined back to the
+//     caller's stream with events, so the small items' kernels fill the tails of the large ones';
 //   * CUDA graphs: the first call with a given item set runs eagerly once (this sizes every
 //     workspace, builds schedules and tables and encodes nothing that later changes), then the
 //     whole batch is captured on a context-owned stream into one graph, which this and every
@@ -38,74 +42,155 @@ std::string grid_key(const pt_grid& g, pt_precision prec) {
   return b;
 }
 
-// Pick the pair-field budget for the grid of `it` by timing candidates (cached per grid).
-size_t tuned_budget(pt_ctx* ctx, const pt_exchange_item& it, pt_precision prec, cudaStream_t st) {
+struct Tuned {
+  size_t budget;
+  int engine;  // exchange64_engine for 64^3 FP32 grids (0 or 1); ignored elsewhere
+};
+
+// Pick the pair-field budget (and the 64^3 engine) for the grid of `it` by timing candidates
+// (cached per grid).
+Tuned tuned_budget(pt_ctx* ctx, const pt_exchange_item& it, pt_precision prec, cudaStream_t st) {
   const std::string key = grid_key(it.grid, prec);
   auto c = ctx->caches.find(key);
-  if (c != ctx->caches.end()) return *std::static_pointer_cast<size_t>(c->second);
+  if (c != ctx->caches.end()) return *std::static_pointer_cast<Tuned>(c->second);
   const size_t field = ng_of(it.grid) * elem_bytes(prec);
   const int nt = std::min(it.N, 32);
   void* out = ctx->get("tune_out", size_t(nt) * field);
   cudaEvent_t e0, e1;
   PT_CUDA_CHECK(cudaEventCreate(&e0));
   PT_CUDA_CHECK(cudaEventCreate(&e1));
-  size_t best = ctx->scratch_budget;
+  Tuned best{ctx->scratch_budget, ctx->exchange64_engine == 1 ? 1 : 0};
   float best_ms = 1e30f;
-  int last_b = -1;
   const size_t mib = size_t(1) << 20;
   const size_t cands[] = {12 * mib, 24 * mib, 48 * mib, 96 * mib, 192 * mib, 512 * mib};
+  const bool two_engines = prec != PT_FP64 && exchange64_applies(it.grid);
+  const int saved_engine = ctx->exchange64_engine;
   try {
-    for (size_t cand : cands) {
-      // candidates that give the same pair tile are the same schedule
-      const int b = std::min(nt, int(std::floor(std::sqrt(double(std::max<size_t>(1, cand / field))))));
-      if (b == last_b) continue;
-      last_b = b;
-      ctx->budget_override = cand;
-      exchange(ctx, it.src, it.occ, nt, nullptr, nt, out, it.grid, it.kernel, prec, st);  // builds the schedule
-      PT_CUDA_CHECK(cudaEventRecord(e0, st));
-      for (int r = 0; r < 2; ++r) exchange(ctx, it.src, it.occ, nt, nullptr, nt, out, it.grid, it.kernel, prec, st);
-      PT_CUDA_CHECK(cudaEventRecord(e1, st));
-      PT_CUDA_CHECK(cudaEventSynchronize(e1));
-      float ms = 0.f;
-      PT_CUDA_CHECK(cudaEventElapsedTime(&ms, e0, e1));
-      if (ms < best_ms) {
-        best_ms = ms;
-        best = cand;
+    for (int engine = 0; engine < (two_engines ? 2 : 1); ++engine) {
+      int last_b = -1;
+      ctx->exchange64_engine = two_engines ? engine : saved_engine;
+      for (size_t cand : cands) {
+        // candidates that give the same pair tile are the same schedule
+        int b = std::min(nt, int(std::floor(std::sqrt(double(std::max<size_t>(1, cand / field))))));
+        if (two_engines && engine == 0) b = std::min(b, kExchange64MaxTile);
+        if (b == last_b) continue;
+        last_b = b;
+        ctx->budget_override = cand;
+        exchange(ctx, it.src, it.occ, nt, nullptr, nt, out, it.grid, it.kernel, prec, st);  // builds the schedule
+        PT_CUDA_CHECK(cudaEventRecord(e0, st));
+        for (int r = 0; r < 2; ++r)
+          exchange(ctx, it.src, it.occ, nt, nullptr, nt, out, it.grid, it.kernel, prec, st);
+        PT_CUDA_CHECK(cudaEventRecord(e1, st));
+        PT_CUDA_CHECK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        PT_CUDA_CHECK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = Tuned{cand, engine};
+        }
       }
     }
   } catch (...) {
     ctx->budget_override = 0;
+    ctx->exchange64_engine = saved_engine;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     throw;
   }
   ctx->budget_override = 0;
+  ctx->exchange64_engine = saved_engine;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  ctx->caches[key] = std::make_shared<size_t>(best);
+  if (!two_engines) best.engine = saved_engine;
+  ctx->caches[key] = std::make_shared<Tuned>(best);
   return best;
 }
 
-long long run_items(pt_ctx* ctx, const pt_exchange_item* items, int count, const std::vector<size_t>& budgets,
+// Items dealt to branches longest first (work ~ pair FFTs x grid points), each branch to the
+// currently lightest one; the same assignment in the eager pass and in the capture.
+std::vector<int> assign_branches(const pt_exchange_item* items, int count, int nb) {
+  std::vector<int> order(count), branch(count, 0);
+  std::vector<double> work(count), load(nb, 0.0);
+  for (int k = 0; k < count; ++k) {
+    const double m = items[k].tgt ? items[k].M : items[k].N;
+    const double pairs = items[k].tgt ? double(items[k].N) * m : 0.5 * m * (m + 1);
+    work[k] = pairs * double(ng_of(items[k].grid));
+    order[k] = k;
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work[a] > work[b]; });
+  for (int k : order) {
+    const int b = int(std::min_element(load.begin(), load.end()) - load.begin());
+    branch[k] = b;
+    load[b] += work[k];
+  }
+  return branch;
+}
+
+struct TagGuard {
+  pt_ctx* ctx;
+  int engine;
+  ~TagGuard() {
+    ctx->scratch_tag.clear();
+    ctx->budget_override = 0;
+    ctx->exchange64_engine = engine;
+  }
+};
+
+long long run_items(pt_ctx* ctx, const pt_exchange_item* items, int count, const std::vector<Tuned>& tuned,
                     pt_precision prec, cudaStream_t st) {
   long long pairs = 0;
-  for (int k = 0; k < count; ++k) {
+  TagGuard guard{ctx, ctx->exchange64_engine};
+  const int nb = std::max(1, std::min(ctx->batch_streams, count));
+  auto one = [&](int k, cudaStream_t s) {
     const pt_exchange_item& it = items[k];
-    ctx->budget_override = budgets[k];
-    pairs += exchange(ctx, it.src, it.occ, it.N, it.tgt, it.tgt ? it.M : it.N, it.out, it.grid, it.kernel, prec, st);
+    ctx->budget_override = tuned[k].budget;
+    if (prec != PT_FP64 && exchange64_applies(it.grid)) ctx->exchange64_engine = tuned[k].engine;
+    pairs += exchange(ctx, it.src, it.occ, it.N, it.tgt, it.tgt ? it.M : it.N, it.out, it.grid, it.kernel, prec, s);
+    ctx->exchange64_engine = guard.engine;
+  };
+  if (nb == 1) {
+    for (int k = 0; k < count; ++k) one(k, st);
+    return pairs;
   }
-  ctx->budget_override = 0;
+  while (int(ctx->side_streams.size()) < nb) {
+    cudaStream_t s = nullptr;
+    PT_CUDA_CHECK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    ctx->side_streams.push_back(s);
+  }
+  const std::vector<int> branch = assign_branches(items, count, nb);
+  std::vector<cudaEvent_t> ev(nb + 1, nullptr);
+  for (auto& e : ev) PT_CUDA_CHECK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  struct EvGuard {
+    std::vector<cudaEvent_t>& v;
+    ~EvGuard() {
+      for (auto e : v)
+        if (e) cudaEventDestroy(e);
+    }
+  } evg{ev};
+  PT_CUDA_CHECK(cudaEventRecord(ev[nb], st));  // fork
+  for (int b = 0; b < nb; ++b) {
+    cudaStream_t s = ctx->side_streams[b];
+    PT_CUDA_CHECK(cudaStreamWaitEvent(s, ev[nb], 0));
+    ctx->scratch_tag = "#" + std::to_string(b);
+    for (int k = 0; k < count; ++k)
+      if (branch[k] == b) one(k, s);
+    PT_CUDA_CHECK(cudaEventRecord(ev[b], s));
+  }
+  ctx->scratch_tag.clear();
+  for (int b = 0; b < nb; ++b) PT_CUDA_CHECK(cudaStreamWaitEvent(st, ev[b], 0));  // join
   return pairs;
 }
 
-std::string batch_key(const pt_exchange_item* items, int count, pt_precision prec, const std::vector<size_t>& budgets) {
-  std::string k = "graph:" + std::to_string(int(prec)) + ":" + std::to_string(count);
+std::string batch_key(const pt_exchange_item* items, int count, pt_precision prec, const std::vector<Tuned>& tuned,
+                      int streams) {
+  std::string k = "graph:" + std::to_string(int(prec)) + ":" + std::to_string(count) + ":" + std::to_string(streams);
   char b[256];
   for (int i = 0; i < count; ++i) {
     const pt_exchange_item& it = items[i];
-    snprintf(b, sizeof(b), "|%p,%p,%d,%p,%d,%p,%d,%d,%d,%.17g,%.17g,%.17g,%d,%.17g,%.17g,%zu", it.src,
+    snprintf(b, sizeof(b), "|%p,%p,%d,%p,%d,%p,%d,%d,%d,%.17g,%.17g,%.17g,%d,%.17g,%.17g,%zu,%d", it.src,
              static_cast<const void*>(it.occ), it.N, it.tgt, it.M, it.out, it.grid.nx, it.grid.ny, it.grid.nz,
-             it.grid.L[0], it.grid.L[1], it.grid.L[2], it.kernel.type, it.kernel.mu, it.kernel.g0, budgets[i]);
+             it.grid.L[0], it.grid.L[1], it.grid.L[2], it.kernel.type, it.kernel.mu, it.kernel.g0, tuned[i].budget,
+             tuned[i].engine);
     k += b;
   }
   return k;
@@ -125,11 +210,11 @@ struct DeferGuard {
 long long exchange_batched(pt_ctx* ctx, const pt_exchange_item* items, int count, pt_precision prec,
                            cudaStream_t st, size_t* graph_nodes) {
   if (graph_nodes) *graph_nodes = 0;
-  std::vector<size_t> budgets(count, ctx->scratch_budget);
+  std::vector<Tuned> tuned(count, Tuned{ctx->scratch_budget, ctx->exchange64_engine == 1 ? 1 : 0});
   if (ctx->autotune)
-    for (int k = 0; k < count; ++k) budgets[k] = tuned_budget(ctx, items[k], prec, st);
+    for (int k = 0; k < count; ++k) tuned[k] = tuned_budget(ctx, items[k], prec, st);
   int* err = static_cast<int*>(ctx->get("exchange_err", sizeof(int)));
-  const std::string key = batch_key(items, count, prec, budgets);
+  const std::string key = batch_key(items, count, prec, tuned, std::min(ctx->batch_streams, count));
   auto c = ctx->caches.find(key);
   if (ctx->use_graphs && c != ctx->caches.end()) {
     auto g = std::static_pointer_cast<GraphHolder>(c->second);
@@ -143,7 +228,7 @@ long long exchange_batched(pt_ctx* ctx, const pt_exchange_item* items, int count
     // eager pass: sizes every workspace and builds every schedule and table the capture will use
     DeferGuard dg(ctx);
     PT_CUDA_CHECK(cudaMemsetAsync(err, 0, sizeof(int), st));
-    pairs = run_items(ctx, items, count, budgets, prec, st);
+    pairs = run_items(ctx, items, count, tuned, prec, st);
   }
   exchange_check(ctx, st);
   if (!ctx->use_graphs) return pairs;
@@ -155,7 +240,7 @@ long long exchange_batched(pt_ctx* ctx, const pt_exchange_item* items, int count
     PT_CUDA_CHECK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
     try {
       PT_CUDA_CHECK(cudaMemsetAsync(err, 0, sizeof(int), ctx->cap_stream));
-      run_items(ctx, items, count, budgets, prec, ctx->cap_stream);
+      run_items(ctx, items, count, tuned, prec, ctx->cap_stream);
     } catch (...) {
       cudaGraph_t g2 = nullptr;
       cudaStreamEndCapture(ctx->cap_stream, &g2);

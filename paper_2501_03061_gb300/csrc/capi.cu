@@ -148,6 +148,7 @@ void pt_destroy(pt_ctx* ctx) {
   ctx->release_all();
   ctx->caches.clear();
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  for (cudaStream_t s : ctx->side_streams) cudaStreamDestroy(s);
   delete ctx;
 }
 
@@ -167,6 +168,11 @@ pt_status pt_trim(pt_ctx* ctx) {
 pt_status pt_set_option(pt_ctx* ctx, const char* key, double value) {
   return guarded(__func__, ctx, [&]() -> pt_status {
     if (!ctx || !key) pt::fail(PT_INVALID_ARG, "context or key is NULL");
+    if (std::string(key) == "batch_streams") {
+      if (!(value >= 1.0 && value <= 16.0)) pt::fail(PT_INVALID_ARG, "batch_streams must be in [1, 16]");
+      ctx->batch_streams = int(value);
+      return PT_OK;
+    }
     if (std::string(key) == "graphs" || std::string(key) == "autotune") {
       (std::string(key) == "graphs" ? ctx->use_graphs : ctx->autotune) = value != 0.0 ? 1 : 0;
       return PT_OK;

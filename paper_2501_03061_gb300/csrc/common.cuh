@@ -148,6 +148,10 @@ struct pt_ctx {
   size_t budget_override = 0;  // pair-field budget in force for the current batched call (0: scratch_budget)
   bool defer_checks = false;   // inside a batched call: device error words are checked once at the end
   cudaStream_t cap_stream = nullptr;  // non-default stream that graph captures are recorded on
+  int batch_streams = 4;              // option: concurrent branches (streams) of a batched exchange call
+  std::vector<cudaStream_t> side_streams;  // the branches' streams (created on first use)
+  std::string scratch_tag;            // suffix of the exchange scratch names: one set per concurrent branch
+  std::string tagged(const char* name) const { return std::string(name) + scratch_tag; }
   std::string err;
   std::map<std::string, pt::DevBuf> bufs;
   std::map<std::string, std::shared_ptr<void>> caches;  // keyed host-side caches of device tables

@@ -249,7 +249,7 @@ long long exchange_t(pt_ctx* ctx, const cx<T>* src, const double* occ, int N, co
       return sch->total_pairs;
     }
   }
-  cx<T>* scratch = static_cast<cx<T>*>(ctx->get("exchange_scratch", size_t(sch->max_pairs) * field));
+  cx<T>* scratch = static_cast<cx<T>*>(ctx->get(ctx->tagged("exchange_scratch"), size_t(sch->max_pairs) * field));
   const cx<T>* twg = static_cast<const cx<T>*>(ft.tw);
   const int nbatch = int(sch->pair_off.size()) - 1;
   if (fixed_cubic(g)) {

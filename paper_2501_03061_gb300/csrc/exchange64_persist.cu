@@ -509,9 +509,9 @@ long long exchange64_persist(pt_ctx* ctx, const c64* src, const double* occ, int
     pl = std::static_pointer_cast<PersistPlan>(it->second);
   }
   const int ring = std::min(pl->ring, std::max(1, pl->P));
-  c64* scratch = static_cast<c64*>(ctx->get("exchange64p_scratch", size_t(pl->ring) * ng * sizeof(c64)));
+  c64* scratch = static_cast<c64*>(ctx->get(ctx->tagged("exchange64p_scratch"), size_t(pl->ring) * ng * sizeof(c64)));
   const size_t ncnt = 1 + 2 * size_t(pl->P) + 2 * size_t(pl->nbatch) + size_t(pl->M) * ZH;
-  int* cnt = static_cast<int*>(ctx->get("exchange64p_counters", ncnt * sizeof(int)));
+  int* cnt = static_cast<int*>(ctx->get(ctx->tagged("exchange64p_counters"), ncnt * sizeof(int)));
   int* err = static_cast<int*>(ctx->get("exchange_err", sizeof(int)));
   PT_CUDA_CHECK(cudaMemsetAsync(cnt, 0, ncnt * sizeof(int), st));
   if (!ctx->defer_checks) PT_CUDA_CHECK(cudaMemsetAsync(err, 0, sizeof(int), st));

@@ -322,7 +322,7 @@ void exchange64_tma(pt_ctx* ctx, const ScheduleImpl& sch, const c64* src, const 
   if (sch.B > MAXB) fail(PT_INVALID_ARG, "64^3 exchange schedule tile exceeds the parameter-block capacity");
   constexpr size_t ng = size_t(G) * G * G;
   const int maxp = sch.max_pairs;
-  c64* scratch = static_cast<c64*>(ctx->get("exchange64_scratch", 4 * size_t(maxp) * ng * sizeof(c64)));
+  c64* scratch = static_cast<c64*>(ctx->get(ctx->tagged("exchange64_scratch"), 4 * size_t(maxp) * ng * sizeof(c64)));
   int* err = static_cast<int*>(ctx->get("exchange_err", sizeof(int)));
   if (!ctx->defer_checks) PT_CUDA_CHECK(cudaMemsetAsync(err, 0, sizeof(int), st));  // else zeroed once per batch
   static DeviceOnce once;  // kernel attribute and the constant twiddle table are per device

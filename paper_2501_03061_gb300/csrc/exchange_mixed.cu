@@ -107,8 +107,8 @@ long long exchange_mixed_t(pt_ctx* ctx, const cx<T>* phi, const c128* sigma, int
   } else {
     pl = std::static_pointer_cast<MixedPlan>(it->second);
   }
-  cx<T>* two = static_cast<cx<T>*>(ctx->get("mixed_src", 2 * field));  // [phi_k | sigma_ik phi_i]
-  cx<T>* scratch = static_cast<cx<T>*>(ctx->get("exchange_scratch", size_t(mb) * field));
+  cx<T>* two = static_cast<cx<T>*>(ctx->get(ctx->tagged("mixed_src"), 2 * field));  // [phi_k | sigma_ik phi_i]
+  cx<T>* scratch = static_cast<cx<T>*>(ctx->get(ctx->tagged("exchange_scratch"), size_t(mb) * field));
   const cx<T>* twg = static_cast<const cx<T>*>(ft.tw);
   const bool fixed = fixed_cubic(g);
   const GridPlan& gp = ft.plan;

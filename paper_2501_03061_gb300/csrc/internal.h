@@ -15,6 +15,8 @@ struct Term {
 // largest pair-tile side of the 64^3 TMA pipeline (its batch descriptors travel in the kernel
 // parameters: 16 bytes x (5 B^2 + 2 B) of the 32 KB parameter space)
 constexpr int kExchange64MaxTile = 16;
+// the 64^3 FP32 exchange engines apply (exchange.cu)
+bool exchange64_applies(const pt_grid& g);
 size_t exchange_scratch_budget(const pt_ctx* ctx);
 // W = V_x tgt (tgt == nullptr: tgt = src, symmetric pairs).  Returns the number of pair FFTs.
 long long exchange(pt_ctx* ctx, const void* src, const double* occ, int N, const void* tgt, int M, void* out,
