@@ -65,9 +65,10 @@ def parse():
                     help="1 (the library's default): kinetically preconditioned inner Anderson iteration "
                          "(context option ptim_precond); 0: plain Anderson")
     ap.add_argument("--anderson-depth", type=int, default=20, help="Anderson history depth of the PT-IM step")
-    ap.add_argument("--engine", type=int, default=None, choices=[0, 1, 2],
+    ap.add_argument("--engine", type=int, default=None, choices=[0, 1, 2, 3],
                     help="64^3 FP32 exchange engine: 0 launch-pipelined TMA kernel, 1 compile-time tile kernels, "
-                         "2 persistent cooperative kernel (default: the library's)")
+                         "2 persistent cooperative kernel, 3 pipelined TMA kernel with the fused CD role "
+                         "(default: the library's)")
     ap.add_argument("--x64p", type=str, default=None, help="tile,ring,lag of the persistent 64^3 engine")
     ap.add_argument("--hxc", action="store_true",
                     help="rebuild V_Hxc[rho] (Hartree + LDA) from the midpoint density in every inner iteration "

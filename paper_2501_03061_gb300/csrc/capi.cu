@@ -187,7 +187,8 @@ pt_status pt_set_option(pt_ctx* ctx, const char* key, double value) {
       return PT_OK;
     }
     if (std::string(key) == "exchange64_engine") {
-      if (!(value == 0.0 || value == 1.0 || value == 2.0)) pt::fail(PT_INVALID_ARG, "exchange64_engine is 0, 1 or 2");
+      if (!(value == 0.0 || value == 1.0 || value == 2.0 || value == 3.0))
+        pt::fail(PT_INVALID_ARG, "exchange64_engine is 0, 1, 2 or 3");
       ctx->exchange64_engine = int(value);
       return PT_OK;
     }

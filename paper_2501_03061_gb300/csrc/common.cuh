@@ -134,8 +134,9 @@ struct pt_ctx {
   double ptim_inner_cap = 1e-2;   // option: loosest inner tolerance (also that of the first outer iteration)
   int ptim_precond = 1;        // option: Anderson on the kinetically preconditioned inner map when 1
   int ptim_q_n = 0;            // the "ptim_Q" buffer holds a complete unitary ptim_q_n x ptim_q_n basis
-  // option: 64^3 FP32 exchange engine: 0 the launch-pipelined TMA kernel, 1 the compile-time tile
-  // kernels, 2 one persistent cooperative launch per application (exchange64_persist.cu)
+  // option: 64^3 FP32 exchange engine: 0 the launch-pipelined TMA kernel (roles A, B, C, D), 1 the
+  // compile-time tile kernels, 2 one persistent cooperative launch per application
+  // (exchange64_persist.cu), 3 the launch-pipelined TMA kernel with C fused into the accumulate
   int exchange64_engine = 0;
   int x64p_tile = 4;   // option: pair-tile side of the persistent engine's schedule
   int x64p_ring = 24;  // option: pair-field ring slots of the persistent engine (raised to tile pairs + 3 lag + 1)

@@ -226,7 +226,8 @@ long long exchange_t(pt_ctx* ctx, const cx<T>* src, const double* occ, int N, co
   const size_t field = ng * sizeof(cx<T>);
   // Pair batch: as many pair fields as fit a budget that keeps them L2-resident (the 64^3 TMA
   // pipeline takes its own, larger budget: see pt_ctx::tma64_budget).
-  const bool tma64 = sizeof(T) == 4 && exchange64_applies(g) && ctx->exchange64_engine == 0;
+  const bool tma64 =
+      sizeof(T) == 4 && exchange64_applies(g) && (ctx->exchange64_engine == 0 || ctx->exchange64_engine == 3);
   const size_t budget = ctx->budget_override ? ctx->budget_override
                                              : (tma64 ? ctx->tma64_budget : exchange_scratch_budget(ctx));
   int B = int(std::floor(std::sqrt(double(std::max<size_t>(1, budget / field)))));
@@ -243,8 +244,9 @@ long long exchange_t(pt_ctx* ctx, const cx<T>* src, const double* occ, int N, co
     sch = std::static_pointer_cast<ScheduleImpl>(it->second);
   }
   if constexpr (sizeof(T) == 4) {
-    if (exchange64_applies(g) && ctx->exchange64_engine == 0) {
-      exchange64_tma(ctx, *sch, src, occ, tgt, M, out, ktab, static_cast<const cx<T>*>(ft.tw), st);
+    if (exchange64_applies(g) && (ctx->exchange64_engine == 0 || ctx->exchange64_engine == 3)) {
+      exchange64_tma(ctx, *sch, src, occ, tgt, M, out, ktab, static_cast<const cx<T>*>(ft.tw), st,
+                     ctx->exchange64_engine == 3);
       if (!ctx->defer_checks) exchange_check(ctx, st);
       return sch->total_pairs;
     }

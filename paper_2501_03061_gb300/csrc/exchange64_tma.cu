@@ -42,6 +42,10 @@ struct Launch {
 
 __constant__ c64 c_tw64[G];
 
+// FUSED = false: roles A, B, C, D over four slots.  FUSED = true: roles CD, A, B over three slots,
+// where a CD CTA owns one target plane and runs C's inverse y/x transforms of each contributing
+// pair's plane itself before accumulating (see the CD role below).
+template <bool FUSED>
 __global__ void __launch_bounds__(THREADS, 2)
     k_exchange64_tma(const __grid_constant__ CUtensorMap tm_src, const __grid_constant__ CUtensorMap tm_tgt,
                      const __grid_constant__ CUtensorMap tm_plane, const __grid_constant__ CUtensorMap tm_slab,
@@ -67,6 +71,88 @@ __global__ void __launch_bounds__(THREADS, 2)
   }
   __syncthreads();
   int bid = blockIdx.x;
+
+  if constexpr (FUSED) {
+    if (bid < L.nD) {
+      // ---------------- pass CD (one target plane per CTA) ----------------
+      // For each contribution (pair slot, partner, occupation, conjugation) of target td at plane z:
+      // the pair's plane z after the z transforms arrives by TMA (double-buffered, one contribution
+      // ahead), the inverse y and x transforms run here (lane t of group y ends with v[y][t + 8k]),
+      // and d * partner * v accumulates in registers.  v_ij never leaves the SM: the C -> D round
+      // trip of the four-role pipeline (write and read of every pair field) is gone, at the price of
+      // transforming a symmetric pair's plane once for each of its two targets.  Plane-major order:
+      // all targets at one z run together, so both targets of a pair read its plane from L2.
+      const int nt = L.nD / G;
+      const int z = bid / nt;
+      const TargetDesc td = L.td[bid % nt];
+      __shared__ int s_list[2 * MAXB];
+      __shared__ int s_n;
+      if (tid == 0) {  // contributions with a nonzero occupation (a skipped pair's slot is stale)
+        int n = 0;
+        for (int i = td.cbeg; i < td.cend; ++i)
+          if (occ[L.cd[i - L.d_cbeg].occ] != 0.0) s_list[n++] = i - L.d_cbeg;
+        s_n = n;
+      }
+      __syncthreads();
+      const int n = s_n;
+      auto issue = [&](int c) {  // one thread
+        const Contrib cc = L.cd[s_list[c]];
+        const int orb = L.slotD * L.max_pairs + cc.slot;
+        const uint32_t b = uint32_t(c & 1);
+        fence_proxy_async_smem();  // the buffer was last read and written through the generic proxy
+        mbar_arrive_expect_tx(bar + 8u * b, TILE_BYTES);
+        for (int q = 0; q < 4; ++q)
+          tma_load_4d(base + b * TILE_BYTES + q * SUB_BYTES, &tm_plane, 16 * q, 0, z, orb, bar + 8u * b);
+      };
+      if (tid == 0) {
+        if (n > 0) issue(0);
+        if (n > 1) issue(1);
+      }
+      c64 acc[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) acc[k] = czero<float>();
+      const int y = grp, kx = grp;
+      for (int c = 0; c < n; ++c) {
+        const uint32_t b = uint32_t(c & 1);
+        const bool ok = mbar_wait(bar + 8u * b, uint32_t(c >> 1) & 1u, TIMEOUT_NS);
+        if (!__syncthreads_and(ok)) {
+          if (tid == 0) atomicOr(err, 16);
+          return;
+        }
+        c64 v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = *reinterpret_cast<const c64*>(sm + b * TILE_BYTES + sw_off(kx, t + 8 * q));
+        __syncthreads();  // the buffer is consumed: it becomes the group-transpose area
+        c64* gs = reinterpret_cast<c64*>(sm + b * TILE_BYTES) + grp * 64;
+        fft64_tma(v, t, gs, gpar, tw, true);  // inverse along y: lane t holds y = t + 8k
+#pragma unroll
+        for (int k = 0; k < 8; ++k) P[pidx(t + 8 * k, kx)] = v[k];
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = P[pidx(y, t + 8 * q)];
+        fft64_tma(v, t, gs, gpar, tw, true);  // inverse along x: lane t holds x = t + 8k
+        const Contrib cc = L.cd[s_list[c]];
+        const float f = float(occ[cc.occ]);
+        const c64* pp = src + size_t(cc.partner) * ng + size_t(z) * G * G + y * G;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          c64 a = v[k];
+          if (cc.conj) a.im = -a.im;
+          acc[k] = acc[k] + cmul(pp[t + 8 * k], a) * f;
+        }
+        __syncthreads();  // the buffer (transpose area) and P are free for the next contribution
+        if (tid == 0 && c + 2 < n) issue(c + 2);
+      }
+      c64* o = out + size_t(td.t) * ng + size_t(z) * G * G + y * G;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int e = t + 8 * k;
+        o[e] = td.first ? czero<float>() - acc[k] : o[e] - acc[k];
+      }
+      return;
+    }
+    bid -= L.nD;
+  }
 
   if (bid < L.nA) {
     // ---------------- pass A ----------------
@@ -160,6 +246,7 @@ __global__ void __launch_bounds__(THREADS, 2)
     return;
   }
   bid -= L.nB;
+  if constexpr (FUSED) return;
   if (bid < L.nC) {
     // ---------------- pass C (two planes per CTA: z and z + G/2) ----------------
     // The second plane loads into the B tile, unused by this role, while the first is transformed.
@@ -318,16 +405,20 @@ void encode_tmap_4d_u64(CUtensorMap* map, const void* base, const uint64_t dims[
 }
 
 void exchange64_tma(pt_ctx* ctx, const ScheduleImpl& sch, const c64* src, const double* occ, const c64* tgt, int M,
-                    c64* out, const float* ktab, const c64* tw, cudaStream_t st) {
+                    c64* out, const float* ktab, const c64* tw, cudaStream_t st, bool fused) {
   if (sch.B > MAXB) fail(PT_INVALID_ARG, "64^3 exchange schedule tile exceeds the parameter-block capacity");
   constexpr size_t ng = size_t(G) * G * G;
   const int maxp = sch.max_pairs;
-  c64* scratch = static_cast<c64*>(ctx->get(ctx->tagged("exchange64_scratch"), 4 * size_t(maxp) * ng * sizeof(c64)));
+  const int ns = fused ? 3 : 4;  // scratch slots: one per role that holds pair fields
+  c64* scratch = static_cast<c64*>(ctx->get(ctx->tagged("exchange64_scratch"), size_t(ns) * maxp * ng * sizeof(c64)));
   int* err = static_cast<int*>(ctx->get("exchange_err", sizeof(int)));
   if (!ctx->defer_checks) PT_CUDA_CHECK(cudaMemsetAsync(err, 0, sizeof(int), st));  // else zeroed once per batch
   static DeviceOnce once;  // kernel attribute and the constant twiddle table are per device
   once([] {
-    PT_CUDA_CHECK(cudaFuncSetAttribute(k_exchange64_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    PT_CUDA_CHECK(
+        cudaFuncSetAttribute(k_exchange64_tma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    PT_CUDA_CHECK(
+        cudaFuncSetAttribute(k_exchange64_tma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
     c64 h[G];
     for (int i = 0; i < G; ++i) {
       const double ang = -2.0 * M_PI * double(i) / double(G);
@@ -342,7 +433,7 @@ void exchange64_tma(pt_ctx* ctx, const ScheduleImpl& sch, const c64* src, const 
   CUtensorMap tm_src, tm_tgt, tm_plane, tm_slab;
   const uint64_t dsrc[4] = {G, G, G, uint64_t(sch.N)};
   const uint64_t dtgt[4] = {G, G, G, uint64_t(M)};
-  const uint64_t dscr[4] = {G, G, G, uint64_t(4) * maxp};
+  const uint64_t dscr[4] = {G, G, G, uint64_t(ns) * maxp};
   encode_tmap_4d_u64(&tm_src, src, dsrc, strides, plane_box, CU_TENSOR_MAP_SWIZZLE_128B);
   encode_tmap_4d_u64(&tm_tgt, tgt, dtgt, strides, plane_box, CU_TENSOR_MAP_SWIZZLE_128B);
   encode_tmap_4d_u64(&tm_plane, scratch, dscr, strides, plane_box, CU_TENSOR_MAP_SWIZZLE_128B);
@@ -354,36 +445,45 @@ void exchange64_tma(pt_ctx* ctx, const ScheduleImpl& sch, const c64* src, const 
     return np;
   };
   Launch L;
-  for (int k = 0; k < nb + 3; ++k) {
+  // launch k: A of batch k, B of batch k - 1, then C of k - 2 and D of k - 3 (four slots), or the
+  // fused CD of batch k - 2 (three slots); the roles of one launch always use distinct slots
+  for (int k = 0; k < nb + ns - 1; ++k) {
     std::memset(&L, 0, sizeof(L));
     L.max_pairs = maxp;
     if (k < nb) {
       L.nA = G * copy_pairs(L.pa, k);
-      L.slotA = k % 4;
+      L.slotA = k % ns;
     }
-    const int b = k - 1, c = k - 2, d = k - 3;
+    const int b = k - 1, c = k - 2, d = fused ? k - 2 : k - 3;
     if (b >= 0 && b < nb) {
       L.nB = (G / 2) * copy_pairs(L.pb, b);
-      L.slotB = b % 4;
+      L.slotB = b % ns;
     }
-    if (c >= 0 && c < nb) {
+    if (!fused && c >= 0 && c < nb) {
       L.nC = (G / 2) * copy_pairs(L.pc, c);
-      L.slotC = c % 4;
+      L.slotC = c % ns;
     }
-    if (d >= 0) {
+    if (d >= 0 && d < nb) {
       const int t0 = sch.tgt_off[d], nt = sch.tgt_off[d + 1] - t0;
       std::copy(sch.h_tgts.begin() + t0, sch.h_tgts.begin() + t0 + nt, L.td);
       L.d_cbeg = sch.h_tgts[t0].cbeg;
       const int cend = sch.h_tgts[t0 + nt - 1].cend;
       if (cend - L.d_cbeg > MAXC || nt > MAXT) fail(PT_INVALID_ARG, "exchange batch exceeds the parameter block");
+      for (int q = 0; q < nt; ++q)
+        if (sch.h_tgts[t0 + q].cend - sch.h_tgts[t0 + q].cbeg > 2 * MAXB)
+          fail(PT_INVALID_ARG, "exchange batch: a target has more contributions than a tile allows");
       std::copy(sch.h_contribs.begin() + L.d_cbeg, sch.h_contribs.begin() + cend, L.cd);
-      L.nD = 2 * G * nt;
-      L.slotD = d % 4;
+      L.nD = (fused ? G : 2 * G) * nt;
+      L.slotD = d % ns;
     }
     const int grid = L.nA + L.nB + L.nC + L.nD;
     if (grid == 0) continue;
-    PT_LAUNCH(k_exchange64_tma, grid, THREADS, SMEM_BYTES, st, tm_src, tm_tgt, tm_plane, tm_slab, L, src, occ, ktab,
-              scratch, out, err);
+    if (fused)
+      PT_LAUNCH(k_exchange64_tma<true>, grid, THREADS, SMEM_BYTES, st, tm_src, tm_tgt, tm_plane, tm_slab, L, src, occ,
+                ktab, scratch, out, err);
+    else
+      PT_LAUNCH(k_exchange64_tma<false>, grid, THREADS, SMEM_BYTES, st, tm_src, tm_tgt, tm_plane, tm_slab, L, src,
+                occ, ktab, scratch, out, err);
   }
 }
 

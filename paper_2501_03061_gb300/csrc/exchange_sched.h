@@ -52,8 +52,9 @@ double kernel_value(const pt_kernel& k, double G2);
 
 bool exchange64_applies(const pt_grid& g);
 // FP32 64^3 path with TMA staging; sets a device error word on a wait timeout (see exchange_check)
+// fused: the three-role form (A, B, and CD: C's inverse plane transforms inside the accumulate)
 void exchange64_tma(pt_ctx* ctx, const ScheduleImpl& sch, const c64* src, const double* occ, const c64* tgt, int M,
-                    c64* out, const float* ktab, const c64* tw, cudaStream_t st);
+                    c64* out, const float* ktab, const c64* tw, cudaStream_t st, bool fused = false);
 // FP32 64^3 path as one persistent cooperative launch (exchange64_persist.cu); returns the pair FFTs
 long long exchange64_persist(pt_ctx* ctx, const c64* src, const double* occ, int N, const c64* tgt, int M, bool sym,
                              c64* out, const float* ktab, const c64* tw, cudaStream_t st);

@@ -1,8 +1,10 @@
-"""The persistent 64^3 FP32 exchange engine (context option exchange64_engine = 2: one cooperative
+"""The alternative 64^3 FP32 exchange engines.  The persistent engine (exchange64_engine = 2: one cooperative
 launch per application, pair fields in an L2-sized ring) against the FP64 oracle and against the
 launch-pipelined engine: symmetric and general targets, ragged tiles, exact-zero occupations,
 ring slots reused many times within a call (small tiles, the smallest ring the schedule admits),
-every stage lag, and the benchmark cell's sampled targets (Sec. IV-A1, Eq. vxdiag).
+every stage lag, and the benchmark cell's sampled targets (Sec. IV-A1, Eq. vxdiag).  The fused
+engine (exchange64_engine = 3: the pipelined TMA kernel whose accumulate role runs the inverse plane
+transforms itself) against the oracle over tile sizes and on the benchmark cell.
 """
 import numpy as np
 import pytest
@@ -90,3 +92,40 @@ def test_persistent_engine_benchmark_cell_sampled_targets(ctx):
     for j in (0, 97, 319):
         ref = O.apply_exchange(w.phi, w.occ, w.phi[j:j + 1], K)[0]
         assert rel(got[j], ref) <= FP32_TOL, j
+
+
+@pytest.mark.parametrize("sym", [True, False])
+@pytest.mark.parametrize("tile", [2, 6, 16])
+def test_fused_cd_engine_matches_oracle(ctx, sym, tile):
+    """Engine 3: the launch-pipelined TMA kernel with C's inverse plane transforms fused into the
+    accumulate (three scratch slots).  Several batches of 2x2, 6x6 or 16x16 pair tiles, ragged at the
+    edge, an exact-zero occupation, separate targets."""
+    rng = np.random.default_rng(900 + 10 * tile + sym)
+    cell = synth.cubic(64, 20.5)
+    n = {2: 7, 6: 13, 16: 21}[tile]
+    src = synth.random_orbitals(rng, cell, n)
+    tgt = None if sym else synth.random_orbitals(rng, cell, {2: 3, 6: 8, 16: 18}[tile])
+    occ = np.linspace(1.0, 0.05, n)
+    occ[2] = 0.0
+    g = O.grid_of(cell)
+    ref = O.apply_exchange(src, occ, src if sym else tgt, O.exchange_kernel(g, 1, synth.SCREENED_MU))
+    ctx.set_option("exchange64_scratch_bytes", tile * tile * g.ng * 8)
+    try:
+        got = run(ctx, src, occ, tgt, cell, 3)
+    finally:
+        ctx.set_option("exchange64_scratch_bytes", 512 << 20)
+    assert rel(got, ref) <= FP32_TOL
+
+
+def test_fused_cd_engine_benchmark_cell(ctx):
+    """64^3, N = 320 with the fused engine: sampled targets against the oracle, the whole result against
+    the four-role engine."""
+    w = synth.ptim_cell128()
+    g = O.grid_of(w.cell)
+    K = O.exchange_kernel(g, 1, synth.SCREENED_MU)
+    got = run(ctx, w.phi, w.occ, None, w.cell, 3)
+    for j in (1, 200, 318):
+        ref = O.apply_exchange(w.phi, w.occ, w.phi[j:j + 1], K)[0]
+        assert rel(got[j], ref) <= FP32_TOL, j
+    four = run(ctx, w.phi, w.occ, None, w.cell, 0)
+    assert rel(got, four) <= 2e-6
