@@ -4,10 +4,11 @@
 //
 // Host runtime around the exchange kernels:
 //   * autotuner: the pair-tile size of a grid (how many pair fields one FFT batch holds, which
-//     sets the L2 footprint and the launch count) and, on 64^3 FP32 grids, the kernel family (the
-//     launch-pipelined TMA kernels or the compile-time tile kernels) are picked by timing
-//     candidates of 12 MiB to 512 MiB on the first item of that grid (its first min(N, 32)
-//     orbitals) and kept in the context;
+//     sets the L2 footprint and the launch count), on 64^3 FP32 grids the kernel family (the
+//     launch-pipelined TMA kernels or the compile-time tile kernels), and for the compile-time
+//     kernels in FP32 the CTA size of their FFT tile kernels (128, 256 or 512 threads) are picked
+//     by timing candidates (budgets of 12 MiB to 512 MiB) on the first item of that grid (its
+//     first min(N, 32) orbitals) and kept in the context;
 //   * concurrent branches: items are dealt to `batch_streams` streams (longest first, by pair
 //     FFTs x grid points), each with its own scratch buffers, forked from and joined back to the
 //     caller's stream with events, so the small items' kernels fill the tails of the large ones';
@@ -21,6 +22,7 @@
 #include <cstdio>
 #include <string>
 
+#include "fft_fixed.cuh"
 #include "internal.h"
 
 namespace pt {
@@ -45,6 +47,7 @@ std::string grid_key(const pt_grid& g, pt_precision prec) {
 struct Tuned {
   size_t budget;
   int engine;  // exchange64_engine for 64^3 FP32 grids (0 or 1); ignored elsewhere
+  int ft;      // threads per CTA of the compile-time tile kernels
 };
 
 // Pick the pair-field budget (and the 64^3 engine) for the grid of `it` by timing candidates
@@ -59,16 +62,28 @@ Tuned tuned_budget(pt_ctx* ctx, const pt_exchange_item& it, pt_precision prec, c
   cudaEvent_t e0, e1;
   PT_CUDA_CHECK(cudaEventCreate(&e0));
   PT_CUDA_CHECK(cudaEventCreate(&e1));
-  Tuned best{ctx->scratch_budget, ctx->exchange64_engine == 1 ? 1 : 0};
+  Tuned best{ctx->scratch_budget, ctx->exchange64_engine == 1 ? 1 : 0, ctx->fft_threads};
   float best_ms = 1e30f;
   const size_t mib = size_t(1) << 20;
   const size_t cands[] = {12 * mib, 24 * mib, 48 * mib, 96 * mib, 192 * mib, 512 * mib};
   const bool two_engines = prec != PT_FP64 && exchange64_applies(it.grid);
-  const int saved_engine = ctx->exchange64_engine;
+  const bool fixed = fixed_cubic(it.grid);
+  const int saved_engine = ctx->exchange64_engine, saved_ft = ctx->fft_threads;
+  struct Variant {
+    int engine, ft;
+  };
+  // the TMA pipeline (64^3 FP32 only), then the compile-time kernels with each CTA size (FP32) or 256
+  std::vector<Variant> variants;
+  if (two_engines) variants.push_back({0, saved_ft});
+  const int fts[3] = {256, 128, 512};
+  const int nft = (fixed && prec != PT_FP64) ? 3 : 1;
+  for (int q = 0; q < nft; ++q) variants.push_back({two_engines ? 1 : saved_engine, fts[q]});
   try {
-    for (int engine = 0; engine < (two_engines ? 2 : 1); ++engine) {
+    for (const Variant& var : variants) {
+      const int engine = var.engine;
       int last_b = -1;
-      ctx->exchange64_engine = two_engines ? engine : saved_engine;
+      ctx->exchange64_engine = engine;
+      ctx->fft_threads = var.ft;
       for (size_t cand : cands) {
         // candidates that give the same pair tile are the same schedule
         int b = std::min(nt, int(std::floor(std::sqrt(double(std::max<size_t>(1, cand / field))))));
@@ -86,19 +101,21 @@ Tuned tuned_budget(pt_ctx* ctx, const pt_exchange_item& it, pt_precision prec, c
         PT_CUDA_CHECK(cudaEventElapsedTime(&ms, e0, e1));
         if (ms < best_ms) {
           best_ms = ms;
-          best = Tuned{cand, engine};
+          best = Tuned{cand, engine, var.ft};
         }
       }
     }
   } catch (...) {
     ctx->budget_override = 0;
     ctx->exchange64_engine = saved_engine;
+    ctx->fft_threads = saved_ft;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     throw;
   }
   ctx->budget_override = 0;
   ctx->exchange64_engine = saved_engine;
+  ctx->fft_threads = saved_ft;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (!two_engines) best.engine = saved_engine;
@@ -128,25 +145,28 @@ std::vector<int> assign_branches(const pt_exchange_item* items, int count, int n
 
 struct TagGuard {
   pt_ctx* ctx;
-  int engine;
+  int engine, ft;
   ~TagGuard() {
     ctx->scratch_tag.clear();
     ctx->budget_override = 0;
     ctx->exchange64_engine = engine;
+    ctx->fft_threads = ft;
   }
 };
 
 long long run_items(pt_ctx* ctx, const pt_exchange_item* items, int count, const std::vector<Tuned>& tuned,
                     pt_precision prec, cudaStream_t st) {
   long long pairs = 0;
-  TagGuard guard{ctx, ctx->exchange64_engine};
+  TagGuard guard{ctx, ctx->exchange64_engine, ctx->fft_threads};
   const int nb = std::max(1, std::min(ctx->batch_streams, count));
   auto one = [&](int k, cudaStream_t s) {
     const pt_exchange_item& it = items[k];
     ctx->budget_override = tuned[k].budget;
     if (prec != PT_FP64 && exchange64_applies(it.grid)) ctx->exchange64_engine = tuned[k].engine;
+    ctx->fft_threads = tuned[k].ft;
     pairs += exchange(ctx, it.src, it.occ, it.N, it.tgt, it.tgt ? it.M : it.N, it.out, it.grid, it.kernel, prec, s);
     ctx->exchange64_engine = guard.engine;
+    ctx->fft_threads = guard.ft;
   };
   if (nb == 1) {
     for (int k = 0; k < count; ++k) one(k, st);
@@ -187,10 +207,10 @@ std::string batch_key(const pt_exchange_item* items, int count, pt_precision pre
   char b[256];
   for (int i = 0; i < count; ++i) {
     const pt_exchange_item& it = items[i];
-    snprintf(b, sizeof(b), "|%p,%p,%d,%p,%d,%p,%d,%d,%d,%.17g,%.17g,%.17g,%d,%.17g,%.17g,%zu,%d", it.src,
+    snprintf(b, sizeof(b), "|%p,%p,%d,%p,%d,%p,%d,%d,%d,%.17g,%.17g,%.17g,%d,%.17g,%.17g,%zu,%d,%d", it.src,
              static_cast<const void*>(it.occ), it.N, it.tgt, it.M, it.out, it.grid.nx, it.grid.ny, it.grid.nz,
              it.grid.L[0], it.grid.L[1], it.grid.L[2], it.kernel.type, it.kernel.mu, it.kernel.g0, tuned[i].budget,
-             tuned[i].engine);
+             tuned[i].engine, tuned[i].ft);
     k += b;
   }
   return k;
@@ -210,7 +230,7 @@ struct DeferGuard {
 long long exchange_batched(pt_ctx* ctx, const pt_exchange_item* items, int count, pt_precision prec,
                            cudaStream_t st, size_t* graph_nodes) {
   if (graph_nodes) *graph_nodes = 0;
-  std::vector<Tuned> tuned(count, Tuned{ctx->scratch_budget, ctx->exchange64_engine == 1 ? 1 : 0});
+  std::vector<Tuned> tuned(count, Tuned{ctx->scratch_budget, ctx->exchange64_engine == 1 ? 1 : 0, ctx->fft_threads});
   if (ctx->autotune)
     for (int k = 0; k < count; ++k) tuned[k] = tuned_budget(ctx, items[k], prec, st);
   int* err = static_cast<int*>(ctx->get("exchange_err", sizeof(int)));

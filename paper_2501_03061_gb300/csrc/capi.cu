@@ -168,6 +168,11 @@ pt_status pt_trim(pt_ctx* ctx) {
 pt_status pt_set_option(pt_ctx* ctx, const char* key, double value) {
   return guarded(__func__, ctx, [&]() -> pt_status {
     if (!ctx || !key) pt::fail(PT_INVALID_ARG, "context or key is NULL");
+    if (std::string(key) == "fft_threads") {
+      if (!(value == 128.0 || value == 256.0 || value == 512.0)) pt::fail(PT_INVALID_ARG, "fft_threads is 128, 256 or 512");
+      ctx->fft_threads = int(value);
+      return PT_OK;
+    }
     if (std::string(key) == "batch_streams") {
       if (!(value >= 1.0 && value <= 16.0)) pt::fail(PT_INVALID_ARG, "batch_streams must be in [1, 16]");
       ctx->batch_streams = int(value);

@@ -150,6 +150,7 @@ struct pt_ctx {
   bool defer_checks = false;   // inside a batched call: device error words are checked once at the end
   cudaStream_t cap_stream = nullptr;  // non-default stream that graph captures are recorded on
   int batch_streams = 4;              // option: concurrent branches (streams) of a batched exchange call
+  int fft_threads = 256;              // option: threads per CTA of the compile-time exchange tile kernels
   std::vector<cudaStream_t> side_streams;  // the branches' streams (created on first use)
   std::string scratch_tag;            // suffix of the exchange scratch names: one set per concurrent branch
   std::string tagged(const char* name) const { return std::string(name) + scratch_tag; }

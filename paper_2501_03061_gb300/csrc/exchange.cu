@@ -260,7 +260,7 @@ long long exchange_t(pt_ctx* ctx, const cx<T>* src, const double* occ, int N, co
       const int p0 = sch->pair_off[b], np = sch->pair_off[b + 1] - p0;
       const int t0 = sch->tgt_off[b], nt = sch->tgt_off[b + 1] - t0;
       exchange_batch_fixed<T>(g.nx, src, tgt, occ, sch->d_pairs + p0, np, sch->d_tgts + t0, nt, sch->d_contribs,
-                              ktab, twg, scratch, out, st);
+                              ktab, twg, scratch, out, st, ctx->fft_threads);
     }
     return sch->total_pairs;
   }

@@ -44,10 +44,11 @@ void exchange_batch_generic(const GridPlan& gp, const cx<T>* src, const cx<T>* t
                             const PairDesc* pairs, int np, const TargetDesc* tgts, int nt, const Contrib* contribs,
                             const T* ktab, const cx<T>* tw, cx<T>* scratch, cx<T>* out, cudaStream_t st);
 // the same passes with compile-time FFT kernels for a cubic grid of side n (fixed_cubic)
+// (ft: threads per CTA of the tile kernels, 256, or in FP32 also 128 or 512)
 template <class T>
 void exchange_batch_fixed(int n, const cx<T>* src, const cx<T>* tgt, const double* occ, const PairDesc* pairs, int np,
                           const TargetDesc* tgts, int nt, const Contrib* contribs, const T* ktab, const cx<T>* tw,
-                          cx<T>* scratch, cx<T>* out, cudaStream_t st);
+                          cx<T>* scratch, cx<T>* out, cudaStream_t st, int ft = 256);
 double kernel_value(const pt_kernel& k, double G2);
 
 bool exchange64_applies(const pt_grid& g);

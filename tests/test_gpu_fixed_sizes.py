@@ -61,3 +61,28 @@ def test_apply_H_cubic_side(ctx, n, precision):
     ref = O.apply_H(psi, v, g, 5.0, 0.25, -psi)
     assert rel(out.cpu().numpy().astype(np.complex128), ref) <= (1e-11 if precision == "fp64" else 1e-5)
     ace.close()
+
+
+@pytest.mark.parametrize("ft", [128, 512])
+@pytest.mark.parametrize("n", SIDES + [24])
+def test_exchange_cubic_side_fp32_cta_sizes(ctx, n, ft):
+    """The FP32 compile-time exchange kernels with 128 or 512 threads per CTA (the batched form's
+    autotuner chooses among 128, 256 and 512 per grid) against the oracle, in several pair batches.
+    64^3 runs the compile-time kernels (engine 1) instead of the TMA pipeline here."""
+    rng = np.random.default_rng(700 + n + ft)
+    cell = synth.cubic(n, 0.32 * n)
+    phi = synth.random_orbitals(rng, cell, 5, ecut=4.0)
+    occ = np.array([1.0, 0.6, 0.0, 0.3, 0.9])
+    g = O.grid_of(cell)
+    ref = O.apply_exchange(phi, occ, phi, O.exchange_kernel(g, 1, synth.SCREENED_MU))
+    ctx.set_option("fft_threads", ft)
+    ctx.set_option("exchange64_engine", 1)
+    ctx.set_option("scratch_bytes", 4 * g.ng * 8)  # 2 x 2 pair tiles: several batches
+    try:
+        out = ctx.apply_exchange(dev(phi.astype(np.complex64)), dev(occ), cell=cell,
+                                 kernel={"type": 1, "mu": synth.SCREENED_MU}, precision="fp32")
+    finally:
+        ctx.set_option("fft_threads", 256)
+        ctx.set_option("exchange64_engine", 0)
+        ctx.set_option("scratch_bytes", 512 << 20)
+    assert rel(out.cpu().numpy().astype(np.complex128), ref) <= 1e-5
