@@ -66,6 +66,14 @@ def parse():
                     help="1 (the library's default): kinetically preconditioned inner Anderson iteration "
                          "(context option ptim_precond); 0: plain Anderson")
     ap.add_argument("--anderson-depth", type=int, default=20, help="Anderson history depth of the PT-IM step")
+    ap.add_argument("--anderson-beta", type=float, default=1.0, help="Anderson mixing parameter of the PT-IM step")
+    ap.add_argument("--ace-warm", type=int, default=1, choices=[0, 1],
+                    help="1 (the library's default): a chained step's first outer pass reuses the previous "
+                         "step's ACE operator (context option ptim_ace_warm); 0: every step builds its own")
+    ap.add_argument("--inner-kappa", type=float, default=None,
+                    help="inner tolerance factor of the PT-IM step (context option ptim_inner_kappa)")
+    ap.add_argument("--inner-cap", type=float, default=None,
+                    help="loosest inner tolerance of the PT-IM step (context option ptim_inner_cap)")
     ap.add_argument("--engine", type=int, default=None, choices=[0, 1, 2, 3],
                     help="64^3 FP32 exchange engine: 0 launch-pipelined TMA kernel, 1 compile-time tile kernels, "
                          "2 persistent cooperative kernel, 3 pipelined TMA kernel with the fused CD role "
@@ -840,6 +848,11 @@ def run_gb300(args):
     ctx = api.Context(local)
     ctx.set_option("tc_gram", args.tc_gram)
     ctx.set_option("ptim_precond", args.precond)
+    ctx.set_option("ptim_ace_warm", args.ace_warm)
+    if args.inner_kappa is not None:
+        ctx.set_option("ptim_inner_kappa", args.inner_kappa)
+    if args.inner_cap is not None:
+        ctx.set_option("ptim_inner_cap", args.inner_cap)
     apply_engine_options(ctx, args)
     phi = phi0.to(devc)
     sigma = sig0.to(devc)
@@ -850,8 +863,8 @@ def run_gb300(args):
     if args.field:
         workload = workload.replace("_step_", "_field_step_")
     kw = dict(cell=w.cell, kernel=w.kernel, precision=args.precision, dt=0.5, alpha=0.25, ecut=10.0,
-              tol=args.tol, max_outer=20, max_inner=100, anderson_depth=args.anderson_depth, hxc=args.hxc,
-              allow_unconverged=True)
+              tol=args.tol, max_outer=20, max_inner=100, anderson_depth=args.anderson_depth,
+              anderson_beta=args.anderson_beta, hxc=args.hxc, allow_unconverged=True)
     stream = torch.cuda.current_stream()
     # sin^2-enveloped pulse (omega = 0.057 Ha, 800 nm; 20 fs envelope), started at its peak region
     pulse_T, pulse_w, t_clock = 826.0, 0.057, [413.0]
@@ -1040,6 +1053,8 @@ def run_gb300(args):
                        "inner_iteration": ("Anderson on the kinetically preconditioned map" if args.precond
                                            else "Anderson on T(x) - x"),
                        "anderson_depth": args.anderson_depth,
+                       "ace_operator": ("the first outer pass of a chained step reuses the previous step's ACE "
+                                        "operator" if args.ace_warm else "every step builds its own"),
                        "local_potential": ("V_loc + V_Hxc[rho_h] (Hartree + LDA), rebuilt every inner iteration"
                                            if args.hxc else "V_loc (V_ext + V_Hxc frozen)"),
                        "field": ({"gauge": "velocity", "A0": args.field, "omega_Ha": pulse_w, "envelope_au": pulse_T,
@@ -1053,7 +1068,7 @@ def run_gb300(args):
             "outer_per_step": sum(s["outer"] for s in stats) / len(stats),
             "inner_per_step": sum(s["inner"] for s in stats) / len(stats),
             "iterations": [{"outer": s["outer"], "inner": s["inner"], "residual": _finite(s["residual"]),
-                            "converged": s["converged"], "eig_sweeps": s["eig_sweeps"],
+                            "converged": s["converged"], "eig_sweeps": s["eig_sweeps"], "ace_warm": s["ace_warm"],
                             "total_energy_in": _finite(s.get("total_energy")),
                             "orth_error": _finite(s.get("orth_error"))} for s in stats],
             "phases_ms_per_step": {k: sum(s["phase_ms"][k] for s in stats) / len(stats)

@@ -113,6 +113,12 @@ pt_status pt_trim(pt_ctx* ctx);
  *                    the fixed point (the step's result) is unchanged; the iteration needs fewer
  *                    steps (64^3 grid, N = 320: 39 inner iterations per step against 46-47).
  *                    Default 1; 0: plain Anderson on T(x) - x.
+ *   "ptim_ace_warm"  1: when a step's input (phi, sigma) is exactly the output of the context's
+ *                    previous step (same sizes, grid, kernel, precision; checked by a fingerprint),
+ *                    its first outer pass solves its loose inner problem with that step's last ACE
+ *                    operator instead of building one, saving an exchange application; the operators
+ *                    the step builds and its stopping test are unchanged (64^3 grid, N = 320: 3 ACE
+ *                    builds per step against 4).  total_energy is NaN for such steps.  Default 1.
  *   "scratch_bytes"  bytes of pair/orbital fields one FFT batch may hold (default 512 MiB: the
  *                    cost per pair falls with the pair tile even past L2 residency, 4-10% from
  *                    48 MiB to 512 MiB; smaller values give more, smaller batches).
@@ -332,6 +338,8 @@ typedef struct {
                                from the first iteration, where the midpoint is (Phi_n, sigma_n) */
   int pure_state;           /* 1 when sigma_n = c I exactly (c real): the pure-state path ran (Eq.
                                pure_vx: no sigma eigensolve, rotation or commutator; sigma_{n+1} = c I) */
+  int ace_warm;             /* 1 when the first outer pass used the previous step's ACE operator
+                               (option "ptim_ace_warm"); total_energy is then NaN */
 } pt_ptim_stats;
 
 /* One PT-IM(-ACE) step from (phi, sigma) = (Phi_n, sigma_n) to (Phi_{n+1}, sigma_{n+1}),

@@ -422,7 +422,7 @@ class Context:
                 "exch_energy": s.exch_energy, "orth_error": s.orth_error, "converged": bool(s.converged),
                 "pair_ffts": int(s.pair_ffts), "exchange_calls": int(s.exchange_calls),
                 "exchange_ms": float(s.exchange_ms), "eig_sweeps": int(s.eig_sweeps),
-                "total_energy": float(s.total_energy), "pure_state": bool(s.pure_state),
+                "total_energy": float(s.total_energy), "pure_state": bool(s.pure_state), "ace_warm": bool(s.ace_warm),
                 "phase_ms": {n: float(s.phase_ms[i]) for i, n in enumerate(L.PHASES)}}
 
 

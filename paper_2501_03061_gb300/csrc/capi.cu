@@ -56,6 +56,7 @@ void pt_ctx::release_all() {
   held = 0;
   tc_err_clean = false;
   ptim_q_n = 0;
+  ptim_warm_valid = false;  // "ptim_xi" is freed
   // captured graphs hold pointers into the freed workspace
   for (auto it = caches.begin(); it != caches.end();) {
     if (it->first.rfind("graph:", 0) == 0) it = caches.erase(it);
@@ -189,6 +190,10 @@ pt_status pt_set_option(pt_ctx* ctx, const char* key, double value) {
     }
     if (std::string(key) == "ptim_precond") {
       ctx->ptim_precond = value != 0.0 ? 1 : 0;
+      return PT_OK;
+    }
+    if (std::string(key) == "ptim_ace_warm") {
+      ctx->ptim_ace_warm = value != 0.0 ? 1 : 0;
       return PT_OK;
     }
     if (std::string(key) == "exchange64_engine") {

@@ -114,6 +114,40 @@ __global__ void k_pure_check(const c128* __restrict__ sig, int N, double* __rest
   }
 }
 
+// Fingerprint of a state (phi, sigma): sum_e w(e) (re_e + 3 im_e) with hashed weights w in [0.5, 1.5),
+// over a fixed grid and a fixed reduction order, so that equal states give bit-equal sums.  Stage 1:
+// one partial per block; stage 2 (one block) sums the partials in order.
+constexpr int FP_BLOCKS = 256;
+__device__ __forceinline__ double fp_weight(size_t e) {
+  uint64_t h = uint64_t(e) * 0x9E3779B97F4A7C15ull;
+  h ^= h >> 31;
+  h *= 0xBF58476D1CE4E5B9ull;
+  h ^= h >> 29;
+  return 0.5 + double(h >> 11) * (1.0 / 9007199254740992.0);
+}
+template <class T>
+__global__ void __launch_bounds__(256) k_fingerprint(const cx<T>* __restrict__ a, size_t n, double* __restrict__ part) {
+  double s = 0.0;
+  for (size_t e = size_t(blockIdx.x) * 256 + threadIdx.x; e < n; e += size_t(FP_BLOCKS) * 256)
+    s += fp_weight(e) * (double(a[e].re) + 3.0 * double(a[e].im));
+  for (int o = 16; o; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  __shared__ double sh[8];
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int w = 0; w < 8; ++w) r += sh[w];
+    part[blockIdx.x] = r;
+  }
+}
+__global__ void k_fingerprint_sum(const double* __restrict__ part, double* __restrict__ out) {
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int b = 0; b < FP_BLOCKS; ++b) r += part[b];
+    out[0] = r;
+  }
+}
+
 __global__ void k_fill(double* __restrict__ d, int n, const double* __restrict__ v) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) d[e] = v[0];
 }
@@ -297,6 +331,31 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
     pure = h[0] == 0.0;
     if (pure) PT_LAUNCH(k_fill, std::max(1, (N + 255) / 256), 256, 0, st, d, N, dsc + 1);  // d_i = c
   }
+  // Warm start of the ACE operator (option ptim_ace_warm): when this step's input is exactly the
+  // output of the context's previous step (same sizes, grid, kernel and precision, equal fingerprint
+  // of (phi, sigma)), "ptim_xi" still holds that step's last ACE operator, built at a midpoint near
+  // this step's first one.  The first outer pass then solves its loose inner problem with it instead
+  // of paying an exchange application; the operators this step builds, the anchors they define and
+  // the stopping test are unchanged, so the fixed point is the same.
+  char warm_key[256];
+  snprintf(warm_key, sizeof(warm_key), "%d:%d:%d:%d:%.17g:%.17g:%.17g:%d:%.17g:%.17g:%d", N, g.nx, g.ny, g.nz,
+           g.L[0], g.L[1], g.L[2], kern.type, kern.mu, kern.g0, int(prec));
+  double* fpd = static_cast<double*>(S.buf("ptim_fingerprint", (2 * FP_BLOCKS + 2) * sizeof(double)));
+  auto fingerprint = [&](const cx<T>* ph, const c128* sg, double out[2]) {
+    PT_LAUNCH(k_fingerprint<T>, FP_BLOCKS, 256, 0, st, ph, S.n1, fpd);
+    PT_LAUNCH(k_fingerprint_sum, 1, 32, 0, st, fpd, fpd + 2 * FP_BLOCKS);
+    PT_LAUNCH(k_fingerprint<double>, FP_BLOCKS, 256, 0, st, sg, S.n2, fpd + FP_BLOCKS);
+    PT_LAUNCH(k_fingerprint_sum, 1, 32, 0, st, fpd + FP_BLOCKS, fpd + 2 * FP_BLOCKS + 1);
+    PT_CUDA_CHECK(cudaMemcpyAsync(out, fpd + 2 * FP_BLOCKS, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    PT_CUDA_CHECK(cudaStreamSynchronize(st));
+  };
+  bool ace_warm = false;
+  if (ctx->ptim_ace_warm && P.use_ace && ctx->ptim_warm_valid && ctx->ptim_warm_key == warm_key) {
+    double f[2];
+    fingerprint(phin, sign, f);
+    ace_warm = f[0] == ctx->ptim_warm_fp[0] && f[1] == ctx->ptim_warm_fp[1];
+  }
+  ctx->ptim_warm_valid = false;  // "ptim_xi" is about to change; valid again only after a finished step
 
   pt_ptim_stats stv;
   std::memset(&stv, 0, sizeof(stv));
@@ -413,6 +472,9 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
         }
       } else {
         inner_tol = kappa > 0.0 ? std::max(P.tol, cap) : P.tol;
+        // warm start: a pre-pass with the previous step's operator; no anchor is set, so the next
+        // outer iteration builds this step's first operator at the improved midpoint
+        if (outer == 0 && ace_warm) rebuild = false;
       }
       if (rebuild) {
         PT_CUDA_CHECK(cudaMemcpyAsync(aphi, phih, fb, cudaMemcpyDeviceToDevice, st));
@@ -525,7 +587,8 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
           for (size_t r = 0; r < S.ng; ++r) rv += e_rho[r] * (e_vt[r] - e_vl[r]);
           e += S.dV * (eh + exc - rv);
         }
-        stv.total_energy = e;
+        // with a warm-started operator the first iteration's exchange is not exact at (Phi_n, sigma_n)
+        stv.total_energy = ace_warm ? NAN : e;
       }
       if (h_info) fail(PT_NOT_PD, "PT-IM: overlap of the midpoint orbitals is not positive definite");
       const double res = std::sqrt(rr / xx);
@@ -655,6 +718,12 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
   }
   stv.converged = converged ? 1 : 0;
   stv.pure_state = pure ? 1 : 0;
+  stv.ace_warm = ace_warm ? 1 : 0;
+  if (ctx->ptim_ace_warm && P.use_ace && stv.outer > 0) {
+    fingerprint(phi, sig, ctx->ptim_warm_fp);
+    ctx->ptim_warm_key = warm_key;
+    ctx->ptim_warm_valid = true;
+  }
   if (stats) *stats = stv;
   warm_guard.done = true;
   restore.armed = false;
