@@ -881,7 +881,17 @@ def run_gb300(args):
         if world > 1:
             dist.barrier()
 
-    for _ in range(args.warmup):
+    def pinned_copy(t):
+        h = torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
+        h.copy_(t)
+        return h
+
+    snap = None
+    for wi in range(args.warmup):
+        if wi == args.warmup - 1 and not args.no_e2e:
+            # the last warm-up step's input and field clock: the end-to-end run below replays the
+            # timed steps from it through host memory
+            snap = (pinned_copy(phi), pinned_copy(sigma), t_clock[0])
         ctx.ptim_step(phi, sigma, vloc, **step_kw())
     torch.cuda.synchronize()
 
@@ -933,34 +943,51 @@ def run_gb300(args):
     e2e = None
     if not args.no_e2e:
         # a propagation through the public API with the state on the host between steps: each step's
-        # input is copied up from pinned memory and its output copied back, then fed to the next step
-        hphi = phi.cpu().pin_memory()
-        hsig = sigma.cpu().pin_memory()
-        hv = vloc0.pin_memory()
-        ophi = torch.empty_like(hphi).pin_memory()
-        osig = torch.empty_like(hsig).pin_memory()
-        barrier()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        e2e_stats = []
-        for _ in range(args.steps):
+        # input is copied up from pinned memory and its output copied back, then fed to the next step.
+        # It replays the timed loop's steps: one untimed step from the last warm-up step's input
+        # brings the state (and the context's chained-step operator) to where the timed loop began.
+        hphi, hsig, t_clock[0] = snap
+        hv = pinned_copy(vloc0)
+        ophi = torch.empty(hphi.shape, dtype=hphi.dtype, pin_memory=True)
+        osig = torch.empty(hsig.shape, dtype=hsig.dtype, pin_memory=True)
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps + 1)]
+
+        def e2e_step(e):
+            # device-side split: upload, the PT-IM step, download (events on the stream every copy
+            # and the step run on)
+            nonlocal hphi, ophi, hsig, osig
+            e[0].record()
             dphi = hphi.to(devc, non_blocking=True)
             dsig = hsig.to(devc, non_blocking=True)
             dv = hv.to(devc, non_blocking=True)
-            e2e_stats.append(ctx.ptim_step(dphi, dsig, dv, **step_kw()))
+            e[1].record()
+            st_ = ctx.ptim_step(dphi, dsig, dv, **step_kw())
+            e[2].record()
             ophi.copy_(dphi, non_blocking=True)
             osig.copy_(dsig, non_blocking=True)
+            e[3].record()
             torch.cuda.current_stream().synchronize()
             hphi, ophi = ophi, hphi
             hsig, osig = osig, hsig
+            return st_
+
+        e2e_step(ev[args.steps])
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_stats = [e2e_step(ev[s_i]) for s_i in range(args.steps)]
         torch.cuda.synchronize()
         te, e2e_value = replicas.job_throughput(time.perf_counter() - t0, args.steps, devc)
+        ev = ev[:args.steps]
         e2e = {"value": e2e_value, "unit": UNIT,
                "h2d_bytes_per_step": int(hphi.numel() * hphi.element_size() + hsig.numel() * 16 + hv.numel() * 8),
                "d2h_bytes_per_step": int(ophi.numel() * ophi.element_size() + osig.numel() * 16),
                "outer_per_step": sum(x["outer"] for x in e2e_stats) / len(e2e_stats),
                "inner_per_step": sum(x["inner"] for x in e2e_stats) / len(e2e_stats),
-               "note": "the propagation continues from the timed steps' state, through the host"}
+               "device_ms_per_step": {k: round(sum(e[a].elapsed_time(e[b]) for e in ev) / len(ev), 2)
+                                      for k, a, b in (("h2d", 0, 1), ("step", 1, 2), ("d2h", 2, 3))},
+               "ace_warm_steps": sum(1 for x in e2e_stats if x.get("ace_warm")),
+               "note": "the timed steps replayed from the same state, through pinned host memory"}
 
     # ---- plain FP64 GPU form: the same PT-IM step in FP64 (the metric's speedup denominator) ----
     fp64_step = None
@@ -1069,7 +1096,7 @@ def run_gb300(args):
             "inner_per_step": sum(s["inner"] for s in stats) / len(stats),
             "iterations": [{"outer": s["outer"], "inner": s["inner"], "residual": _finite(s["residual"]),
                             "converged": s["converged"], "eig_sweeps": s["eig_sweeps"], "ace_warm": s["ace_warm"],
-                            "total_energy_in": _finite(s.get("total_energy")),
+                            "pass_inner": s["pass_inner"], "total_energy_in": _finite(s.get("total_energy")),
                             "orth_error": _finite(s.get("orth_error"))} for s in stats],
             "phases_ms_per_step": {k: sum(s["phase_ms"][k] for s in stats) / len(stats)
                                    for k in stats[0]["phase_ms"]},

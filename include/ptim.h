@@ -340,6 +340,9 @@ typedef struct {
                                pure_vx: no sigma eigensolve, rotation or commutator; sigma_{n+1} = c I) */
   int ace_warm;             /* 1 when the first outer pass used the previous step's ACE operator
                                (option "ptim_ace_warm"); total_energy is then NaN */
+  int passes;               /* inner loops run: one per ACE operator built, plus the warm-started
+                               first pass and any pass that kept the operator to finish at tol */
+  int pass_inner[16];       /* inner iterations of each of the first 16 passes */
 } pt_ptim_stats;
 
 /* One PT-IM(-ACE) step from (phi, sigma) = (Phi_n, sigma_n) to (Phi_{n+1}, sigma_{n+1}),

@@ -423,6 +423,7 @@ class Context:
                 "pair_ffts": int(s.pair_ffts), "exchange_calls": int(s.exchange_calls),
                 "exchange_ms": float(s.exchange_ms), "eig_sweeps": int(s.eig_sweeps),
                 "total_energy": float(s.total_energy), "pure_state": bool(s.pure_state), "ace_warm": bool(s.ace_warm),
+                "pass_inner": [int(s.pass_inner[i]) for i in range(min(int(s.passes), 16))],
                 "phase_ms": {n: float(s.phase_ms[i]) for i, n in enumerate(L.PHASES)}}
 
 

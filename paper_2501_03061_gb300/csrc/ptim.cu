@@ -446,6 +446,16 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
   // throughout.
   const double kappa = ctx->ptim_inner_kappa, cap = ctx->ptim_inner_cap;
   double inner_tol = P.tol;
+  // relative distance of the midpoint (phih, sigh) from the anchor (aphi, asig) the operator was
+  // built on; the difference goes to W and T1 (free outside the build and the commutator), so the
+  // anchor itself is kept
+  auto anchor_distance = [&]() {
+    PT_LAUNCH(k_diff<T>, sblocks, nthreads, 0, st, W, phih, aphi, S.n1);
+    PT_LAUNCH(k_diff<double>, sblocks2, nthreads, 0, st, T1, sigh, asig, S.n2);
+    double ch = 0, nr = 0;
+    S.norm2_pair(W, T1, phih, sigh, &ch, &nr);
+    return std::sqrt(ch / nr);
+  };
   const int max_outer = P.use_ace ? P.max_outer : 1;
   int aces = 0;
   for (int outer = 0; outer < max_outer && !converged; ++outer) {
@@ -453,11 +463,7 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
     if (P.use_ace) {
       bool rebuild = true;
       if (have_anchor) {
-        PT_LAUNCH(k_diff<T>, sblocks, nthreads, 0, st, aphi, phih, aphi, S.n1);
-        PT_LAUNCH(k_diff<double>, sblocks2, nthreads, 0, st, asig, sigh, asig, S.n2);
-        double ch = 0, nr = 0;
-        S.norm2_pair(aphi, asig, phih, sigh, &ch, &nr);
-        const double delta = std::sqrt(ch / nr);
+        const double delta = anchor_distance();
         if (delta < P.tol) {
           if (inner_conv) {
             converged = true;
@@ -491,10 +497,12 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
     }
     // ---- inner Anderson loop ----
     inner_conv = false;
+    const int pass = stv.passes++;
     int next_slot = 0;
     std::vector<int> order;  // active history slots, oldest first
     for (int inner = 0; inner < P.max_inner; ++inner) {
       stv.inner++;
+      if (pass < 16) stv.pass_inner[pass]++;
       const bool first = stv.inner == 1;
       cx<T>* rphi = rphi_buf[inner & 1];
       c128* rsig = rsig_buf[inner & 1];
@@ -595,9 +603,17 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
       stv.residual = res;
       if (!std::isfinite(res)) fail(PT_NONFINITE, "PT-IM residual is not finite");
       if (res < inner_tol) {
-        tm.end();
-        inner_conv = res < P.tol;
-        break;
+        const bool at_tol = res < P.tol;
+        // Loose tolerance met.  When the midpoint is still within tol of the anchor, the outer
+        // check that follows would keep the operator and finish the inner solve to tol: do that
+        // here, going on from this iteration's residual instead of recomputing it in a new loop
+        if (!at_tol && P.use_ace && have_anchor && anchor_distance() < P.tol) {
+          inner_tol = P.tol;
+        } else {
+          tm.end();
+          inner_conv = at_tol;
+          break;
+        }
       }
       // kinetic preconditioning: Anderson then solves x = x + M (T(x) - x), same fixed point
       if (ctx->ptim_precond) precondition_residual(ctx, rphi, N, A, P.dt, P.ecut, g, prec, st, P.A);
