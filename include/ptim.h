@@ -129,7 +129,10 @@ pt_status pt_trim(pt_ctx* ctx);
  *                    the tensor cores with a 3-product TF32 split (hi*hi + hi*lo + lo*hi) that
  *                    keeps FP32-level accuracy; 0 (default): CUDA cores.
  *   "tc_period"      K stages of 32 floats the tensor-core Gram accumulates in TMEM between
- *                    readouts into compensated registers (1..64, default 2). */
+ *                    readouts into compensated registers (1..64, default 2).
+ *   "tc_gram_wide"   1 (default): tensor-core Grams with more than 64 right-hand orbitals use
+ *                    64 x 128 tiles, and the PT-IM step computes <Phi|H Phi> and <Phi|Phi> in
+ *                    one pass over Phi; 0: 64 x 64 tiles, one Gram at a time. */
 pt_status pt_set_option(pt_ctx* ctx, const char* key, double value);
 
 /* ---- Fock exchange (Sec. IV-A1, Eq. vxdiag; Alg. 2 with sigma diagonalised) ------------ */

@@ -320,7 +320,10 @@ void gram(pt_ctx* ctx, const cx<T>* A, const cx<T>* B, int N1, int N2, size_t ng
       return;
     }
     if (ctx->active_tc && gram_tc_applies(A, B, ng)) {
-      gram_tc(ctx, A, B, N1, N2, ng, scale, C, st, herm, ctx->active_tc == 1);
+      if (ctx->tc_gram_wide && N2 > 64)
+        gram_tc_wide(ctx, A, B, C, nullptr, nullptr, N1, N2, ng, scale, st, herm, ctx->active_tc == 1);
+      else
+        gram_tc(ctx, A, B, N1, N2, ng, scale, C, st, herm, ctx->active_tc == 1);
       return;
     }
   }
@@ -345,6 +348,20 @@ void gram(pt_ctx* ctx, const cx<T>* A, const cx<T>* B, int N1, int N2, size_t ng
   const size_t n = size_t(N1) * N2;
   PT_LAUNCH(k_reduce_parts, dim3(unsigned((n + 255) / 256)), 256, 0, st, part, splits, N1, N2, scale,
             herm ? tile : 0, C);
+}
+
+template <class T>
+void gram2(pt_ctx* ctx, const cx<T>* A, const cx<T>* B0, c128* C0, const cx<T>* B1, c128* C1, int N1, int N2,
+           size_t ng, double scale, cudaStream_t st, bool herm) {
+  if constexpr (sizeof(T) == 4) {
+    if (!ctx->bf16_requested && ctx->active_tc && ctx->tc_gram_wide && gram_tc_applies(A, B0, ng) &&
+        gram_tc_applies(A, B1, ng)) {
+      gram_tc_wide(ctx, A, B0, C0, B1, C1, N1, N2, ng, scale, st, herm, ctx->active_tc == 1);
+      return;
+    }
+  }
+  gram<T>(ctx, A, B0, N1, N2, ng, scale, C0, st, herm);
+  gram<T>(ctx, A, B1, N1, N2, ng, scale, C1, st, herm);
 }
 
 template <class T>
@@ -391,6 +408,10 @@ void potential_apply(pt_ctx* ctx, cx<T>* out, const cx<T>* psi, const double* v,
 
 template void gram<float>(pt_ctx*, const c64*, const c64*, int, int, size_t, double, c128*, cudaStream_t, bool);
 template void gram<double>(pt_ctx*, const c128*, const c128*, int, int, size_t, double, c128*, cudaStream_t, bool);
+template void gram2<float>(pt_ctx*, const c64*, const c64*, c128*, const c64*, c128*, int, int, size_t, double,
+                           cudaStream_t, bool);
+template void gram2<double>(pt_ctx*, const c128*, const c128*, c128*, const c128*, c128*, int, int, size_t, double,
+                            cudaStream_t, bool);
 template void rotate<float>(pt_ctx*, const c64*, const c128*, int, int, int, size_t, c128, const Term*, int, c64*,
                             cudaStream_t);
 template void rotate<double>(pt_ctx*, const c128*, const c128*, int, int, int, size_t, c128, const Term*, int,

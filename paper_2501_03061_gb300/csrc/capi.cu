@@ -215,6 +215,10 @@ pt_status pt_set_option(pt_ctx* ctx, const char* key, double value) {
       ctx->tc_period = int(value);
       return PT_OK;
     }
+    if (std::string(key) == "tc_gram_wide") {
+      ctx->tc_gram_wide = value != 0.0 ? 1 : 0;
+      return PT_OK;
+    }
     if (std::string(key) == "tc_gram") {
       ctx->tc_gram = value != 0.0 ? 1 : 0;
       return PT_OK;

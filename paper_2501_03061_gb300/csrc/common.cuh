@@ -145,6 +145,7 @@ struct pt_ctx {
   int x64p_tile = 4;   // option: pair-tile side of the persistent engine's schedule
   int x64p_ring = 24;  // option: pair-field ring slots of the persistent engine (raised to tile pairs + 3 lag + 1)
   int x64p_lag = 2;    // option: waves between the A, B, C and D stages of a pair in the persistent engine
+  int tc_gram_wide = 1;  // option: 64 x 128 tensor-core Gram tiles (and the fused two-product pass) when 1
   int tc_period = 2;   // option: K stages (32 floats each) accumulated in TMEM between readouts
   bool tc_err_clean = false;  // the tensor-core Gram's device error word exists and has been zeroed
   // batched exchange (batched.cu)

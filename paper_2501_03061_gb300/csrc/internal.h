@@ -34,6 +34,10 @@ void exchange_check(pt_ctx* ctx, cudaStream_t st);
 template <class T>
 void gram(pt_ctx* ctx, const cx<T>* A, const cx<T>* B, int N1, int N2, size_t ng, double scale, c128* C,
           cudaStream_t st, bool herm = false);
+// C0 = scale A^H B0 and C1 = scale A^H B1 (one pass over A on the tensor-core path, two Grams otherwise)
+template <class T>
+void gram2(pt_ctx* ctx, const cx<T>* A, const cx<T>* B0, c128* C0, const cx<T>* B1, c128* C1, int N1, int N2,
+           size_t ng, double scale, cudaStream_t st, bool herm = false);
 template <class T>
 void rotate(pt_ctx* ctx, const cx<T>* A, const c128* Bm, int ldb, int N1, int N2, size_t ng, c128 alpha,
             const Term* terms, int nterms, cx<T>* out, cudaStream_t st);
@@ -52,6 +56,9 @@ void sqnorms(pt_ctx* ctx, const cx<T>* a0, const c128* s0, const cx<T>* a1, cons
 void gram_tc(pt_ctx* ctx, const c64* A, const c64* B, int N1, int N2, size_t ng, double scale, c128* C,
              cudaStream_t st, bool herm, bool split3);
 void gram_tc_check(pt_ctx* ctx, cudaStream_t st);  // raises PT_TIMEOUT if a bounded wait expired
+// 64 x 128 tiles (gram_tc_wide.cu): C0 = scale A^H B0 and, when B1 is not NULL, C1 = scale A^H B1
+void gram_tc_wide(pt_ctx* ctx, const c64* A, const c64* B0, c128* C0, const c64* B1, c128* C1, int N1, int N2,
+                  size_t ng, double scale, cudaStream_t st, bool herm, bool split3);
 bool gram_tc_applies(const void* A, const void* B, size_t ng);
 
 // ---- tensor-core rotation (rotate_tc.cu): out = alpha A Bm + sum_t c_t x_t (complex64 orbitals) ----

@@ -530,8 +530,7 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
       tm.end();
       tm.begin(PH_SUB);
       // A = <Phi_h|H Phi_h> and S = <Phi_h|Phi_h> are Hermitian: upper tiles only, mirrored
-      gram<T>(ctx, phih, Hphi, N, N, S.ng, S.dV, A, st, true);
-      gram<T>(ctx, phih, phih, N, N, S.ng, S.dV, Sm, st, true);
+      gram2<T>(ctx, phih, Hphi, A, phih, Sm, N, N, S.ng, S.dV, st, true);
       if (first) {
         e_A.resize(S.n2);
         e_sig.resize(S.n2);

@@ -46,17 +46,20 @@ def fields(rng, cell, n, offset=True):
     return a.astype(np.complex64)
 
 
-def run(ctx, mode, A, B, cell):
-    """Overlap on the GPU in one of the forms: fp64, fp32 (CUDA cores), fp32_tc, tf32."""
+def run(ctx, mode, A, B, cell, wide=1):
+    """Overlap on the GPU in one of the forms: fp64, fp32 (CUDA cores), fp32_tc, tf32; `wide`
+    selects the 64 x 128 tensor-core tiles (1, used when N2 > 64) or the 64 x 64 ones (0)."""
     prec = {"fp32_tc": "fp32"}.get(mode, mode)
     dt = np.complex128 if prec == "fp64" else np.complex64
     a = dev(A.astype(dt))
     b = a if B is A else dev(B.astype(dt))
     ctx.set_option("tc_gram", 1 if mode == "fp32_tc" else 0)
+    ctx.set_option("tc_gram_wide", wide)
     try:
         return ctx.overlap(a, b, cell=cell, precision=prec).cpu().numpy()
     finally:
         ctx.set_option("tc_gram", 0)
+        ctx.set_option("tc_gram_wide", 1)
 
 
 def check(got, A, B, dV, tol):
@@ -68,13 +71,15 @@ def check(got, A, B, dV, tol):
     return float((err / scale).max())
 
 
+@pytest.mark.parametrize("wide", [1, 0])
 @pytest.mark.parametrize("mode", ["fp64", "fp32", "fp32_tc", "tf32", "bf16"])
-def test_overlap_general_ragged(ctx, mode):
-    """N1 = 70, N2 = 130 (ragged 64-wide tiles), 24^3 grid."""
+def test_overlap_general_ragged(ctx, mode, wide):
+    """N1 = 70, N2 = 130 (ragged 64-wide tiles; 64 x 128 tensor-core tiles with an absent second
+    half in the last one), 24^3 grid."""
     rng = np.random.default_rng(301)
     cell = synth.cubic(24, 10.0)
     A, B = fields(rng, cell, 70), fields(rng, cell, 130)
-    got = run(ctx, mode, A, B, cell)
+    got = run(ctx, mode, A, B, cell, wide)
     if mode == "fp64":
         ref = O.overlap(A.astype(np.complex128), B.astype(np.complex128), O.grid_of(cell).dV)
         assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
@@ -82,14 +87,15 @@ def test_overlap_general_ragged(ctx, mode):
         check(got, A, B, O.grid_of(cell).dV, TOL[mode])
 
 
+@pytest.mark.parametrize("wide", [1, 0])
 @pytest.mark.parametrize("mode", ["fp32", "fp32_tc", "tf32", "bf16"])
-def test_overlap_hermitian_ragged_K_tail(ctx, mode):
+def test_overlap_hermitian_ragged_K_tail(ctx, mode, wide):
     """S = <A|A> with N = 97 (mirrored tiles) on a 9 x 10 x 12 grid: 2 Ng = 2160 floats is not a
     multiple of the 32-float stage, so the last stage is partly zero-filled."""
     rng = np.random.default_rng(302)
     cell = synth.Cell((9, 10, 12), (5.0, 5.5, 6.0))
     A = fields(rng, cell, 97)
-    got = run(ctx, mode, A, A, cell)
+    got = run(ctx, mode, A, A, cell, wide)
     check(got, A, A, O.grid_of(cell).dV, TOL[mode])
     # tiles below the diagonal are mirrors of the ones above: exact conjugates across tiles
     t = np.arange(97) // 64
@@ -108,18 +114,22 @@ def test_overlap_orthonormal_orbitals(ctx, mode):
     assert np.abs(got - np.eye(40)).max() <= 1e-5
 
 
-def test_overlap_64cubed_N320_tensor_cores_sampled(ctx):
-    """Full size of the PT-IM overlap (64^3 grid, N = 320): the tensor-core form on sampled
-    entries against the FP64 oracle's definition, and against the CUDA-core form everywhere."""
+@pytest.mark.parametrize("wide", [1, 0])
+def test_overlap_64cubed_N320_tensor_cores_sampled(ctx, wide):
+    """Full size of the PT-IM overlap (64^3 grid, N = 320): the tensor-core form (64 x 128 or
+    64 x 64 tiles) on sampled entries against the FP64 oracle's definition, and against the
+    CUDA-core form everywhere."""
     rng = np.random.default_rng(304)
     cell = synth.cubic(64, 20.5)
     A = fields(rng, cell, 320)
     a = dev(A)
     ctx.set_option("tc_gram", 1)
+    ctx.set_option("tc_gram_wide", wide)
     try:
         tc = ctx.overlap(a, a, cell=cell, precision="fp32").cpu().numpy()
     finally:
         ctx.set_option("tc_gram", 0)
+        ctx.set_option("tc_gram_wide", 1)
     simt = ctx.overlap(a, a, cell=cell, precision="fp32").cpu().numpy()
     dV = O.grid_of(cell).dV
     Af = A.reshape(320, -1).astype(np.complex128)
