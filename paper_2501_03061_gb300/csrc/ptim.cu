@@ -262,6 +262,7 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
   c128* Lc = Mx("ptim_L");
   c128* Li = Mx("ptim_Linv");
   c128* T1 = Mx("ptim_T1");
+  c128* Tc = Mx("ptim_Tcomm");  // the sigma commutator, computed on a side stream
   c128* SinvA = Mx("ptim_SinvA");
   c128* rsig_buf[2] = {Mx("ptim_rsig0"), Mx("ptim_rsig1")};
   c128* dxp_sig = Mx("ptim_dxpend_sig");
@@ -377,6 +378,23 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
       }
     }
   } ev_guard{ev};
+  // The sigma commutator [A, sigma_h] needs only A: it runs on a side stream while the overlap is
+  // factorised (the FP64 Cholesky chain keeps a few CTAs busy at a time) and joins before r_sigma
+  if (ctx->side_streams.empty()) {
+    cudaStream_t s2 = nullptr;
+    PT_CUDA_CHECK(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+    ctx->side_streams.push_back(s2);
+  }
+  cudaStream_t side = ctx->side_streams[0];
+  cudaEvent_t comm_ev[2] = {nullptr, nullptr};
+  for (auto& e : comm_ev) PT_CUDA_CHECK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  struct CommEvGuard {
+    cudaEvent_t* e;
+    ~CommEvGuard() {
+      cudaEventDestroy(e[0]);
+      cudaEventDestroy(e[1]);
+    }
+  } comm_guard{comm_ev};
   // V_x[P_h] Phi_h through the sigma_h eigenbasis: (V_x phit) Q^*, phit = Phi_h Q
   // sigma_h changes little between outer iterations and between steps: eigensolves start from the
   // last basis the context holds (any unitary start is correct; a near one converges in a sweep or two)
@@ -549,6 +567,13 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
         }
       }
       tm.end();
+      if (!pure) {
+        PT_CUDA_CHECK(cudaEventRecord(comm_ev[0], st));
+        PT_CUDA_CHECK(cudaStreamWaitEvent(side, comm_ev[0], 0));
+        zgemm('N', 'N', N, N, N, c128{1, 0}, A, N, sigh, N, c128{0, 0}, Tc, N, side);
+        zgemm('N', 'N', N, N, N, c128{-1, 0}, sigh, N, A, N, c128{1, 0}, Tc, N, side);
+        PT_CUDA_CHECK(cudaEventRecord(comm_ev[1], side));
+      }
       tm.begin(PH_SUBNN);
       // S^{-1} A = L^{-*} (L^{-1} A)
       cholesky(ctx, Sm, N, Lc, info, st);
@@ -564,12 +589,11 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
       tm.begin(PH_COMM);
       // r_sigma = sigma_n - i dt (A sigma_h - sigma_h A) - sigma  (the commutator is 0 in a pure state)
       if (pure) {
-        PT_CUDA_CHECK(cudaMemsetAsync(T1, 0, mb, st));
+        PT_CUDA_CHECK(cudaMemsetAsync(Tc, 0, mb, st));
       } else {
-        zgemm('N', 'N', N, N, N, c128{1, 0}, A, N, sigh, N, c128{0, 0}, T1, N, st);
-        zgemm('N', 'N', N, N, N, c128{-1, 0}, sigh, N, A, N, c128{1, 0}, T1, N, st);
+        PT_CUDA_CHECK(cudaStreamWaitEvent(st, comm_ev[1], 0));
       }
-      Term ts[3] = {{sign, c128{1, 0}}, {T1, c128{0, -P.dt}}, {sig, c128{-1, 0}}};
+      Term ts[3] = {{sign, c128{1, 0}}, {Tc, c128{0, -P.dt}}, {sig, c128{-1, 0}}};
       lincomb<double>(ctx, rsig, S.n2, ts, 3, st);
       tm.end();
       tm.begin(PH_AND);

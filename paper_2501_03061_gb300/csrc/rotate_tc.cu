@@ -13,8 +13,11 @@
 // operand the tensor core reads, so TMA brings in a [16 orbitals][128 points] block of complex64
 // values and a converter warpgroup writes it out as 128 K-major rows of 32 floats (128B swizzle),
 // once as the raw values (the tensor core reads their TF32 bits: "hi") and once as the FP32
-// remainders x - tf32(x) ("lo").  B' hi/lo tiles come from global memory by TMA.  Products
-// summed per tile: hi*hi + hi*lo + lo*hi.
+// remainders x - tf32(x) ("lo").  B' is written once per call as the shared-memory images of
+// its stages (for every 128-row block and 32-float K stage, the hi and the lo tile in the 128B
+// swizzle the tensor core reads, 32 KB contiguous), so a stage's B operands arrive with one bulk
+// copy instead of a tiled load of 2 x 128 rows of 128 bytes.  Products summed per tile:
+// hi*hi + hi*lo + lo*hi.
 //
 // Warp roles (320 threads): warp 0 TMA producer, warp 1 TMEM allocation and MMA issue (one
 // lane), warps 2..5 converter, warps 6..9 TMEM readout and the epilogue (alpha is folded into
@@ -103,20 +106,24 @@ struct RotArgs {
   int stages;          // K stages per tile: ceil(N1 / KO)
   int period;          // stages per TMEM accumulation window
   int split3;
+  const float* bp;     // B' stage images: [tiles_j][stages][hi | lo][128 rows x 32 floats, swizzled]
   const c64* e[3];     // epilogue terms (may be null)
   c64 c[3];
   c64* out;
 };
 
-// B'[n'][k'] hi and lo parts (K-major rows of kpad floats, npad rows), alpha folded in
 // read-only load of one complex64 through the non-coherent path
 __device__ __forceinline__ c64 ldg_c64(const c64* p) {
   const float2 v = __ldg(reinterpret_cast<const float2*>(p));
   return c64{v.x, v.y};
 }
 
+// B'[n'][k'] (npad = tiles_j * 128 rows, kpad = stages * 32 floats), alpha folded in, written as
+// stage images: element (n', k') of row block jt = n' / 128, stage s = k' / 32 goes to row
+// r = n' % 128, 16-byte chunk (k' % 32) / 4 XOR (r % 8) of the 32 KB block (jt * stages + s),
+// the hi part in its first 16 KB and the lo part in its second
 __global__ void k_rot_prep_b(const c128* __restrict__ Bm, int ldb, int N1, int N2, c128 alpha, int npad, int kpad,
-                             float* __restrict__ bhi, float* __restrict__ blo) {
+                             int stages, float* __restrict__ bp) {
   const size_t e = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (e >= size_t(npad) * kpad) return;
   const int n = int(e / kpad), kk = int(e % kpad);
@@ -129,13 +136,15 @@ __global__ void k_rot_prep_b(const c128* __restrict__ Bm, int ldb, int N1, int N
   }
   const float f = float(v);
   const float h = tf32_hi(f);
-  bhi[e] = h;
-  blo[e] = float(v - double(h));
+  const int jt = n / NC, r = n % NC, s = kk / (2 * KO), kq = kk % (2 * KO);
+  const size_t blk = size_t(jt * stages + s) * 2 * (NC * 2 * KO);
+  const size_t off = size_t(r) * (2 * KO) + size_t((((kq >> 2) ^ (r & 7)) << 2) + (kq & 3));
+  bp[blk + off] = h;
+  bp[blk + NC * 2 * KO + off] = float(v - double(h));
 }
 
 __global__ void __launch_bounds__(THREADS, 1)
-    k_rotate_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBh,
-                const __grid_constant__ CUtensorMap tmBl, RotArgs P, int* __restrict__ err) {
+    k_rotate_tc(const __grid_constant__ CUtensorMap tmA, RotArgs P, int* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -223,8 +232,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           break;
         }
         mbar_arrive_expect_tx(bar_b_full(sc), 2 * OP_BYTES);
-        tma_load_4d(c_bhi(sc), &tmBh, s * 2 * KO, jt * NC, 0, 0, bar_b_full(sc));
-        tma_load_4d(c_blo(sc), &tmBl, s * 2 * KO, jt * NC, 0, 0, bar_b_full(sc));
+        bulk_load(c_bhi(sc), P.bp + size_t(jt * S + s) * (2 * OP_BYTES / 4), 2 * OP_BYTES, bar_b_full(sc));
         issued_b = q + 1;
       }
       // copies in flight land before the CTA's shared memory is released
@@ -403,30 +411,24 @@ void rotate_tc(pt_ctx* ctx, const c64* A, const c128* Bm, int ldb, int N1, int N
   const int tiles_j = (N2 + RJ - 1) / RJ;
   const int npad = tiles_j * NC;
   const int tiles_r = int((ng + RM - 1) / RM);
-  float* bhi = static_cast<float*>(ctx->get("rot_tc_bhi", size_t(npad) * kpad * sizeof(float)));
-  float* blo = static_cast<float*>(ctx->get("rot_tc_blo", size_t(npad) * kpad * sizeof(float)));
+  float* bp = static_cast<float*>(ctx->get("rot_tc_bp", 2 * size_t(npad) * kpad * sizeof(float)));
   int* err = static_cast<int*>(ctx->get("gram_tc_err", sizeof(int)));
   if (!ctx->tc_err_clean) {
     PT_CUDA_CHECK(cudaMemsetAsync(err, 0, sizeof(int), st));
     ctx->tc_err_clean = true;
   }
   const size_t nb = size_t(npad) * kpad;
-  PT_LAUNCH(k_rot_prep_b, unsigned((nb + 255) / 256), 256, 0, st, Bm, ldb, N1, N2, alpha, npad, kpad, bhi, blo);
+  PT_LAUNCH(k_rot_prep_b, unsigned((nb + 255) / 256), 256, 0, st, Bm, ldb, N1, N2, alpha, npad, kpad, stages, bp);
   static DeviceOnce once;
   once([] { PT_CUDA_CHECK(cudaFuncSetAttribute(k_rotate_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES)); });
   // A as a [N1][Ng] array of 8-byte elements; box = 128 points x 16 orbitals, no swizzle
-  CUtensorMap ta, tbh, tbl;
+  CUtensorMap ta;
   const uint64_t da[4] = {ng, uint64_t(N1), 1, 1};
   const uint64_t sa[3] = {ng * 8, ng * 8 * uint64_t(N1), ng * 8 * uint64_t(N1)};
   const uint32_t boxa[4] = {RM, KO, 1, 1};
   encode_tmap_4d_u64(&ta, A, da, sa, boxa, CU_TENSOR_MAP_SWIZZLE_NONE);
-  // B' hi / lo: [npad][kpad] floats, box = 32 floats x 128 rows, 128B swizzle
-  const uint64_t db[4] = {uint64_t(kpad), uint64_t(npad), 1, 1};
-  const uint64_t sb[3] = {uint64_t(kpad) * 4, uint64_t(kpad) * 4 * npad, uint64_t(kpad) * 4 * npad};
-  const uint32_t boxb[4] = {2 * KO, NC, 1, 1};
-  encode_tmap_4d_f32(&tbh, bhi, db, sb, boxb, CU_TENSOR_MAP_SWIZZLE_128B);
-  encode_tmap_4d_f32(&tbl, blo, db, sb, boxb, CU_TENSOR_MAP_SWIZZLE_128B);
   RotArgs P{};
+  P.bp = bp;
   P.N1 = N1;
   P.N2 = N2;
   P.ng = (long long)ng;
@@ -442,7 +444,7 @@ void rotate_tc(pt_ctx* ctx, const c64* A, const c128* Bm, int ldb, int N1, int N
   }
   P.out = out;
   const int grid = std::min(P.ntiles, ctx->num_sms);
-  PT_LAUNCH(k_rotate_tc, grid, THREADS, SMEM_BYTES, st, ta, tbh, tbl, P, err);
+  PT_LAUNCH(k_rotate_tc, grid, THREADS, SMEM_BYTES, st, ta, P, err);
 }
 
 }  // namespace pt
