@@ -101,8 +101,7 @@ __global__ void __launch_bounds__(THREADS, 2)
         const uint32_t b = uint32_t(c & 1);
         fence_proxy_async_smem();  // the buffer was last read and written through the generic proxy
         mbar_arrive_expect_tx(bar + 8u * b, TILE_BYTES);
-        for (int q = 0; q < 4; ++q)
-          tma_load_4d(base + b * TILE_BYTES + q * SUB_BYTES, &tm_plane, 16 * q, 0, z, orb, bar + 8u * b);
+        tma_load_5d(base + b * TILE_BYTES, &tm_plane, 0, 0, z, orb, 0, bar + 8u * b);
       };
       if (tid == 0) {
         if (n > 0) issue(0);
@@ -163,10 +162,8 @@ __global__ void __launch_bounds__(THREADS, 2)
     const PairDesc pd = L.pa[p];
     if (tid == 0) {
       mbar_arrive_expect_tx(bar, 2 * TILE_BYTES);
-      for (int s = 0; s < 4; ++s) {
-        tma_load_4d(base + OFF_A + s * SUB_BYTES, &tm_src, 16 * s, 0, z, pd.i, bar);
-        tma_load_4d(base + OFF_B + s * SUB_BYTES, &tm_tgt, 16 * s, 0, z, pd.j, bar);
-      }
+      tma_load_5d(base + OFF_A, &tm_src, 0, 0, z, pd.i, 0, bar);
+      tma_load_5d(base + OFF_B, &tm_tgt, 0, 0, z, pd.j, 0, bar);
     }
     const bool skip = pair_skipped(pd, occ);
     if (!mbar_wait(bar, 0, TIMEOUT_NS)) {
@@ -208,10 +205,9 @@ __global__ void __launch_bounds__(THREADS, 2)
     const int orb = L.slotB * L.max_pairs + p;
     if (tid == 0) {
       mbar_arrive_expect_tx(bar, TILE_BYTES);
-      for (int s = 0; s < 4; ++s) tma_load_4d(base + OFF_A + s * SUB_BYTES, &tm_slab, 16 * s, ky0, 0, orb, bar);
+      tma_load_5d(base + OFF_A, &tm_slab, 0, ky0, 0, orb, 0, bar);
       mbar_arrive_expect_tx(bar + 8, TILE_BYTES);
-      for (int s = 0; s < 4; ++s)
-        tma_load_4d(base + OFF_P + s * SUB_BYTES, &tm_slab, 16 * s, ky0 + H, 0, orb, bar + 8);
+      tma_load_5d(base + OFF_P, &tm_slab, 0, ky0 + H, 0, orb, 0, bar + 8);
     }
     const bool skip = pair_skipped(pd, occ);
     c64* gs = reinterpret_cast<c64*>(sm + OFF_B) + grp * 64;
@@ -238,7 +234,7 @@ __global__ void __launch_bounds__(THREADS, 2)
       fence_proxy_async_smem();
       __syncthreads();
       if (tid == 0) {
-        for (int s = 0; s < 4; ++s) tma_store_4d(&tm_slab, 16 * s, ky, 0, orb, base + off + s * SUB_BYTES);
+        tma_store_5d(&tm_slab, 0, ky, 0, orb, 0, base + off);
         tma_store_commit();
       }
     }
@@ -256,10 +252,9 @@ __global__ void __launch_bounds__(THREADS, 2)
     const int orb = L.slotC * L.max_pairs + p;
     if (tid == 0) {
       mbar_arrive_expect_tx(bar, TILE_BYTES);
-      for (int s = 0; s < 4; ++s) tma_load_4d(base + OFF_A + s * SUB_BYTES, &tm_plane, 16 * s, 0, z0, orb, bar);
+      tma_load_5d(base + OFF_A, &tm_plane, 0, 0, z0, orb, 0, bar);
       mbar_arrive_expect_tx(bar + 8, TILE_BYTES);
-      for (int s = 0; s < 4; ++s)
-        tma_load_4d(base + OFF_B + s * SUB_BYTES, &tm_plane, 16 * s, 0, z0 + H, orb, bar + 8);
+      tma_load_5d(base + OFF_B, &tm_plane, 0, 0, z0 + H, orb, 0, bar + 8);
     }
     const bool skip = pair_skipped(pd, occ);
     const int kx = grp;
@@ -392,6 +387,18 @@ void encode_tmap_4d_bf16(CUtensorMap* map, const void* base, const uint64_t dims
   encode_tmap_4d(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, base, dims, strides_bytes, box, swizzle);
 }
 
+void encode_tmap_5d_u64(CUtensorMap* map, const void* base, const uint64_t dims[5], const uint64_t strides_bytes[4],
+                        const uint32_t box[5], CUtensorMapSwizzle swizzle) {
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  cuuint64_t d[5] = {dims[0], dims[1], dims[2], dims[3], dims[4]};
+  cuuint64_t s[4] = {strides_bytes[0], strides_bytes[1], strides_bytes[2], strides_bytes[3]};
+  cuuint32_t b[5] = {box[0], box[1], box[2], box[3], box[4]};
+  CUresult r = encode_fn()(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 5, const_cast<void*>(base), d, s, b, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) fail(PT_CUDA, "cuTensorMapEncodeTiled (5-D) failed (" + std::to_string(int(r)) + ")");
+}
+
 void encode_tmap_4d_u64(CUtensorMap* map, const void* base, const uint64_t dims[4], const uint64_t strides_bytes[3],
                         const uint32_t box[4], CUtensorMapSwizzle swizzle) {
   const cuuint32_t estr[4] = {1, 1, 1, 1};
@@ -427,17 +434,20 @@ void exchange64_tma(pt_ctx* ctx, const ScheduleImpl& sch, const c64* src, const 
     PT_CUDA_CHECK(cudaMemcpyToSymbol(c_tw64, h, sizeof(h)));
   });
   (void)tw;
-  const uint64_t strides[3] = {G * 8, G * G * 8, ng * 8};
-  const uint32_t plane_box[4] = {16, 64, 1, 1};
-  const uint32_t slab_box[4] = {16, 1, 64, 1};
+  // 5-D views (x mod 16, y, z, field, x / 16) of the [field][z][y][x] complex64 arrays: one copy
+  // moves a whole 64 x 64 plane or slab as four 16-column sub-tiles of 128-byte rows (the x / 16
+  // dimension, stride 128 B, outermost in the box), the shared-memory layout the line transforms read
+  const uint64_t strides[4] = {G * 8, G * G * 8, ng * 8, 16 * 8};
+  const uint32_t plane_box[5] = {16, 64, 1, 1, 4};
+  const uint32_t slab_box[5] = {16, 1, 64, 1, 4};
   CUtensorMap tm_src, tm_tgt, tm_plane, tm_slab;
-  const uint64_t dsrc[4] = {G, G, G, uint64_t(sch.N)};
-  const uint64_t dtgt[4] = {G, G, G, uint64_t(M)};
-  const uint64_t dscr[4] = {G, G, G, uint64_t(ns) * maxp};
-  encode_tmap_4d_u64(&tm_src, src, dsrc, strides, plane_box, CU_TENSOR_MAP_SWIZZLE_128B);
-  encode_tmap_4d_u64(&tm_tgt, tgt, dtgt, strides, plane_box, CU_TENSOR_MAP_SWIZZLE_128B);
-  encode_tmap_4d_u64(&tm_plane, scratch, dscr, strides, plane_box, CU_TENSOR_MAP_SWIZZLE_128B);
-  encode_tmap_4d_u64(&tm_slab, scratch, dscr, strides, slab_box, CU_TENSOR_MAP_SWIZZLE_128B);
+  const uint64_t dsrc[5] = {16, G, G, uint64_t(sch.N), 4};
+  const uint64_t dtgt[5] = {16, G, G, uint64_t(M), 4};
+  const uint64_t dscr[5] = {16, G, G, uint64_t(ns) * maxp, 4};
+  encode_tmap_5d_u64(&tm_src, src, dsrc, strides, plane_box, CU_TENSOR_MAP_SWIZZLE_128B);
+  encode_tmap_5d_u64(&tm_tgt, tgt, dtgt, strides, plane_box, CU_TENSOR_MAP_SWIZZLE_128B);
+  encode_tmap_5d_u64(&tm_plane, scratch, dscr, strides, plane_box, CU_TENSOR_MAP_SWIZZLE_128B);
+  encode_tmap_5d_u64(&tm_slab, scratch, dscr, strides, slab_box, CU_TENSOR_MAP_SWIZZLE_128B);
   const int nb = int(sch.pair_off.size()) - 1;
   auto copy_pairs = [&](PairDesc* dst, int batch) {
     const int p0 = sch.pair_off[batch], np = sch.pair_off[batch + 1] - p0;
