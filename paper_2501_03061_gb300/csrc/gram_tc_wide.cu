@@ -81,19 +81,26 @@ __device__ __forceinline__ void commit_w(uint32_t bar) {
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
+__device__ __forceinline__ void ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 __device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+// 16-byte shared-memory accesses by 32-bit shared-window address
+__device__ __forceinline__ float4 lds128(uint32_t a) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ void sts128(uint32_t a, float4 v) {
+  asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w) : "memory");
+}
 __device__ __forceinline__ float4 lo4(float4 v) {
   return make_float4(v.x - tf32_hi(v.x), v.y - tf32_hi(v.y), v.z - tf32_hi(v.z), v.w - tf32_hi(v.w));
 }
@@ -134,7 +141,6 @@ __global__ void __launch_bounds__(W_THREADS, 1)
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int tile = blockIdx.x, split = blockIdx.y;
-  const WideTile T = tiles[tile];
   const int st0 = split * P.stages_per_split;
   const int st1 = min(P.stages_total, st0 + P.stages_per_split);
   const int nst = max(0, st1 - st0);
@@ -173,6 +179,7 @@ __global__ void __launch_bounds__(W_THREADS, 1)
   if (warp == 0) {
     // ---------------- TMA producer ----------------
     if (lane == 0) {
+      const WideTile T = tiles[tile];
       const CUtensorMap* h0 = T.m0 == 1 ? &tmB1 : &tmB0;
       // an absent second half re-reads the first (its columns are never reduced)
       const CUtensorMap* h1 = T.m1 < 0 ? h0 : (T.m1 == 1 ? &tmB1 : &tmB0);
@@ -246,11 +253,11 @@ __global__ void __launch_bounds__(W_THREADS, 1)
       if (!__all_sync(0xffffffffu, mbar_wait(bar_acc_full(b), (per / 2) & 1, TIMEOUT_NS))) return false;
       fence_after();
 #pragma unroll
-      for (int c0 = 0; c0 < 32; c0 += 16) {
-        float v[16];
-        ld16(tmem + lane_base + uint32_t(b * WN + 32 * wg + c0), v);
+      for (int c0 = 0; c0 < 32; c0 += 8) {
+        float v[8];
+        ld8(tmem + lane_base + uint32_t(b * WN + 32 * wg + c0), v);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
+        for (int i = 0; i < 8; ++i) {
           const float y = v[i] - comp[c0 + i];
           const float t = sum[c0 + i] + y;
           comp[c0 + i] = (t - sum[c0 + i]) - y;
@@ -274,17 +281,19 @@ __global__ void __launch_bounds__(W_THREADS, 1)
         fail_out(8);
         break;
       }
-      unsigned char* st = sm + (stg(s) - base);
-      const float4 a = *reinterpret_cast<const float4*>(st + offa);
-      *reinterpret_cast<float4*>(st + ROWS + offa) = times_i(a);
+      const uint32_t st = stg(s);
+      {
+        const float4 a = lds128(st + offa);
+        sts128(st + ROWS + offa, times_i(a));
+        if (P.split3) {
+          const float4 al = lo4(a);
+          sts128(st + 4 * ROWS + offa, al);
+          sts128(st + 5 * ROWS + offa, times_i(al));
+        }
+      }
       if (P.split3) {
-        const float4 b0 = *reinterpret_cast<const float4*>(st + 2 * ROWS + offb0);
-        const float4 b1 = *reinterpret_cast<const float4*>(st + 2 * ROWS + offb1);
-        const float4 al = lo4(a);
-        *reinterpret_cast<float4*>(st + 4 * ROWS + offa) = al;
-        *reinterpret_cast<float4*>(st + 5 * ROWS + offa) = times_i(al);
-        *reinterpret_cast<float4*>(st + 6 * ROWS + offb0) = lo4(b0);
-        *reinterpret_cast<float4*>(st + 6 * ROWS + offb1) = lo4(b1);
+        sts128(st + 6 * ROWS + offb0, lo4(lds128(st + 2 * ROWS + offb0)));
+        sts128(st + 6 * ROWS + offb1, lo4(lds128(st + 2 * ROWS + offb1)));
       }
       fence_proxy_async_smem();
       mbar_arrive(bar_cvt(s));
