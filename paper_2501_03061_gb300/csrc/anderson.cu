@@ -31,49 +31,63 @@ __device__ __forceinline__ T rdot(cx<T> a, cx<T> b) {
   return a.re * b.re + a.im * b.im;
 }
 
-// out partial layout: [2*mo + 2][nblk] per segment call, written at column offset blk_off
-template <class T>
+// out partial layout: [2*MO + 2][nblk] per segment call, written at column offset blk_off.  The
+// number of other entries MO is a template constant, so a call with a short history holds only
+// the accumulators it needs (registers, and with them the resident warps that keep this streaming
+// pass's loads in flight, fall with MO).
+template <class T, int MO>
 __global__ void __launch_bounds__(AT) k_and_prepare(const cx<T>* __restrict__ rk, const cx<T>* __restrict__ rprev,
                                                     const cx<T>* __restrict__ dxp, cx<T>* __restrict__ dRs,
-                                                    cx<T>* __restrict__ Zs, HistPtrs<T> dR, int mo, T beta, size_t n,
+                                                    cx<T>* __restrict__ Zs, HistPtrs<T> dR, T beta, size_t n,
                                                     double w, double* __restrict__ part, int ld, int blk_off) {
-  T s[2 * HMAX + 2];
+  constexpr int NV = 2 * MO + 2;
+  T s[NV];
 #pragma unroll
-  for (int a = 0; a < 2 * HMAX + 2; ++a) s[a] = T(0);
+  for (int a = 0; a < NV; ++a) s[a] = T(0);
   for (size_t e = size_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n; e += size_t(gridDim.x) * blockDim.x) {
     const cx<T> r = rk[e];
     const cx<T> d = r - rprev[e];
     dRs[e] = d;
     Zs[e] = dxp[e] + d * beta;
-    s[2 * HMAX] += rdot(d, d);
-    s[2 * HMAX + 1] += rdot(d, r);
+    s[2 * MO] += rdot(d, d);
+    s[2 * MO + 1] += rdot(d, r);
 #pragma unroll
-    for (int a = 0; a < HMAX; ++a) {
-      if (a < mo) {
-        const cx<T> h = dR.v[a][e];
-        s[2 * a] += rdot(h, d);
-        s[2 * a + 1] += rdot(h, r);
-      }
+    for (int a = 0; a < MO; ++a) {
+      const cx<T> h = dR.v[a][e];
+      s[2 * a] += rdot(h, d);
+      s[2 * a + 1] += rdot(h, r);
     }
   }
   // block sums: warp shuffles, then one value per warp in shared memory
-  __shared__ double red[2 * HMAX + 2][AT / 32];
+  __shared__ double red[NV][AT / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int q = 0; q < 2 * HMAX + 2; ++q) {
-    if (q >= 2 * mo && q < 2 * HMAX) continue;  // absent history entries
+  for (int q = 0; q < NV; ++q) {
     double x = double(s[q]);
     for (int off = 16; off; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
     if (lane == 0) red[q][warp] = x;
   }
   __syncthreads();
-  const int nv = 2 * mo + 2;
-  if (threadIdx.x < nv) {
-    // output order: the pairs of the other entries, then the two values of the new entry
-    const int q = threadIdx.x < 2 * mo ? threadIdx.x : 2 * HMAX + (threadIdx.x - 2 * mo);
+  // output order: the pairs of the other entries, then the two values of the new entry
+  if (threadIdx.x < NV) {
     double t = 0;
-    for (int k = 0; k < AT / 32; ++k) t += red[q][k];
+    for (int k = 0; k < AT / 32; ++k) t += red[threadIdx.x][k];
     part[size_t(threadIdx.x) * ld + blk_off + blockIdx.x] = w * t;
+  }
+}
+
+template <class T, int MO = 0>
+void launch_prepare(int mo, int blocks, cudaStream_t st, const cx<T>* rk, const cx<T>* rprev, const cx<T>* dxp,
+                    cx<T>* dRs, cx<T>* Zs, const HistPtrs<T>& h, T beta, size_t n, double w, double* part, int ld,
+                    int blk_off) {
+  if constexpr (MO < HMAX) {
+    if (mo != MO) {
+      launch_prepare<T, MO + 1>(mo, blocks, st, rk, rprev, dxp, dRs, Zs, h, beta, n, w, part, ld, blk_off);
+      return;
+    }
+    PT_LAUNCH((k_and_prepare<T, MO>), blocks, AT, 0, st, rk, rprev, dxp, dRs, Zs, h, beta, n, w, part, ld, blk_off);
+  } else {
+    fail(PT_INVALID_ARG, "Anderson history too deep");
   }
 }
 
@@ -154,10 +168,8 @@ void anderson_prepare(pt_ctx* ctx, const AndersonSeg<T>& phi, const AndersonSeg<
     h1.v[a] = phi.dR[a];
     h2.v[a] = sig.dR[a];
   }
-  PT_LAUNCH(k_and_prepare<T>, b1, AT, 0, st, phi.rk, phi.rprev, phi.dxp, phi.dRs, phi.Zs, h1, mo, T(beta), phi.n,
-            w_phi, part, ld, 0);
-  PT_LAUNCH(k_and_prepare<double>, b2, AT, 0, st, sig.rk, sig.rprev, sig.dxp, sig.dRs, sig.Zs, h2, mo, beta, sig.n,
-            1.0, part, ld, b1);
+  launch_prepare<T>(mo, b1, st, phi.rk, phi.rprev, phi.dxp, phi.dRs, phi.Zs, h1, T(beta), phi.n, w_phi, part, ld, 0);
+  launch_prepare<double>(mo, b2, st, sig.rk, sig.rprev, sig.dxp, sig.dRs, sig.Zs, h2, beta, sig.n, 1.0, part, ld, b1);
   PT_LAUNCH(k_and_reduce, nv, 256, 0, st, part, ld, nv, dots);
 }
 
