@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(FT) k_hx_fwd_plane(const cx<T>* __restrict__ p
   if (k & 1) {
     const double* v = vloc + size_t(z) * PL;
     const cx<T>* xx = X ? X + off : nullptr;
-#pragma unroll 4
+#pragma unroll 8
     for (int e = threadIdx.x; e < PL; e += FT) {
       const int yy = e / N, x = e - yy * N;
       cx<T> val = f[e] * T(v[e]);
@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(FT) k_hx_fwd_plane(const cx<T>* __restrict__ p
       buf[yy * kPitch<N> + x] = val;
     }
   } else {
-#pragma unroll 4
+#pragma unroll 8
     for (int e = threadIdx.x; e < PL; e += FT) {
       const int yy = e / N, x = e - yy * N;
       buf[yy * kPitch<N> + x] = f[e];
@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(FT) k_hx_fwd_plane(const cx<T>* __restrict__ p
   cfft_fast<N, false, FT>(buf, tw);
   cfft_slow<N, false, FT>(buf, tw);
   cx<T>* o = scratch + size_t(k) * NG + size_t(z) * PL;
-#pragma unroll 4
+#pragma unroll 8
   for (int e = threadIdx.x; e < PL; e += FT) {
     const int yy = e / N, x = e - yy * N;
     o[e] = buf[yy * kPitch<N> + x];
@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(FT) k_hx_column(cx<T>* __restrict__ scratch, c
   for (int t = threadIdx.x; t < N; t += FT) tw[t] = twg[t];
   cx<T>* fa = scratch + size_t(2 * j) * NG;
   cx<T>* fb = fa + NG;
-#pragma unroll 4
+#pragma unroll 8
   for (int e = threadIdx.x; e < N * N; e += FT) {
     const int z = e / N, x = e - z * N;
     const size_t gi = (size_t(z) * N + yrow) * N + x;
@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(FT) k_hx_column(cx<T>* __restrict__ scratch, c
   const double* g2x = g2;
   const double* g2y = g2 + N;
   const double* g2z = g2 + 2 * N;
-#pragma unroll 4
+#pragma unroll 8
   for (int e = threadIdx.x; e < N * N; e += FT) {
     const int z = e / N, x = e - z * N;
     const double half = 0.5 * (g2x[x] + g2y[yrow] + g2z[z]);
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(FT) k_hx_column(cx<T>* __restrict__ scratch, c
   }
   __syncthreads();
   cfft_slow<N, true, FT>(ba, tw);
-#pragma unroll 4
+#pragma unroll 8
   for (int e = threadIdx.x; e < N * N; e += FT) {
     const int z = e / N, x = e - z * N;
     fa[(size_t(z) * N + yrow) * N + x] = ba[z * kPitch<N> + x];
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(FT) k_hx_inv_plane(const cx<T>* __restrict__ s
   const int z = blockIdx.x, j = blockIdx.y;
   for (int t = threadIdx.x; t < N; t += FT) tw[t] = twg[t];
   const cx<T>* f = scratch + size_t(2 * j) * NG + size_t(z) * PL;
-#pragma unroll 4
+#pragma unroll 8
   for (int e = threadIdx.x; e < PL; e += FT) {
     const int yy = e / N, x = e - yy * N;
     buf[yy * kPitch<N> + x] = f[e];
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(FT) k_hx_inv_plane(const cx<T>* __restrict__ s
   cfft_slow<N, true, FT>(buf, tw);
   cfft_fast<N, true, FT>(buf, tw);
   cx<T>* o = out + size_t(j0 + j) * NG + size_t(z) * PL;
-#pragma unroll 4
+#pragma unroll 8
   for (int e = threadIdx.x; e < PL; e += FT) {
     const int yy = e / N, x = e - yy * N;
     o[e] = buf[yy * kPitch<N> + x];
