@@ -34,8 +34,8 @@ sys.path.insert(0, ROOT)
 METRIC = "Vx·Ψ pair-FFTs/s and PT-IM steps/s vs plain FP64 GPU form; serve p50/p99"
 # DRAM bytes (read + write) per steady-state launch of the 64^3 FP32 exchange kernel: mean of two
 # launches (2.849 and 2.951 GB) of an ncu --set full capture with the 16 x 16 pair tiles the
-# benchmark cell uses (N = 64 orbitals, the same launch shape), taken after the swizzled
-# plane-transpose buffer; the kernel is unchanged since that capture
+# benchmark cell uses (N = 64 orbitals, the same launch shape), taken on the kernel with one 5-D
+# TMA copy per plane or slab; the kernel is unchanged since that capture
 EXCHANGE64_TRAFFIC_PER_LAUNCH = 2.90e9
 UNIT = "PT-IM steps/s"
 WORKLOAD = "ptim_ace_step_64^3_N320_128site_L20.5"
