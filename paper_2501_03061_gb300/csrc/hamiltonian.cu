@@ -19,9 +19,24 @@ namespace pt {
 template <class T>
 void apply_h_batch_fixed(int n, const cx<T>* psi, const double* vloc, const cx<T>* X, double alpha, int j0, int nb,
                          cx<T>* scratch, const double* g2d, double ecut, KinField kf, const cx<T>* tw, cx<T>* out,
-                         cudaStream_t st);
+                         cudaStream_t st, const unsigned long long* masks);
 
 namespace {
+
+__global__ void k_sphere_masks(const double* __restrict__ g2, int n, double ecut, unsigned long long* __restrict__ m) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * n) return;
+  const int y = e / n, x = e % n;
+  unsigned long long bits = 0;
+  for (int z = 0; z < n; ++z)
+    if (0.5 * (g2[x] + g2[n + y] + g2[2 * n + z]) <= ecut) bits |= 1ull << z;
+  m[e] = bits;
+}
+
+struct SphereMasks {
+  unsigned long long* d = nullptr;
+  ~SphereMasks() { cudaFree(d); }
+};
 
 constexpr int NT = 512;
 constexpr int MAXE = kMaxDim * kMaxDim;
@@ -165,9 +180,12 @@ void apply_h_t(pt_ctx* ctx, const cx<T>* psi, int M, cx<T>* out, const double* v
   mb = std::min(mb, M);
   cx<T>* scratch = static_cast<cx<T>*>(ctx->get("h_scratch", 2 * size_t(mb) * field));
   if (fixed_cubic(g)) {
+    const unsigned long long* masks =
+        sizeof(T) == 4 ? sphere_masks(ctx, g, static_cast<const double*>(ft.g2d), ecut, st) : nullptr;
     for (int j0 = 0; j0 < M; j0 += mb)
       apply_h_batch_fixed<T>(g.nx, psi, vloc, X, alpha, j0, std::min(mb, M - j0), scratch,
-                             static_cast<const double*>(ft.g2d), ecut, kf, static_cast<const cx<T>*>(ft.tw), out, st);
+                             static_cast<const double*>(ft.g2d), ecut, kf, static_cast<const cx<T>*>(ft.tw), out, st,
+                             masks);
     return;
   }
   set_attrs<T>();
@@ -194,6 +212,21 @@ void apply_h(pt_ctx* ctx, const void* psi, int M, void* out, const double* vloc,
   else
     apply_h_t<float>(ctx, static_cast<const c64*>(psi), M, static_cast<c64*>(out), vloc, static_cast<const c64*>(X),
                      alpha, ecut, g, prec, st, A);
+}
+
+const unsigned long long* sphere_masks(pt_ctx* ctx, const pt_grid& g, const double* g2d, double ecut,
+                                       cudaStream_t st) {
+  if (g.nx != g.ny || g.nx != g.nz || g.nx > 64) fail(PT_INVALID_ARG, "sphere masks: cubic grids of side <= 64");
+  char key[160];
+  snprintf(key, sizeof(key), "sphere_masks:%d:%.17g:%.17g:%.17g:%.17g", g.nx, g.L[0], g.L[1], g.L[2], ecut);
+  auto it = ctx->caches.find(key);
+  if (it != ctx->caches.end()) return std::static_pointer_cast<SphereMasks>(it->second)->d;
+  auto sm = std::make_shared<SphereMasks>();
+  const int n = g.nx;
+  PT_CUDA_CHECK(cudaMalloc(&sm->d, size_t(n) * n * sizeof(unsigned long long)));
+  PT_LAUNCH(k_sphere_masks, (n * n + 255) / 256, 256, 0, st, g2d, n, ecut, sm->d);
+  ctx->caches[key] = sm;
+  return sm->d;
 }
 
 KinField make_kin_field(const pt_grid& g, const double* A) {

@@ -64,7 +64,8 @@ __global__ void __launch_bounds__(FT) k_hx_fwd_plane(const cx<T>* __restrict__ p
 template <int N, class T>
 __global__ void __launch_bounds__(FT) k_hx_column(cx<T>* __restrict__ scratch, const double* __restrict__ g2,
                                                   double ecut, KinField kf, T inv_ng,
-                                                  const cx<T>* __restrict__ twg) {
+                                                  const cx<T>* __restrict__ twg,
+                                                  const unsigned long long* __restrict__ masks) {
   extern __shared__ unsigned char smem_raw[];
   cx<T>* ba = reinterpret_cast<cx<T>*>(smem_raw);
   cx<T>* bb = ba + N * kPitch<N>;
@@ -72,6 +73,21 @@ __global__ void __launch_bounds__(FT) k_hx_column(cx<T>* __restrict__ scratch, c
   constexpr size_t NG = size_t(N) * N * N;
   const int yrow = blockIdx.x, j = blockIdx.y;
   for (int t = threadIdx.x; t < N; t += FT) tw[t] = twg[t];
+  // FP32 form: the sphere test from the exact FP64 masks, the kinetic factor in FP32 from per-axis
+  // terms (an FP64 operation per grid point would take this pass's time on this part's FP64 pipe)
+  __shared__ unsigned long long mrow[N];
+  __shared__ float kx[N], kz[N];
+  __shared__ float ky;
+  if constexpr (sizeof(T) == 4) {
+    for (int t = threadIdx.x; t < N; t += FT) {
+      mrow[t] = masks[size_t(yrow) * N + t];
+      const double w = double(wrapped_freq(t, N));
+      kx[t] = float(0.5 * g2[t] + (kf.on ? w * kf.c[0] : 0.0));
+      kz[t] = float(0.5 * g2[2 * N + t] + (kf.on ? w * kf.c[2] : 0.0));
+    }
+    if (threadIdx.x == 0)
+      ky = float(0.5 * g2[N + yrow] + (kf.on ? double(wrapped_freq(yrow, N)) * kf.c[1] + kf.a2h : 0.0));
+  }
   cx<T>* fa = scratch + size_t(2 * j) * NG;
   cx<T>* fb = fa + NG;
 #pragma unroll 8
@@ -84,20 +100,33 @@ __global__ void __launch_bounds__(FT) k_hx_column(cx<T>* __restrict__ scratch, c
   __syncthreads();
   cfft_slow<N, false, FT>(ba, tw);
   cfft_slow<N, false, FT>(bb, tw);
-  // |G|^2 and the sphere test in FP64 so that the cutoff boundary does not depend on the precision
-  const double* g2x = g2;
-  const double* g2y = g2 + N;
-  const double* g2z = g2 + 2 * N;
+  if constexpr (sizeof(T) == 4) {
 #pragma unroll 8
-  for (int e = threadIdx.x; e < N * N; e += FT) {
-    const int z = e / N, x = e - z * N;
-    const double half = 0.5 * (g2x[x] + g2y[yrow] + g2z[z]);
-    cx<T> v = czero<T>();
-    if (half <= ecut) {
-      const double kin = half + kin_shift(kf, x, yrow, z, N, N, N);  // 1/2 |G + A|^2
-      v = (ba[z * kPitch<N> + x] * T(kin) + bb[z * kPitch<N> + x]) * inv_ng;
+    for (int e = threadIdx.x; e < N * N; e += FT) {
+      const int z = e / N, x = e - z * N;
+      cx<T> v = czero<T>();
+      if ((mrow[x] >> z) & 1ull) {
+        const float kin = kx[x] + (ky + kz[z]);  // 1/2 |G + A|^2
+        v = (ba[z * kPitch<N> + x] * kin + bb[z * kPitch<N> + x]) * inv_ng;
+      }
+      ba[z * kPitch<N> + x] = v;
     }
-    ba[z * kPitch<N> + x] = v;
+  } else {
+    // |G|^2 and the sphere test in FP64 so that the cutoff boundary does not depend on the precision
+    const double* g2x = g2;
+    const double* g2y = g2 + N;
+    const double* g2z = g2 + 2 * N;
+#pragma unroll 8
+    for (int e = threadIdx.x; e < N * N; e += FT) {
+      const int z = e / N, x = e - z * N;
+      const double half = 0.5 * (g2x[x] + g2y[yrow] + g2z[z]);
+      cx<T> v = czero<T>();
+      if (half <= ecut) {
+        const double kin = half + kin_shift(kf, x, yrow, z, N, N, N);  // 1/2 |G + A|^2
+        v = (ba[z * kPitch<N> + x] * T(kin) + bb[z * kPitch<N> + x]) * inv_ng;
+      }
+      ba[z * kPitch<N> + x] = v;
+    }
   }
   __syncthreads();
   cfft_slow<N, true, FT>(ba, tw);
@@ -137,7 +166,8 @@ __global__ void __launch_bounds__(FT) k_hx_inv_plane(const cx<T>* __restrict__ s
 
 template <int N, class T>
 void h_batch_n(const cx<T>* psi, const double* vloc, const cx<T>* X, T alpha, int j0, int nb, cx<T>* scratch,
-               const double* g2d, double ecut, KinField kf, const cx<T>* tw, cx<T>* out, cudaStream_t st) {
+               const double* g2d, double ecut, KinField kf, const cx<T>* tw, cx<T>* out, cudaStream_t st,
+               const unsigned long long* masks) {
   static DeviceOnce once;
   const size_t one = tile_bytes_n<N, T>() + N * sizeof(cx<T>);
   const size_t two = 2 * tile_bytes_n<N, T>() + N * sizeof(cx<T>);
@@ -148,7 +178,7 @@ void h_batch_n(const cx<T>* psi, const double* vloc, const cx<T>* X, T alpha, in
   });
   constexpr double ng = double(N) * N * N;
   PT_LAUNCH((k_hx_fwd_plane<N, T>), dim3(N, 2 * nb), FT, one, st, psi, vloc, X, alpha, j0, scratch, tw);
-  PT_LAUNCH((k_hx_column<N, T>), dim3(N, nb), FT, two, st, scratch, g2d, ecut, kf, T(1.0 / ng), tw);
+  PT_LAUNCH((k_hx_column<N, T>), dim3(N, nb), FT, two, st, scratch, g2d, ecut, kf, T(1.0 / ng), tw, masks);
   PT_LAUNCH((k_hx_inv_plane<N, T>), dim3(N, nb), FT, one, st, scratch, j0, out, tw);
 }
 
@@ -157,11 +187,12 @@ void h_batch_n(const cx<T>* psi, const double* vloc, const cx<T>* X, T alpha, in
 template <class T>
 void apply_h_batch_fixed(int n, const cx<T>* psi, const double* vloc, const cx<T>* X, double alpha, int j0, int nb,
                          cx<T>* scratch, const double* g2d, double ecut, KinField kf, const cx<T>* tw, cx<T>* out,
-                         cudaStream_t st) {
+                         cudaStream_t st, const unsigned long long* masks) {
+  if (sizeof(T) == 4 && !masks) fail(PT_INVALID_ARG, "FP32 column pass without its sphere masks");
   switch (n) {
 #define PT_CASE(s)                                                                                     \
   case s:                                                                                              \
-    h_batch_n<s, T>(psi, vloc, X, T(alpha), j0, nb, scratch, g2d, ecut, kf, tw, out, st);              \
+    h_batch_n<s, T>(psi, vloc, X, T(alpha), j0, nb, scratch, g2d, ecut, kf, tw, out, st, masks);       \
     return;
     PT_FIXED_SIZES(PT_CASE)
 #undef PT_CASE
@@ -171,8 +202,10 @@ void apply_h_batch_fixed(int n, const cx<T>* psi, const double* vloc, const cx<T
 }
 
 template void apply_h_batch_fixed<float>(int, const c64*, const double*, const c64*, double, int, int, c64*,
-                                         const double*, double, KinField, const c64*, c64*, cudaStream_t);
+                                         const double*, double, KinField, const c64*, c64*, cudaStream_t,
+                                         const unsigned long long*);
 template void apply_h_batch_fixed<double>(int, const c128*, const double*, const c128*, double, int, int, c128*,
-                                          const double*, double, KinField, const c128*, c128*, cudaStream_t);
+                                          const double*, double, KinField, const c128*, c128*, cudaStream_t,
+                                          const unsigned long long*);
 
 }  // namespace pt

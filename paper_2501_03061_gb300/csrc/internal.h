@@ -124,6 +124,11 @@ void anderson_update(pt_ctx* ctx, cx<T>* x, const cx<T>* r, const cx<T>* const* 
                      double beta, cx<T>* dxp, size_t n, cudaStream_t st);
 
 // ---- Hamiltonian (hamiltonian.cu) ----
+// sphere masks of the compile-time column passes (cubic grids of side n <= 64): bit z of
+// mask[y * n + x] is set when 0.5 (g2[x] + g2[n + y] + g2[2n + z]) <= ecut, the FP64 test of the
+// basis sphere, evaluated once per (grid, ecut) and kept in the context
+const unsigned long long* sphere_masks(pt_ctx* ctx, const pt_grid& g, const double* g2d, double ecut,
+                                       cudaStream_t st);
 // out = P_sph[ -1/2 Lap psi + y ],  y = vloc*psi + alpha*X (X may be null)
 // A: vector potential of the velocity-gauge field (host double[3]; null = no field)
 void apply_h(pt_ctx* ctx, const void* psi, int M, void* out, const double* vloc, const void* X, double alpha,

@@ -69,7 +69,8 @@ __global__ void __launch_bounds__(FT) k_pc_fwd_plane(const cx<T>* __restrict__ r
 template <int N, class T>
 __global__ void __launch_bounds__(FT) k_pc_column(cx<T>* __restrict__ scratch, const double* __restrict__ g2,
                                                   double ecut, KinField kf, double dt, const c128* __restrict__ A,
-                                                  int lda, int j0, const cx<T>* __restrict__ twg) {
+                                                  int lda, int j0, const cx<T>* __restrict__ twg,
+                                                  const unsigned long long* __restrict__ masks) {
   extern __shared__ unsigned char smem_raw[];
   cx<T>* ba = reinterpret_cast<cx<T>*>(smem_raw);
   cx<T>* tw = ba + N * kPitch<N>;
@@ -78,6 +79,22 @@ __global__ void __launch_bounds__(FT) k_pc_column(cx<T>* __restrict__ scratch, c
   const int yrow = blockIdx.x, k = blockIdx.y;
   for (int t = threadIdx.x; t < N; t += FT) tw[t] = twg[t];
   const double shift = A[size_t(j0 + k) * lda + (j0 + k)].re;
+  // FP32 form: the sphere test from the exact FP64 masks, the factor in FP32 from per-axis kinetic
+  // terms (M only chooses the iteration path, so FP32 rounding of it leaves the fixed point alone;
+  // an FP64 division per grid point would set this pass's time on this part's FP64 pipe)
+  __shared__ unsigned long long mrow[N];
+  __shared__ float kx[N], kz[N];
+  __shared__ float ky;
+  if constexpr (sizeof(T) == 4) {
+    for (int t = threadIdx.x; t < N; t += FT) {
+      mrow[t] = masks[size_t(yrow) * N + t];
+      const double w = double(wrapped_freq(t, N));
+      kx[t] = float(0.5 * g2[t] + (kf.on ? w * kf.c[0] : 0.0));
+      kz[t] = float(0.5 * g2[2 * N + t] + (kf.on ? w * kf.c[2] : 0.0));
+    }
+    if (threadIdx.x == 0)
+      ky = float(0.5 * g2[N + yrow] + (kf.on ? double(wrapped_freq(yrow, N)) * kf.c[1] + kf.a2h : 0.0) - shift);
+  }
   cx<T>* fa = scratch + size_t(k) * NG;
 #pragma unroll 8
   for (int e = threadIdx.x; e < N * N; e += FT) {
@@ -86,18 +103,35 @@ __global__ void __launch_bounds__(FT) k_pc_column(cx<T>* __restrict__ scratch, c
   }
   __syncthreads();
   cfft_slow<N, false, FT>(ba, tw);
-  // |G|^2 and the sphere test in FP64, as in the Hamiltonian kernels
-  const double* g2x = g2;
-  const double* g2y = g2 + N;
-  const double* g2z = g2 + 2 * N;
+  if constexpr (sizeof(T) == 4) {
+    const float hdt = float(0.5 * dt), fng = float(inv_ng);
 #pragma unroll 8
-  for (int e = threadIdx.x; e < N * N; e += FT) {
-    const int z = e / N, x = e - z * N;
-    const double half = 0.5 * (g2x[x] + g2y[yrow] + g2z[z]);
-    const cx<T> v = ba[z * kPitch<N> + x];
-    ba[z * kPitch<N> + x] = half <= ecut
-                                ? cmul(v, pc_factor<T>(half + kin_shift(kf, x, yrow, z, N, N, N), shift, dt, inv_ng))
-                                : v * T(inv_ng);
+    for (int e = threadIdx.x; e < N * N; e += FT) {
+      const int z = e / N, x = e - z * N;
+      const cx<T> v = ba[z * kPitch<N> + x];
+      if ((mrow[x] >> z) & 1ull) {
+        // (1 - i th) / (1 + th^2) / Ng with th = dt/2 (|G + A|^2/2 - Re A_kk)
+        const float th = hdt * (kx[x] + (ky + kz[z]));
+        const float sc = fng / (1.f + th * th);
+        ba[z * kPitch<N> + x] = cmul(v, cx<T>{sc, -th * sc});
+      } else {
+        ba[z * kPitch<N> + x] = v * fng;
+      }
+    }
+  } else {
+    // |G|^2 and the sphere test in FP64, as in the Hamiltonian kernels
+    const double* g2x = g2;
+    const double* g2y = g2 + N;
+    const double* g2z = g2 + 2 * N;
+#pragma unroll 8
+    for (int e = threadIdx.x; e < N * N; e += FT) {
+      const int z = e / N, x = e - z * N;
+      const double half = 0.5 * (g2x[x] + g2y[yrow] + g2z[z]);
+      const cx<T> v = ba[z * kPitch<N> + x];
+      ba[z * kPitch<N> + x] = half <= ecut ? cmul(v, pc_factor<T>(half + kin_shift(kf, x, yrow, z, N, N, N), shift,
+                                                                   dt, inv_ng))
+                                           : v * T(inv_ng);
+    }
   }
   __syncthreads();
   cfft_slow<N, true, FT>(ba, tw);
@@ -137,7 +171,7 @@ __global__ void __launch_bounds__(FT) k_pc_inv_plane(const cx<T>* __restrict__ s
 
 template <int N, class T>
 void pc_batch_n(cx<T>* r, int j0, int nb, cx<T>* scratch, const double* g2d, double ecut, KinField kf, double dt,
-                const c128* A, int lda, const cx<T>* tw, cudaStream_t st) {
+                const c128* A, int lda, const cx<T>* tw, cudaStream_t st, const unsigned long long* masks) {
   static DeviceOnce once;
   const size_t one = pc_tile_bytes<N, T>() + N * sizeof(cx<T>);
   once([&] {
@@ -146,17 +180,19 @@ void pc_batch_n(cx<T>* r, int j0, int nb, cx<T>* scratch, const double* g2d, dou
     PT_CUDA_CHECK(cudaFuncSetAttribute(k_pc_inv_plane<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(one)));
   });
   PT_LAUNCH((k_pc_fwd_plane<N, T>), dim3(N, nb), FT, one, st, r, j0, scratch, tw);
-  PT_LAUNCH((k_pc_column<N, T>), dim3(N, nb), FT, one, st, scratch, g2d, ecut, kf, dt, A, lda, j0, tw);
+  PT_LAUNCH((k_pc_column<N, T>), dim3(N, nb), FT, one, st, scratch, g2d, ecut, kf, dt, A, lda, j0, tw, masks);
   PT_LAUNCH((k_pc_inv_plane<N, T>), dim3(N, nb), FT, one, st, scratch, j0, r, tw);
 }
 
 template <class T>
 void pc_batch_fixed(int n, cx<T>* r, int j0, int nb, cx<T>* scratch, const double* g2d, double ecut, KinField kf,
-                    double dt, const c128* A, int lda, const cx<T>* tw, cudaStream_t st) {
+                    double dt, const c128* A, int lda, const cx<T>* tw, cudaStream_t st,
+                    const unsigned long long* masks) {
+  if (sizeof(T) == 4 && !masks) fail(PT_INVALID_ARG, "FP32 column pass without its sphere masks");
   switch (n) {
 #define PT_CASE(s)                                                                  \
   case s:                                                                           \
-    pc_batch_n<s, T>(r, j0, nb, scratch, g2d, ecut, kf, dt, A, lda, tw, st);       \
+    pc_batch_n<s, T>(r, j0, nb, scratch, g2d, ecut, kf, dt, A, lda, tw, st, masks); \
     return;
     PT_FIXED_SIZES(PT_CASE)
 #undef PT_CASE
@@ -280,8 +316,9 @@ void precondition_t(pt_ctx* ctx, cx<T>* r, int N, const c128* A, double dt, doub
   const cx<T>* twg = static_cast<const cx<T>*>(ft.tw);
   const double* g2d = static_cast<const double*>(ft.g2d);
   if (fixed_cubic(g)) {
+    const unsigned long long* masks = sizeof(T) == 4 ? sphere_masks(ctx, g, g2d, ecut, st) : nullptr;
     for (int j0 = 0; j0 < N; j0 += pb)
-      pc_batch_fixed<T>(g.nx, r, j0, std::min(pb, N - j0), scratch, g2d, ecut, kf, dt, A, N, twg, st);
+      pc_batch_fixed<T>(g.nx, r, j0, std::min(pb, N - j0), scratch, g2d, ecut, kf, dt, A, N, twg, st, masks);
     return;
   }
   static DeviceOnce once;
