@@ -17,7 +17,7 @@ namespace pt {
 
 // compile-time-size passes for cubic grids (hamiltonian_fixed.cu)
 template <class T>
-void apply_h_batch_fixed(int n, const cx<T>* psi, const double* vloc, const cx<T>* X, double alpha, int j0, int nb,
+void apply_h_batch_fixed(int n, const cx<T>* psi, const T* vloc, const cx<T>* X, double alpha, int j0, int nb,
                          cx<T>* scratch, const double* g2d, double ecut, KinField kf, const cx<T>* tw, cx<T>* out,
                          cudaStream_t st, const unsigned long long* masks);
 
@@ -31,6 +31,12 @@ __global__ void k_sphere_masks(const double* __restrict__ g2, int n, double ecut
   for (int z = 0; z < n; ++z)
     if (0.5 * (g2[x] + g2[n + y] + g2[2 * n + z]) <= ecut) bits |= 1ull << z;
   m[e] = bits;
+}
+
+// V_loc in the orbital precision (the FP32 passes multiply by the FP32-rounded value either way)
+__global__ void k_to_float(const double* __restrict__ a, size_t n, float* __restrict__ b) {
+  for (size_t e = size_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n; e += size_t(gridDim.x) * blockDim.x)
+    b[e] = float(a[e]);
 }
 
 struct SphereMasks {
@@ -180,10 +186,19 @@ void apply_h_t(pt_ctx* ctx, const cx<T>* psi, int M, cx<T>* out, const double* v
   mb = std::min(mb, M);
   cx<T>* scratch = static_cast<cx<T>*>(ctx->get("h_scratch", 2 * size_t(mb) * field));
   if (fixed_cubic(g)) {
-    const unsigned long long* masks =
-        sizeof(T) == 4 ? sphere_masks(ctx, g, static_cast<const double*>(ft.g2d), ecut, st) : nullptr;
+    const unsigned long long* masks = nullptr;
+    const T* vl = nullptr;
+    if constexpr (sizeof(T) == 4) {
+      masks = sphere_masks(ctx, g, static_cast<const double*>(ft.g2d), ecut, st);
+      float* v32 = static_cast<float*>(ctx->get("h_vloc32", ng * sizeof(float)));
+      PT_LAUNCH(k_to_float, int(std::min<size_t>((ng + 255) / 256, size_t(ctx->num_sms) * 8)), 256, 0, st, vloc, ng,
+                v32);
+      vl = v32;
+    } else {
+      vl = vloc;
+    }
     for (int j0 = 0; j0 < M; j0 += mb)
-      apply_h_batch_fixed<T>(g.nx, psi, vloc, X, alpha, j0, std::min(mb, M - j0), scratch,
+      apply_h_batch_fixed<T>(g.nx, psi, vl, X, alpha, j0, std::min(mb, M - j0), scratch,
                              static_cast<const double*>(ft.g2d), ecut, kf, static_cast<const cx<T>*>(ft.tw), out, st,
                              masks);
     return;

@@ -21,7 +21,7 @@ constexpr size_t tile_bytes_n() {
 
 // item k of the batch: psi_{j0+k/2} (k even) or y_{j0+k/2} = V_loc psi + alpha X (k odd)
 template <int N, class T>
-__global__ void __launch_bounds__(FT) k_hx_fwd_plane(const cx<T>* __restrict__ psi, const double* __restrict__ vloc,
+__global__ void __launch_bounds__(FT) k_hx_fwd_plane(const cx<T>* __restrict__ psi, const T* __restrict__ vloc,
                                                      const cx<T>* __restrict__ X, T alpha, int j0,
                                                      cx<T>* __restrict__ scratch, const cx<T>* __restrict__ twg) {
   extern __shared__ unsigned char smem_raw[];
@@ -34,12 +34,12 @@ __global__ void __launch_bounds__(FT) k_hx_fwd_plane(const cx<T>* __restrict__ p
   const size_t off = size_t(j0 + (k >> 1)) * NG + size_t(z) * PL;
   const cx<T>* f = psi + off;
   if (k & 1) {
-    const double* v = vloc + size_t(z) * PL;
+    const T* v = vloc + size_t(z) * PL;
     const cx<T>* xx = X ? X + off : nullptr;
 #pragma unroll 8
     for (int e = threadIdx.x; e < PL; e += FT) {
       const int yy = e / N, x = e - yy * N;
-      cx<T> val = f[e] * T(v[e]);
+      cx<T> val = f[e] * v[e];
       if (xx) val = val + xx[e] * alpha;
       buf[yy * kPitch<N> + x] = val;
     }
@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(FT) k_hx_inv_plane(const cx<T>* __restrict__ s
 }
 
 template <int N, class T>
-void h_batch_n(const cx<T>* psi, const double* vloc, const cx<T>* X, T alpha, int j0, int nb, cx<T>* scratch,
+void h_batch_n(const cx<T>* psi, const T* vloc, const cx<T>* X, T alpha, int j0, int nb, cx<T>* scratch,
                const double* g2d, double ecut, KinField kf, const cx<T>* tw, cx<T>* out, cudaStream_t st,
                const unsigned long long* masks) {
   static DeviceOnce once;
@@ -185,7 +185,7 @@ void h_batch_n(const cx<T>* psi, const double* vloc, const cx<T>* X, T alpha, in
 }  // namespace
 
 template <class T>
-void apply_h_batch_fixed(int n, const cx<T>* psi, const double* vloc, const cx<T>* X, double alpha, int j0, int nb,
+void apply_h_batch_fixed(int n, const cx<T>* psi, const T* vloc, const cx<T>* X, double alpha, int j0, int nb,
                          cx<T>* scratch, const double* g2d, double ecut, KinField kf, const cx<T>* tw, cx<T>* out,
                          cudaStream_t st, const unsigned long long* masks) {
   if (sizeof(T) == 4 && !masks) fail(PT_INVALID_ARG, "FP32 column pass without its sphere masks");
@@ -201,7 +201,7 @@ void apply_h_batch_fixed(int n, const cx<T>* psi, const double* vloc, const cx<T
   }
 }
 
-template void apply_h_batch_fixed<float>(int, const c64*, const double*, const c64*, double, int, int, c64*,
+template void apply_h_batch_fixed<float>(int, const c64*, const float*, const c64*, double, int, int, c64*,
                                          const double*, double, KinField, const c64*, c64*, cudaStream_t,
                                          const unsigned long long*);
 template void apply_h_batch_fixed<double>(int, const c128*, const double*, const c128*, double, int, int, c128*,
