@@ -136,7 +136,7 @@ struct pt_ctx {
   int ptim_ace_warm = 1;       // option: a chained step's first outer pass uses the previous step's ACE
   bool ptim_warm_valid = false;  // "ptim_xi" holds the last ACE of the step whose output is fingerprinted
   std::string ptim_warm_key;     // sizes, grid, kernel and precision of that step
-  double ptim_warm_fp[2] = {0.0, 0.0};  // fingerprint of that step's output (phi, sigma)
+  unsigned long long ptim_warm_fp[2] = {0, 0};  // fingerprint of that step's output (phi, sigma)
   int ptim_q_n = 0;            // the "ptim_Q" buffer holds a complete unitary ptim_q_n x ptim_q_n basis
   // option: 64^3 FP32 exchange engine: 0 the launch-pipelined TMA kernel (roles A, B, C, D), 1 the
   // compile-time tile kernels, 2 one persistent cooperative launch per application

@@ -114,35 +114,46 @@ __global__ void k_pure_check(const c128* __restrict__ sig, int N, double* __rest
   }
 }
 
-// Fingerprint of a state (phi, sigma): sum_e w(e) (re_e + 3 im_e) with hashed weights w in [0.5, 1.5),
-// over a fixed grid and a fixed reduction order, so that equal states give bit-equal sums.  Stage 1:
-// one partial per block; stage 2 (one block) sums the partials in order.
+// Fingerprint of a state (phi, sigma): the wrapping 64-bit sum over elements e of a mixed hash of
+// (e, bit pattern of element e).  Integer arithmetic only, so it is exact and independent of the
+// reduction order; any change of a bit of any element changes it except with probability ~2^-64.
+// Stage 1: one partial per block; stage 2 (one block) sums the partials.
 constexpr int FP_BLOCKS = 256;
-__device__ __forceinline__ double fp_weight(size_t e) {
-  uint64_t h = uint64_t(e) * 0x9E3779B97F4A7C15ull;
-  h ^= h >> 31;
+__device__ __forceinline__ uint64_t fp_mix(uint64_t h) {  // splitmix64 finaliser (Steele, Lea, Flood 2014)
+  h ^= h >> 30;
   h *= 0xBF58476D1CE4E5B9ull;
-  h ^= h >> 29;
-  return 0.5 + double(h >> 11) * (1.0 / 9007199254740992.0);
+  h ^= h >> 27;
+  h *= 0x94D049BB133111EBull;
+  h ^= h >> 31;
+  return h;
+}
+__device__ __forceinline__ uint64_t fp_bits(float re, float im) {
+  return (uint64_t(__float_as_uint(re)) << 32) | __float_as_uint(im);
+}
+__device__ __forceinline__ uint64_t fp_bits(double re, double im) {
+  return fp_mix(uint64_t(__double_as_longlong(re))) ^ uint64_t(__double_as_longlong(im));
 }
 template <class T>
-__global__ void __launch_bounds__(256) k_fingerprint(const cx<T>* __restrict__ a, size_t n, double* __restrict__ part) {
-  double s = 0.0;
-  for (size_t e = size_t(blockIdx.x) * 256 + threadIdx.x; e < n; e += size_t(FP_BLOCKS) * 256)
-    s += fp_weight(e) * (double(a[e].re) + 3.0 * double(a[e].im));
+__global__ void __launch_bounds__(256) k_fingerprint(const cx<T>* __restrict__ a, size_t n,
+                                                     unsigned long long* __restrict__ part) {
+  unsigned long long s = 0;
+  for (size_t e = size_t(blockIdx.x) * 256 + threadIdx.x; e < n; e += size_t(FP_BLOCKS) * 256) {
+    const cx<T> v = a[e];
+    s += fp_mix(fp_bits(v.re, v.im) ^ (uint64_t(e) * 0x9E3779B97F4A7C15ull));
+  }
   for (int o = 16; o; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  __shared__ double sh[8];
+  __shared__ unsigned long long sh[8];
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double r = 0.0;
+    unsigned long long r = 0;
     for (int w = 0; w < 8; ++w) r += sh[w];
     part[blockIdx.x] = r;
   }
 }
-__global__ void k_fingerprint_sum(const double* __restrict__ part, double* __restrict__ out) {
+__global__ void k_fingerprint_sum(const unsigned long long* __restrict__ part, unsigned long long* __restrict__ out) {
   if (threadIdx.x == 0) {
-    double r = 0.0;
+    unsigned long long r = 0;
     for (int b = 0; b < FP_BLOCKS; ++b) r += part[b];
     out[0] = r;
   }
@@ -160,9 +171,21 @@ __global__ void k_weighted_diag(const cx<T>* __restrict__ a, const cx<T>* __rest
   const cx<T>* x = a + size_t(i) * ng;
   const cx<T>* y = b + size_t(i) * ng;
   double s = 0;
-  for (size_t e = threadIdx.x; e < ng; e += blockDim.x) {
-    const cx<T> u = x[e], v = y[e];
-    s += double(u.re * v.re + u.im * v.im);
+  if constexpr (sizeof(T) == 4) {
+    float sf = 0.f, cf = 0.f;  // compensated FP32 sum per thread, FP64 across threads
+    for (size_t e = threadIdx.x; e < ng; e += blockDim.x) {
+      const cx<T> u = x[e], v = y[e];
+      const float yv = (u.re * v.re + u.im * v.im) - cf;
+      const float t = sf + yv;
+      cf = (t - sf) - yv;
+      sf = t;
+    }
+    s = double(sf) - double(cf);
+  } else {
+    for (size_t e = threadIdx.x; e < ng; e += blockDim.x) {
+      const cx<T> u = x[e], v = y[e];
+      s += double(u.re * v.re + u.im * v.im);
+    }
   }
   for (int o = 16; o; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
   __shared__ double sh[32];
@@ -341,18 +364,19 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
   char warm_key[256];
   snprintf(warm_key, sizeof(warm_key), "%d:%d:%d:%d:%.17g:%.17g:%.17g:%d:%.17g:%.17g:%d", N, g.nx, g.ny, g.nz,
            g.L[0], g.L[1], g.L[2], kern.type, kern.mu, kern.g0, int(prec));
-  double* fpd = static_cast<double*>(S.buf("ptim_fingerprint", (2 * FP_BLOCKS + 2) * sizeof(double)));
-  auto fingerprint = [&](const cx<T>* ph, const c128* sg, double out[2]) {
+  auto* fpd = static_cast<unsigned long long*>(
+      S.buf("ptim_fingerprint", (2 * FP_BLOCKS + 2) * sizeof(unsigned long long)));
+  auto fingerprint = [&](const cx<T>* ph, const c128* sg, unsigned long long out[2]) {
     PT_LAUNCH(k_fingerprint<T>, FP_BLOCKS, 256, 0, st, ph, S.n1, fpd);
     PT_LAUNCH(k_fingerprint_sum, 1, 32, 0, st, fpd, fpd + 2 * FP_BLOCKS);
     PT_LAUNCH(k_fingerprint<double>, FP_BLOCKS, 256, 0, st, sg, S.n2, fpd + FP_BLOCKS);
     PT_LAUNCH(k_fingerprint_sum, 1, 32, 0, st, fpd + FP_BLOCKS, fpd + 2 * FP_BLOCKS + 1);
-    PT_CUDA_CHECK(cudaMemcpyAsync(out, fpd + 2 * FP_BLOCKS, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    PT_CUDA_CHECK(cudaMemcpyAsync(out, fpd + 2 * FP_BLOCKS, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     PT_CUDA_CHECK(cudaStreamSynchronize(st));
   };
   bool ace_warm = false;
   if (ctx->ptim_ace_warm && P.use_ace && ctx->ptim_warm_valid && ctx->ptim_warm_key == warm_key) {
-    double f[2];
+    unsigned long long f[2];
     fingerprint(phin, sign, f);
     ace_warm = f[0] == ctx->ptim_warm_fp[0] && f[1] == ctx->ptim_warm_fp[1];
   }

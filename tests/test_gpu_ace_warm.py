@@ -77,3 +77,28 @@ def test_warm_start_needs_the_previous_output(ctx):
                                  torch.from_numpy(w2.vloc).cuda(), **kw)["ace_warm"]
     finally:
         ctx.set_option("ptim_ace_warm", 1)
+
+
+def test_warm_start_sees_a_one_ulp_change_fp32(ctx):
+    """The state fingerprint hashes bit patterns: one unit in the last place of one element of Phi
+    (complex64) or of sigma (complex128) is a different input."""
+    w = synth.small_cell(77, 12, 8.0, 6, kT=0.05, ecut=6.0)
+    phi = torch.from_numpy(w.phi.astype(np.complex64)).cuda()
+    sigma = torch.from_numpy(w.sigma.copy()).cuda()
+    vloc = torch.from_numpy(w.vloc).cuda()
+    kw = dict(cell=w.cell, kernel=w.kernel, precision="fp32", dt=0.5, ecut=6.0, tol=1e-5)
+    ctx.set_option("ptim_ace_warm", 1)
+    ctx.trim()
+    try:
+        assert not ctx.ptim_step(phi, sigma, vloc, **kw)["ace_warm"]
+        assert ctx.ptim_step(phi, sigma, vloc, **kw)["ace_warm"]
+        re = torch.view_as_real(phi)
+        re[3, 1, 2, 0, 1] = torch.nextafter(re[3, 1, 2, 0, 1], torch.tensor(np.inf, device="cuda"))
+        assert not ctx.ptim_step(phi, sigma, vloc, **kw)["ace_warm"]
+        assert ctx.ptim_step(phi, sigma, vloc, **kw)["ace_warm"]
+        sr = torch.view_as_real(sigma)
+        sr[2, 4, 0] = torch.nextafter(sr[2, 4, 0], torch.tensor(-np.inf, device="cuda", dtype=torch.float64))
+        assert not ctx.ptim_step(phi, sigma, vloc, **kw)["ace_warm"]
+        assert ctx.ptim_step(phi, sigma, vloc, **kw)["ace_warm"]
+    finally:
+        ctx.set_option("ptim_ace_warm", 1)
