@@ -1097,7 +1097,8 @@ def run_gb300(args):
             "iterations": [{"outer": s["outer"], "inner": s["inner"], "residual": _finite(s["residual"]),
                             "converged": s["converged"], "eig_sweeps": s["eig_sweeps"], "ace_warm": s["ace_warm"],
                             "pass_inner": s["pass_inner"], "total_energy_in": _finite(s.get("total_energy")),
-                            "orth_error": _finite(s.get("orth_error"))} for s in stats],
+                            "orth_error": _finite(s.get("orth_error")), "sinv_path": s["sinv_path"],
+                            "s_dev_max": _finite(s.get("s_dev_max"))} for s in stats],
             "phases_ms_per_step": {k: sum(s["phase_ms"][k] for s in stats) / len(stats)
                                    for k in stats[0]["phase_ms"]},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -119,6 +119,14 @@ pt_status pt_trim(pt_ctx* ctx);
  *                    operator instead of building one, saving an exchange application; the operators
  *                    the step builds and its stopping test are unchanged (64^3 grid, N = 320: 3 ACE
  *                    builds per step against 4).  total_energy is NaN for such steps.  Default 1.
+ *   "ptim_sinv_series"  how the inner iteration forms S^{-1} A, S = <Phi_h|Phi_h> = I + E the
+ *                    overlap of the midpoint block.  1 (default): with e = ||E||_F < 1/4, the cheaper
+ *                    of the Neumann series sum_{k<=K} (-E)^k A (K products, error <= e^{K+1}/(1-e))
+ *                    and the product (I - E)(I + E^2)...(I + E^{2^J}) A (2J+1 products, error
+ *                    <= e^{2^{J+1}}/(1-e)) that reaches 1e-17 relative, unless the Cholesky route
+ *                    is cheaper; 2: the product form wherever it applies; 0: always S = L L^* and
+ *                    S^{-1} A = L^{-*} (L^{-1} A).  The forms agree to FP64 rounding; the series
+ *                    costs one synchronisation per inner iteration to read e.
  *   "scratch_bytes"  bytes of pair/orbital fields one FFT batch may hold (default 512 MiB: the
  *                    cost per pair falls with the pair tile even past L2 residency, 4-10% from
  *                    48 MiB to 512 MiB; smaller values give more, smaller batches).
@@ -346,6 +354,10 @@ typedef struct {
   int passes;               /* inner loops run: one per ACE operator built, plus the warm-started
                                first pass and any pass that kept the operator to finish at tol */
   int pass_inner[16];       /* inner iterations of each of the first 16 passes */
+  int sinv_path[3];         /* inner iterations whose S^{-1} A took [0] the Cholesky route, [1] the
+                               Neumann series in E = S - I, [2] the product form (option
+                               "ptim_sinv_series") */
+  double s_dev_max;         /* largest ||S - I||_F of the midpoint overlaps met (0 with the option off) */
 } pt_ptim_stats;
 
 /* One PT-IM(-ACE) step from (phi, sigma) = (Phi_n, sigma_n) to (Phi_{n+1}, sigma_{n+1}),

@@ -192,6 +192,11 @@ pt_status pt_set_option(pt_ctx* ctx, const char* key, double value) {
       ctx->ptim_precond = value != 0.0 ? 1 : 0;
       return PT_OK;
     }
+    if (std::string(key) == "ptim_sinv_series") {
+      if (!(value == 0.0 || value == 1.0 || value == 2.0)) pt::fail(PT_INVALID_ARG, "ptim_sinv_series must be 0, 1 or 2");
+      ctx->ptim_sinv_series = int(value);
+      return PT_OK;
+    }
     if (std::string(key) == "ptim_ace_warm") {
       ctx->ptim_ace_warm = value != 0.0 ? 1 : 0;
       return PT_OK;
@@ -603,7 +608,8 @@ size_t pt_ptim_footprint(int N, const pt_grid* grid, pt_precision prec, int ande
   const size_t nn = size_t(N) * N * sizeof(double) * 2;
   const size_t gram_parts = size_t(4 * 160 + 64) * nn;  // split partials, bounded by 4 waves of tiles
   const size_t blocks = (12 + 2 * size_t(depth)) * block;
-  const size_t small = 40 * nn + (size_t(64) << 20);
+  // N x N matrices: the step's named ones, the eigensolver's and the sigma half of the Anderson ring
+  const size_t small = (24 + 2 * size_t(depth)) * nn + (size_t(64) << 20);
   const size_t hxc = 4 * ng * sizeof(double);  // rho, total potential, FFT scratch (params.hxc = 1)
   return blocks + exch + hscr + std::min(gram_parts, size_t(8) * block) + small + hxc;
 }

@@ -1,9 +1,11 @@
 // FP64 dense linear algebra on N x N complex matrices (N up to a few hundred), on the GPU.
 //
 //   zgemm        C = alpha op(A) op(B) + beta C, op in {N, C (conjugate transpose), T}
+//   zgemm_add    C = alpha op(A) op(B) + beta D (D read-only, may differ from C)
 //   heev         Hermitian eigen-decomposition by parallel two-sided cyclic Jacobi
 //                (round-robin pairing; one launch per round; every 2x2 block of the
-//                matrix is updated by J_k^H X J_l in the same launch)
+//                matrix is updated by J_k^H X J_l in the same launch; entries below the
+//                stopping level are not rotated, so late sweeps are mostly copies)
 //   cholesky     blocked lower Cholesky (32-wide panels), error flag on a non-positive or
 //                non-finite pivot
 //   tri_inv      L^{-1} of a lower-triangular matrix, one CTA per column
@@ -28,9 +30,10 @@ __device__ __forceinline__ c128 opval(const c128* A, int lda, char op, int i, in
 
 constexpr int ZT = 16;
 
+// C = alpha op(A) op(B) + beta D  (D may be C itself, or another matrix with leading dimension ldd)
 __global__ void __launch_bounds__(ZT* ZT) k_zgemm(char opA, char opB, int m, int n, int k, c128 alpha,
                                                   const c128* __restrict__ A, int lda, const c128* __restrict__ B,
-                                                  int ldb, c128 beta, c128* __restrict__ C, int ldc) {
+                                                  int ldb, c128 beta, const c128* D, int ldd, c128* C, int ldc) {
   __shared__ c128 As[ZT][ZT + 1];
   __shared__ c128 Bs[ZT][ZT + 1];
   const int tx = threadIdx.x % ZT, ty = threadIdx.x / ZT;
@@ -47,7 +50,7 @@ __global__ void __launch_bounds__(ZT* ZT) k_zgemm(char opA, char opB, int m, int
   }
   if (i < m && j < n) {
     c128 v = cmul(alpha, acc);
-    if (beta.re != 0.0 || beta.im != 0.0) v = v + cmul(beta, C[size_t(i) * ldc + j]);
+    if (beta.re != 0.0 || beta.im != 0.0) v = v + cmul(beta, D[size_t(i) * ldd + j]);
     C[size_t(i) * ldc + j] = v;
   }
 }
@@ -66,15 +69,17 @@ struct Rot {
   c128 u;  // J = [[c, s u], [-s conj(u), c]]
 };
 
-__device__ __forceinline__ Rot jacobi_rot(const c128* A, int N, int p, int q) {
+// the rotation that annihilates a_pq, or the identity (s = 0) when |a_pq|^2 <= thr2 (threshold
+// Jacobi: an entry already below the stopping level is left in place)
+__device__ __forceinline__ Rot jacobi_rot(const c128* A, int N, int p, int q, double thr2) {
   Rot r{1.0, 0.0, c128{1.0, 0.0}};
   if (q >= N) return r;  // padding player
-  const double app = A[size_t(p) * N + p].re, aqq = A[size_t(q) * N + q].re;
   const c128 apq = A[size_t(p) * N + q];
-  // reciprocal square roots in place of square roots and divisions (each a long FP64 sequence on
-  // the round's critical path); an off-diagonal entry below 1e-140 is treated as zero
   const double b2 = apq.re * apq.re + apq.im * apq.im;
-  if (!(b2 > 1e-280)) return r;
+  if (!(b2 > thr2)) return r;
+  const double app = A[size_t(p) * N + p].re, aqq = A[size_t(q) * N + q].re;
+  // reciprocal square roots in place of square roots and divisions (each a long FP64 sequence on
+  // the round's critical path)
   const double rb = rsqrt(b2);  // 1 / |a_pq|
   const double zeta = (aqq - app) * (0.5 * rb);
   const double az = fabs(zeta);
@@ -95,7 +100,7 @@ __device__ __forceinline__ Rot jacobi_rot(const c128* A, int N, int p, int q) {
 constexpr int JB = 8;  // pairs per CTA side (16 x 16 elements): (N/16)^2 CTAs spread over every SM
 
 __global__ void __launch_bounds__(JB* JB) k_jacobi_round(const c128* __restrict__ Ain, c128* __restrict__ Aout,
-                                                         c128* __restrict__ V, int N, int Np, int r) {
+                                                         c128* __restrict__ V, int N, int Np, int r, double thr2) {
   __shared__ Rot rk[JB], rl[JB];
   __shared__ int pk[JB], qk[JB], pl[JB], ql[JB];
   const int kb = blockIdx.y * JB, lb = blockIdx.x * JB;
@@ -105,13 +110,13 @@ __global__ void __launch_bounds__(JB* JB) k_jacobi_round(const c128* __restrict_
     const int k = kb + t;
     if (k < half) {
       jacobi_pair(k, r, Np, &pk[t], &qk[t]);
-      rk[t] = jacobi_rot(Ain, N, pk[t], qk[t]);
+      rk[t] = jacobi_rot(Ain, N, pk[t], qk[t], thr2);
     }
   } else if (t < 2 * JB) {
     const int l = lb + t - JB;
     if (l < half) {
       jacobi_pair(l, r, Np, &pl[t - JB], &ql[t - JB]);
-      rl[t - JB] = jacobi_rot(Ain, N, pl[t - JB], ql[t - JB]);
+      rl[t - JB] = jacobi_rot(Ain, N, pl[t - JB], ql[t - JB], thr2);
     }
   }
   __syncthreads();
@@ -124,27 +129,34 @@ __global__ void __launch_bounds__(JB* JB) k_jacobi_round(const c128* __restrict_
       return (i < N && j < N) ? Ain[size_t(i) * N + j] : czero<double>();
     };
     const c128 x00 = get(p1, p2), x01 = get(p1, q2), x10 = get(q1, p2), x11 = get(q1, q2);
-    // Y = J_a^H X:  J^H = [[c, -s u], [s conj(u), c]]
-    const c128 su = a.u * a.s, suc = conjc(a.u) * a.s;
-    const c128 y00 = x00 * a.c - cmul(su, x10), y01 = x01 * a.c - cmul(su, x11);
-    const c128 y10 = cmul(suc, x00) + x10 * a.c, y11 = cmul(suc, x01) + x11 * a.c;
-    // Z = Y J_b:  J = [[c, s u], [-s conj(u), c]]
-    const c128 tu = b.u * b.s, tuc = conjc(b.u) * b.s;
-    c128 z00 = y00 * b.c - cmul(y01, tuc), z01 = cmul(y00, tu) + y01 * b.c;
-    c128 z10 = y10 * b.c - cmul(y11, tuc), z11 = cmul(y10, tu) + y11 * b.c;
-    if (k == l) {  // the 2x2 block this rotation diagonalises
-      z01 = czero<double>();
-      z10 = czero<double>();
-      z00.im = 0.0;
-      z11.im = 0.0;
-    }
     auto put = [&](int i, int j, c128 v) {
       if (i < N && j < N) Aout[size_t(i) * N + j] = v;
     };
-    put(p1, p2, z00);
-    put(p1, q2, z01);
-    put(q1, p2, z10);
-    put(q1, q2, z11);
+    if (a.s == 0.0 && b.s == 0.0) {  // both rotations the identity: the block is carried over
+      put(p1, p2, x00);
+      put(p1, q2, x01);
+      put(q1, p2, x10);
+      put(q1, q2, x11);
+    } else {
+      // Y = J_a^H X:  J^H = [[c, -s u], [s conj(u), c]]
+      const c128 su = a.u * a.s, suc = conjc(a.u) * a.s;
+      const c128 y00 = x00 * a.c - cmul(su, x10), y01 = x01 * a.c - cmul(su, x11);
+      const c128 y10 = cmul(suc, x00) + x10 * a.c, y11 = cmul(suc, x01) + x11 * a.c;
+      // Z = Y J_b:  J = [[c, s u], [-s conj(u), c]]
+      const c128 tu = b.u * b.s, tuc = conjc(b.u) * b.s;
+      c128 z00 = y00 * b.c - cmul(y01, tuc), z01 = cmul(y00, tu) + y01 * b.c;
+      c128 z10 = y10 * b.c - cmul(y11, tuc), z11 = cmul(y10, tu) + y11 * b.c;
+      if (k == l) {  // the 2x2 block this rotation diagonalises
+        z01 = czero<double>();
+        z10 = czero<double>();
+        z00.im = 0.0;
+        z11.im = 0.0;
+      }
+      put(p1, p2, z00);
+      put(p1, q2, z01);
+      put(q1, p2, z10);
+      put(q1, q2, z11);
+    }
   }
   // V <- V J for the column pairs of this CTA's l-range; the rows are split over the CTAs of the
   // same l-range so every CTA of the grid shares the update
@@ -158,6 +170,7 @@ __global__ void __launch_bounds__(JB* JB) k_jacobi_round(const c128* __restrict_
       const int p2 = pl[tl2], q2 = ql[tl2];
       if (q2 >= N) continue;
       const Rot b = rl[tl2];
+      if (b.s == 0.0) continue;  // identity
       const c128 vp = V[size_t(row) * N + p2], vq = V[size_t(row) * N + q2];
       const c128 tu = b.u * b.s, tuc = conjc(b.u) * b.s;
       V[size_t(row) * N + p2] = vp * b.c - cmul(vq, tuc);
@@ -411,7 +424,13 @@ __global__ void k_small_solve(const double* __restrict__ G, const double* __rest
 void zgemm(char opA, char opB, int m, int n, int k, c128 alpha, const c128* A, int lda, const c128* B, int ldb,
            c128 beta, c128* C, int ldc, cudaStream_t st) {
   dim3 grid((n + ZT - 1) / ZT, (m + ZT - 1) / ZT);
-  PT_LAUNCH(k_zgemm, grid, ZT * ZT, 0, st, opA, opB, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+  PT_LAUNCH(k_zgemm, grid, ZT * ZT, 0, st, opA, opB, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, C, ldc);
+}
+
+void zgemm_add(char opA, char opB, int m, int n, int k, c128 alpha, const c128* A, int lda, const c128* B, int ldb,
+               c128 beta, const c128* D, int ldd, c128* C, int ldc, cudaStream_t st) {
+  dim3 grid((n + ZT - 1) / ZT, (m + ZT - 1) / ZT);
+  PT_LAUNCH(k_zgemm, grid, ZT * ZT, 0, st, opA, opB, m, n, k, alpha, A, lda, B, ldb, beta, D, ldd, C, ldc);
 }
 
 int heev(pt_ctx* ctx, const c128* S, int N, c128* Q, double* d, cudaStream_t st, int max_sweeps, const c128* Q0,
@@ -449,8 +468,13 @@ int heev(pt_ctx* ctx, const c128* S, int N, c128* Q, double* d, cudaStream_t st,
     if (h[0] <= rel_tol * rel_tol * h[1]) break;
     if (h[0] <= 1e-24 * h[1] && h[0] > 0.25 * prev_off) break;
     prev_off = h[0];
+    // entries with |a_pq|^2 at or below the stopping level spread over all N^2 entries are not
+    // rotated: all of them together stay within the stopping test, and late sweeps, where most
+    // entries are there, skip their FP64 arithmetic
+    const double stop2 = rel_tol > 0.0 ? rel_tol * rel_tol * h[1] : floor2;
+    const double thr2 = std::max(1e-280, stop2 / (double(N) * double(N)));
     for (int r = 0; r < Np - 1; ++r) {
-      PT_LAUNCH(k_jacobi_round, grid, JB * JB, 0, st, A0, A1, V, N, Np, r);
+      PT_LAUNCH(k_jacobi_round, grid, JB * JB, 0, st, A0, A1, V, N, Np, r, thr2);
       std::swap(A0, A1);
     }
     ++sweeps;

@@ -84,6 +84,8 @@ void rotate_bf16(pt_ctx* ctx, const c64* A, const c128* Bm, int ldb, int N1, int
 // ---- FP64 N x N (dense.cu) ----
 void zgemm(char opA, char opB, int m, int n, int k, c128 alpha, const c128* A, int lda, const c128* B, int ldb,
            c128 beta, c128* C, int ldc, cudaStream_t st);
+void zgemm_add(char opA, char opB, int m, int n, int k, c128 alpha, const c128* A, int lda, const c128* B, int ldb,
+               c128 beta, const c128* D, int ldd, c128* C, int ldc, cudaStream_t st);
 // S (Hermitian part used) = Q diag(d) Q^*, ascending d.  Synchronises st once per sweep.
 // Q0 (optional): an orthonormal basis that nearly diagonalises S (warm start); may alias Q.
 // rel_tol (optional): also stop once the off-diagonal Frobenius norm of Q^* S Q is at most

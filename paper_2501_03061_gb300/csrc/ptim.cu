@@ -159,6 +159,44 @@ __global__ void k_fingerprint_sum(const unsigned long long* __restrict__ part, u
   }
 }
 
+// ||S - I||_F^2 in a fixed order: one partial per block, then one block adds the partials
+constexpr int SD_BLOCKS = 64;
+__global__ void __launch_bounds__(256) k_sdev_part(const c128* __restrict__ S, int N, double* __restrict__ part) {
+  double s = 0.0;
+  const int nn = N * N;
+  for (int e = blockIdx.x * 256 + threadIdx.x; e < nn; e += SD_BLOCKS * 256) {
+    c128 v = S[e];
+    if (e / N == e % N) v.re -= 1.0;
+    s += v.re * v.re + v.im * v.im;
+  }
+  for (int o = 16; o; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  __shared__ double sh[8];
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int w = 0; w < 8; ++w) r += sh[w];
+    part[blockIdx.x] = r;
+  }
+}
+__global__ void k_sdev_sum(const double* __restrict__ part, double* __restrict__ out) {
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int b = 0; b < SD_BLOCKS; ++b) r += part[b];
+    out[0] = r;
+  }
+}
+
+// out = M - M^*: the commutator A sigma - sigma A of two Hermitian matrices from M = A sigma alone
+// (sigma A = (A sigma)^*), exactly anti-Hermitian
+__global__ void k_minus_adjoint(const c128* __restrict__ M, int N, c128* __restrict__ out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= N * N) return;
+  const int i = e / N, j = e - i * N;
+  const c128 a = M[e], b = M[size_t(j) * N + i];
+  out[e] = c128{a.re - b.re, a.im + b.im};
+}
+
 __global__ void k_fill(double* __restrict__ d, int n, const double* __restrict__ v) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) d[e] = v[0];
 }
@@ -202,6 +240,43 @@ template <class T>
 __global__ void k_diff(cx<T>* out, const cx<T>* a, const cx<T>* b, size_t n) {
   for (size_t e = size_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n; e += size_t(gridDim.x) * blockDim.x)
     out[e] = a[e] - b[e];
+}
+
+// How S^{-1} A is formed for the overlap S = I + E of the midpoint block.  With e = ||E||_F (an
+// upper bound of ||E||_2), the Neumann series sum_{k=0..K} (-E)^k A in Horner form (K products)
+// is off by at most e^{K+1}/(1-e) relative, and the product (I - E)(I + E^2)(I + E^4)...(I + E^{2^J}),
+// which equals (I - E^{2^{J+1}}) (I + E)^{-1}, by e^{2^{J+1}}/(1-e) (2J+1 products).  A form is
+// usable when that bound is at the FP64 rounding level; the Cholesky route (factor, triangular
+// inverse, two products) costs about as much as kSinvCholCost products on this part, whose FP64
+// pipe runs the serial pivot chain slowly.  mode 1 takes the cheapest usable form, mode 2 the product
+// form whenever usable, mode 0 always the Cholesky route.
+enum SinvKind { kSinvChol = 0, kSinvHorner = 1, kSinvProduct = 2 };
+struct SinvPlan {
+  SinvKind kind;
+  int terms;  // K (Horner) or J (product)
+};
+constexpr double kSinvTol = 1e-17;
+constexpr int kSinvCholCost = 10;
+SinvPlan sinv_plan(double e, int mode) {
+  if (mode == 0 || !(e < 0.25)) return {kSinvChol, 0};
+  const double bound = kSinvTol * (1.0 - e);
+  int K = 0;
+  double p = e;  // e^{K+1}
+  while (p > bound && K < kSinvCholCost) {
+    p *= e;
+    ++K;
+  }
+  int J = 0;
+  double q = e * e;  // e^{2^{J+1}}
+  while (q > bound && 2 * J + 1 < kSinvCholCost) {
+    q *= q;
+    ++J;
+  }
+  const bool horner_ok = p <= bound, product_ok = q <= bound;
+  if (mode == 2) return product_ok ? SinvPlan{kSinvProduct, J} : SinvPlan{kSinvChol, 0};
+  if (horner_ok && (!product_ok || K <= 2 * J + 1)) return {kSinvHorner, K};
+  if (product_ok) return {kSinvProduct, J};
+  return {kSinvChol, 0};
 }
 
 template <class T>
@@ -286,12 +361,14 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
   c128* Li = Mx("ptim_Linv");
   c128* T1 = Mx("ptim_T1");
   c128* Tc = Mx("ptim_Tcomm");  // the sigma commutator, computed on a side stream
+  c128* Tcm = Mx("ptim_Tcomm_half");  // A sigma_h, its half
   c128* SinvA = Mx("ptim_SinvA");
   c128* rsig_buf[2] = {Mx("ptim_rsig0"), Mx("ptim_rsig1")};
   c128* dxp_sig = Mx("ptim_dxpend_sig");
   double* d = static_cast<double*>(S.buf("ptim_d", N * sizeof(double)));
   double* dsc = static_cast<double*>(S.buf("ptim_dscratch", (2 * N + 64) * sizeof(double)));
   int* info = static_cast<int*>(S.buf("ptim_info", sizeof(int)));
+  double* sdp = static_cast<double*>(S.buf("ptim_sdev", (SD_BLOCKS + 1) * sizeof(double)));
   // Anderson history ring: dR and Z = dX + beta dR per slot, for both segments
   std::vector<cx<T>*> Zp(depth), dRp(depth);
   std::vector<c128*> Zs(depth), dRs(depth);
@@ -594,16 +671,63 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
       if (!pure) {
         PT_CUDA_CHECK(cudaEventRecord(comm_ev[0], st));
         PT_CUDA_CHECK(cudaStreamWaitEvent(side, comm_ev[0], 0));
-        zgemm('N', 'N', N, N, N, c128{1, 0}, A, N, sigh, N, c128{0, 0}, Tc, N, side);
-        zgemm('N', 'N', N, N, N, c128{-1, 0}, sigh, N, A, N, c128{1, 0}, Tc, N, side);
+        // A sigma_h - sigma_h A = M - M^* with M = A sigma_h (both Hermitian): one product
+        zgemm('N', 'N', N, N, N, c128{1, 0}, A, N, sigh, N, c128{0, 0}, Tcm, N, side);
+        PT_LAUNCH(k_minus_adjoint, (N * N + 255) / 256, 256, 0, side, Tcm, N, Tc);
         PT_CUDA_CHECK(cudaEventRecord(comm_ev[1], side));
       }
       tm.begin(PH_SUBNN);
-      // S^{-1} A = L^{-*} (L^{-1} A)
-      cholesky(ctx, Sm, N, Lc, info, st);
-      tri_inv_lower(ctx, Lc, N, Li, st);
-      zgemm('N', 'N', N, N, N, c128{1, 0}, Li, N, A, N, c128{0, 0}, T1, N, st);
-      zgemm('C', 'N', N, N, N, c128{1, 0}, Li, N, T1, N, c128{0, 0}, SinvA, N, st);
+      SinvPlan plan{kSinvChol, 0};
+      if (ctx->ptim_sinv_series) {
+        PT_LAUNCH(k_sdev_part, SD_BLOCKS, 256, 0, st, Sm, N, sdp);
+        PT_LAUNCH(k_sdev_sum, 1, 32, 0, st, sdp, sdp + SD_BLOCKS);
+        double e2 = NAN;
+        PT_CUDA_CHECK(cudaMemcpyAsync(&e2, sdp + SD_BLOCKS, sizeof(double), cudaMemcpyDeviceToHost, st));
+        PT_CUDA_CHECK(cudaStreamSynchronize(st));
+        const double e = std::sqrt(e2);
+        if (!(e <= stv.s_dev_max)) stv.s_dev_max = e;
+        plan = sinv_plan(e, ctx->ptim_sinv_series);
+      }
+      stv.sinv_path[plan.kind]++;
+      if (plan.kind == kSinvChol) {
+        // S^{-1} A = L^{-*} (L^{-1} A)
+        cholesky(ctx, Sm, N, Lc, info, st);
+        tri_inv_lower(ctx, Lc, N, Li, st);
+        zgemm('N', 'N', N, N, N, c128{1, 0}, Li, N, A, N, c128{0, 0}, T1, N, st);
+        zgemm('C', 'N', N, N, N, c128{1, 0}, Li, N, T1, N, c128{0, 0}, SinvA, N, st);
+      } else {
+        PT_CUDA_CHECK(cudaMemsetAsync(info, 0, sizeof(int), st));
+        add_diagonal(Sm, N, -1.0, st);  // E = S - I
+        // every product writes a fresh buffer (T1 and SinvA in turn, the last one SinvA)
+        const int writes = plan.kind == kSinvHorner ? plan.terms : plan.terms + 1;
+        int w = 0;
+        auto next_out = [&]() {
+          ++w;
+          return ((writes - w) & 1) ? T1 : SinvA;
+        };
+        const c128* y = A;
+        if (writes == 0) PT_CUDA_CHECK(cudaMemcpyAsync(SinvA, A, mb, cudaMemcpyDeviceToDevice, st));  // E = 0
+        if (plan.kind == kSinvHorner) {
+          for (int k = 0; k < plan.terms; ++k) {  // y <- A - E y
+            c128* o = next_out();
+            zgemm_add('N', 'N', N, N, N, c128{-1, 0}, Sm, N, y, N, c128{1, 0}, A, N, o, N, st);
+            y = o;
+          }
+        } else {
+          c128* o = next_out();  // y <- (I - E) A
+          zgemm_add('N', 'N', N, N, N, c128{-1, 0}, Sm, N, A, N, c128{1, 0}, A, N, o, N, st);
+          y = o;
+          c128* Pw = Sm;  // E^{2^j}
+          c128* Pn = Li;
+          for (int j = 1; j <= plan.terms; ++j) {
+            zgemm('N', 'N', N, N, N, c128{1, 0}, Pw, N, Pw, N, c128{0, 0}, Pn, N, st);
+            std::swap(Pw, Pn);
+            o = next_out();  // y <- (I + E^{2^j}) y
+            zgemm_add('N', 'N', N, N, N, c128{1, 0}, Pw, N, y, N, c128{1, 0}, y, N, o, N, st);
+            y = o;
+          }
+        }
+      }
       tm.end();
       tm.begin(PH_SUB);
       // r_Phi = Phi_n - i dt (H Phi_h - Phi_h S^{-1}A) - Phi

@@ -164,16 +164,18 @@ def test_diag_occupations(ctx, N):
     assert np.abs(d - np.linalg.eigvalsh(sigma)).max() <= 1e-13 * N
 
 
-def test_diag_occupations_fermi_dirac_clustered(ctx):
+@pytest.mark.parametrize("N", [64, 320])
+def test_diag_occupations_fermi_dirac_clustered(ctx, N):
     """Many nearly equal occupations (f ~ 1): the backward error stays at FP64 level."""
-    f = synth.fermi_dirac_occupations(64, 0.002)
+    f = synth.fermi_dirac_occupations(N, 0.002)
     rng = np.random.default_rng(0)
-    Qr, _ = np.linalg.qr(rng.standard_normal((64, 64)) + 1j * rng.standard_normal((64, 64)))
+    Qr, _ = np.linalg.qr(rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N)))
     sigma = Qr @ np.diag(f) @ Qr.conj().T
     Q, d = ctx.diag_occupations(dev(sigma))
     Q, d = Q.cpu().numpy(), d.cpu().numpy()
-    assert np.abs(Q @ np.diag(d) @ Q.conj().T - sigma).max() <= 1e-13
-    assert np.abs(np.sort(f) - d).max() <= 1e-13
+    assert np.abs(Q @ np.diag(d) @ Q.conj().T - sigma).max() <= 1e-13 * max(1.0, N / 64)
+    assert np.abs(Q.conj().T @ Q - np.eye(N)).max() <= 1e-13 * max(1.0, N / 64)
+    assert np.abs(np.sort(f) - d).max() <= 1e-13 * max(1.0, N / 64)
 
 
 # ---------------------------------------------------------------------------- ACE ----

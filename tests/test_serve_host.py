@@ -88,15 +88,15 @@ def test_latency_summary_percentiles():
 
 
 def test_footprint_structure():
-    """pt_ptim_footprint: the Anderson ring adds two orbital blocks per history entry, FP64 needs
-    more than FP32, the footprint grows with N, and the 64^3 FP32 exchange's four scratch slots
-    of B x B pair fields are in it."""
+    """pt_ptim_footprint: the Anderson ring adds two orbital blocks and two N x N matrices per
+    history entry, FP64 needs more than FP32, the footprint grows with N, and the 64^3 FP32
+    exchange's four scratch slots of B x B pair fields are in it."""
     from paper_2501_03061_gb300 import api
     cell = synth.cubic(48, 15.0)
     ng = 48 ** 3
     for N in (32, 200):
         d = api.ptim_footprint(N, cell, "fp32", 20) - api.ptim_footprint(N, cell, "fp32", 10)
-        assert d == 2 * 10 * N * ng * 8
+        assert d == 2 * 10 * (N * ng * 8 + N * N * 16)
         assert api.ptim_footprint(N, cell, "fp64", 20) > api.ptim_footprint(N, cell, "fp32", 20)
     assert api.ptim_footprint(200, cell, "fp32", 20) > api.ptim_footprint(32, cell, "fp32", 20)
     c64 = synth.cubic(64, 20.5)
