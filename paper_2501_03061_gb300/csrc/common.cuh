@@ -100,6 +100,31 @@ class DeviceOnce {
     ::pt::check_cuda(cudaGetLastError(), #kernel);                                \
   } while (0)
 
+// Programmatic dependent launch for chains of short dependent kernels (the N x N FP64 chains):
+// the kernel may be launched while its predecessor on the stream still runs.  A kernel launched
+// this way calls pdl_wait() before it reads anything an earlier kernel wrote (it returns once the
+// predecessor has completed and its writes are visible; a no-op for a plain launch), then
+// pdl_launch_dependents(), which lets the next link of the chain be launched; so at most two
+// links are resident at a time.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+#define PT_LAUNCH_PDL(kernel, grid, block, smem, strm, ...)                        \
+  do {                                                                            \
+    cudaLaunchConfig_t cfg_{};                                                    \
+    cfg_.gridDim = dim3(grid);                                                    \
+    cfg_.blockDim = dim3(block);                                                  \
+    cfg_.dynamicSmemBytes = (smem);                                               \
+    cfg_.stream = (strm);                                                         \
+    cudaLaunchAttribute at_[1];                                                   \
+    at_[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;               \
+    at_[0].val.programmaticStreamSerializationAllowed = 1;                        \
+    cfg_.attrs = at_;                                                             \
+    cfg_.numAttrs = 1;                                                            \
+    ::pt::check_cuda(cudaLaunchKernelEx(&cfg_, kernel, __VA_ARGS__), #kernel);    \
+    ::pt::g_launches.fetch_add(1, std::memory_order_relaxed);                     \
+  } while (0)
+
 // ------------------------------------------------------------------------------------------
 // context and workspace
 // ------------------------------------------------------------------------------------------

@@ -106,6 +106,8 @@ __global__ void __launch_bounds__(JB* JB) k_jacobi_round(const c128* __restrict_
   const int kb = blockIdx.y * JB, lb = blockIdx.x * JB;
   const int half = Np / 2;
   const int t = threadIdx.x;
+  pdl_wait();  // the previous round's A and V
+  pdl_launch_dependents();
   if (t < JB) {
     const int k = kb + t;
     if (k < half) {
@@ -192,6 +194,7 @@ __global__ void k_herm_part_and_basis(const c128* __restrict__ S, c128* __restri
 
 // sums of |offdiag|^2 and |all|^2 (one block)
 __global__ void k_offnorm(const c128* __restrict__ A, int N, double* __restrict__ out) {
+  pdl_wait();  // the last Jacobi round
   double off = 0, all = 0;
   for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
     const double v = A[e].re * A[e].re + A[e].im * A[e].im;
@@ -248,6 +251,8 @@ __global__ void __launch_bounds__(256) k_chol_diag(c128* __restrict__ A, int N, 
   // the trailing triangle of step k (j > k) is one contiguous range and no thread idles on the
   // upper half
   __shared__ unsigned short tri[CB * (CB + 1) / 2];
+  pdl_wait();  // the previous panel's trailing update
+  pdl_launch_dependents();
   if (*info) return;
   const int tid = threadIdx.x;
   for (int e = tid; e < bs * bs; e += blockDim.x) {
@@ -319,6 +324,8 @@ __global__ void __launch_bounds__(256) k_chol_panel(c128* __restrict__ A, int N,
                                                     const c128* __restrict__ Winv, const int* __restrict__ info) {
   __shared__ c128 w[CB][CB + 1];
   __shared__ c128 r[8][CB + 1];
+  pdl_wait();  // the diagonal block and its inverse
+  pdl_launch_dependents();
   if (*info) return;
   const int tid = threadIdx.x;
   const int i0 = kb + bs + blockIdx.x * 8;
@@ -340,6 +347,8 @@ __global__ void __launch_bounds__(256) k_chol_panel(c128* __restrict__ A, int N,
 // trailing update A[i][j] -= sum_p L[i][kb+p] conj(L[j][kb+p]) for kb+bs <= j <= i < N
 __global__ void __launch_bounds__(256) k_chol_update(c128* __restrict__ A, int N, int kb, int bs,
                                                      const int* __restrict__ info) {
+  pdl_wait();  // the panel below the diagonal block
+  pdl_launch_dependents();
   if (*info) return;
   const int t0 = kb + bs;
   const int bi = blockIdx.y, bj = blockIdx.x;
@@ -456,7 +465,7 @@ int heev(pt_ctx* ctx, const c128* S, int N, c128* Q, double* d, cudaStream_t st,
   double prev_off = INFINITY;
   int sweeps = 0;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    PT_LAUNCH(k_offnorm, 1, 1024, 0, st, A0, N, nrm);
+    PT_LAUNCH_PDL(k_offnorm, 1, 1024, 0, st, A0, N, nrm);
     PT_CUDA_CHECK(cudaMemcpyAsync(h, nrm, sizeof(h), cudaMemcpyDeviceToHost, st));
     PT_CUDA_CHECK(cudaStreamSynchronize(st));
     if (!std::isfinite(h[1])) fail(PT_NONFINITE, "non-finite entry in the matrix to diagonalise");
@@ -474,7 +483,7 @@ int heev(pt_ctx* ctx, const c128* S, int N, c128* Q, double* d, cudaStream_t st,
     const double stop2 = rel_tol > 0.0 ? rel_tol * rel_tol * h[1] : floor2;
     const double thr2 = std::max(1e-280, stop2 / (double(N) * double(N)));
     for (int r = 0; r < Np - 1; ++r) {
-      PT_LAUNCH(k_jacobi_round, grid, JB * JB, 0, st, A0, A1, V, N, Np, r, thr2);
+      PT_LAUNCH_PDL(k_jacobi_round, grid, JB * JB, 0, st, A0, A1, V, N, Np, r, thr2);
       std::swap(A0, A1);
     }
     ++sweeps;
@@ -490,12 +499,12 @@ void cholesky(pt_ctx* ctx, c128* A, int N, c128* L, int* info, cudaStream_t st) 
   for (int kb = 0; kb < N; kb += CB) {
     const int bs = std::min(CB, N - kb);
     c128* winv = winv_all + size_t(kb) * CB;
-    PT_LAUNCH(k_chol_diag, 1, 256, 0, st, A, N, kb, bs, winv, info);
+    PT_LAUNCH_PDL(k_chol_diag, 1, 256, 0, st, A, N, kb, bs, winv, info);
     const int rest = N - kb - bs;
     if (rest <= 0) break;
-    PT_LAUNCH(k_chol_panel, (rest + 7) / 8, 256, 0, st, A, N, kb, bs, winv, info);
+    PT_LAUNCH_PDL(k_chol_panel, (rest + 7) / 8, 256, 0, st, A, N, kb, bs, winv, info);
     const int nt = (rest + 15) / 16;
-    PT_LAUNCH(k_chol_update, dim3(nt, nt), 256, 0, st, A, N, kb, bs, info);
+    PT_LAUNCH_PDL(k_chol_update, dim3(nt, nt), 256, 0, st, A, N, kb, bs, info);
   }
   PT_LAUNCH(k_chol_finish, (N * N + 255) / 256, 256, 0, st, A, N, L, info);
 }
