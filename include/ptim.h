@@ -119,6 +119,16 @@ pt_status pt_trim(pt_ctx* ctx);
  *                    operator instead of building one, saving an exchange application; the operators
  *                    the step builds and its stopping test are unchanged (64^3 grid, N = 320: 3 ACE
  *                    builds per step against 4).  total_energy is NaN for such steps.  Default 1.
+ *   "ptim_pw"        1 (default): on cubic grids of side <= 64 with compile-time FFT kernels, the
+ *                    step holds its orbital blocks (iterates, residuals, Anderson history, ACE
+ *                    operator) as their coefficients at the plane waves |G|^2/2 <= ecut of the
+ *                    unitary FFT (the orbital basis of Sec. VI), entering real space only for the
+ *                    local potential, the exchange and the density.  Inner products and so every
+ *                    iterate equal those of the grid form; it applies when the input phi lies in
+ *                    the sphere (the part of sum |phi|^2 outside it at most 1e-24 in PT_FP64, 1e-10
+ *                    otherwise: the rounding of the transform), else the step runs on the grid.
+ *                    The output phi is the real-space field of the final coefficients.  0: always
+ *                    on the grid.
  *   "ptim_sinv_series"  how the inner iteration forms S^{-1} A, S = <Phi_h|Phi_h> = I + E the
  *                    overlap of the midpoint block.  1 (default): with e = ||E||_F < 1/4, the cheaper
  *                    of the Neumann series sum_{k<=K} (-E)^k A (K products, error <= e^{K+1}/(1-e))
@@ -358,6 +368,8 @@ typedef struct {
                                Neumann series in E = S - I, [2] the product form (option
                                "ptim_sinv_series") */
   double s_dev_max;         /* largest ||S - I||_F of the midpoint overlaps met (0 with the option off) */
+  int plane_waves;          /* plane waves of the Ecut sphere the step held its orbitals in (option
+                               "ptim_pw"); 0 when it ran on the grid */
 } pt_ptim_stats;
 
 /* One PT-IM(-ACE) step from (phi, sigma) = (Phi_n, sigma_n) to (Phi_{n+1}, sigma_{n+1}),

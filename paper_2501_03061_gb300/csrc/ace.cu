@@ -34,8 +34,8 @@ void conj_transpose(const c128* A, int N, c128* B, cudaStream_t st) {
 }
 
 void ace_from_w(pt_ctx* ctx, const void* W, const void* phi, int N, const pt_grid& g, pt_precision prec, void* xi,
-                cudaStream_t st) {
-  const size_t ng = ng_of(g);
+                cudaStream_t st, size_t nvec) {
+  const size_t ng = nvec ? nvec : ng_of(g);
   const double dV = dv_of(g);
   const size_t nn = size_t(N) * N * sizeof(c128);
   c128* M = static_cast<c128*>(ctx->get("ace_M", nn));
@@ -66,8 +66,8 @@ void ace_from_w(pt_ctx* ctx, const void* W, const void* phi, int N, const pt_gri
 }
 
 void ace_apply(pt_ctx* ctx, const void* xi, int N, const void* psi, int M, void* out, const pt_grid& g,
-               pt_precision prec, cudaStream_t st) {
-  const size_t ng = ng_of(g);
+               pt_precision prec, cudaStream_t st, size_t nvec) {
+  const size_t ng = nvec ? nvec : ng_of(g);
   const double dV = dv_of(g);
   c128* C = static_cast<c128*>(ctx->get("ace_C", size_t(N) * M * sizeof(c128)));
   if (prec == PT_FP64) {

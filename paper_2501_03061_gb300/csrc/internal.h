@@ -146,6 +146,38 @@ void current(pt_ctx* ctx, const void* phi, const c128* sigma, int N, const pt_gr
 
 void conj_transpose(const c128* A, int N, c128* B, cudaStream_t st);
 
+// ---- plane-wave basis of the Ecut sphere (pw.cu; cubic grids of side <= 64) ----
+// Orbitals as unitary-FFT coefficients at the plane waves |G|^2/2 <= ecut, each vector npad long
+// (npw coefficients, zero padding); inner products over the grid equal those over the coefficients.
+struct PwBasis {
+  pt_grid grid;
+  double ecut;
+  size_t npw, npad;
+  const unsigned long long* masks;  // bit z of masks[y n + x]: (x, y, z) in the sphere
+  const int* col_off;               // index of the first plane wave of column (y, x)
+  const int* xyz;                   // plane wave -> x | y << 8 | z << 16 (-1 on the padding)
+  std::shared_ptr<void> tables;     // owner of col_off and xyz
+};
+bool pw_applies(const pt_grid& g);
+const PwBasis& pw_basis(pt_ctx* ctx, const pt_grid& g, double ecut, cudaStream_t st);
+// c = coefficients of the M real-space fields phi (projection onto the sphere); with check, returns
+// the part of sum |phi|^2 outside the sphere as a fraction of the whole (synchronises st), else 0
+template <class T>
+double pw_from_grid(pt_ctx* ctx, const PwBasis& b, const cx<T>* phi, int M, cx<T>* c, cudaStream_t st,
+                    bool check = false);
+// phi = the M real-space fields of the coefficient vectors c
+template <class T>
+void pw_to_grid(pt_ctx* ctx, const PwBasis& b, const cx<T>* c, int M, cx<T>* phi, cudaStream_t st);
+// out = coefficients of P_sph[1/2 (-i grad + A)^2 psi + vloc psi] + alpha X for coefficient vectors c
+// (X: coefficient vectors or null; Avec: vector potential, host double[3] or null)
+template <class T>
+void pw_apply_h(pt_ctx* ctx, const PwBasis& b, const cx<T>* c, int M, cx<T>* out, const double* vloc, const cx<T>* X,
+                double alpha, const double* Avec, cudaStream_t st);
+// r_j(G) <- r_j(G) / (1 + i dt/2 (|G + A|^2/2 - Re A_jj)) (the kinetic preconditioner, diagonal here)
+template <class T>
+void pw_precondition(pt_ctx* ctx, const PwBasis& b, cx<T>* r, int M, const c128* A, double dt, const double* Avec,
+                     cudaStream_t st);
+
 // ---- PT-IM step (ptim.cu) ----
 pt_status ptim_step(pt_ctx* ctx, void* phi, void* sigma, int N, const double* vloc, const pt_grid& g,
                     const pt_kernel& k, const pt_ptim_params& P, pt_precision prec, pt_ptim_stats* stats,
@@ -153,11 +185,13 @@ pt_status ptim_step(pt_ctx* ctx, void* phi, void* sigma, int N, const double* vl
 
 // ---- ACE (ace.cu) ----
 // xi from (phi, W): M = <phi|W>, -M = L L^*, xi = W L^{-*}.  Synchronises st (pivot check).
+// nvec: length of each vector when they are not grid fields (plane-wave coefficient vectors; 0:
+// the grid's Ng); the inner products keep the grid's dV either way.
 void ace_from_w(pt_ctx* ctx, const void* W, const void* phi, int N, const pt_grid& g, pt_precision prec, void* xi,
-                cudaStream_t st);
+                cudaStream_t st, size_t nvec = 0);
 // out = -xi (xi^* psi)  (+ beta*out0 is not supported: out is overwritten)
 void ace_apply(pt_ctx* ctx, const void* xi, int N, const void* psi, int M, void* out, const pt_grid& g,
-               pt_precision prec, cudaStream_t st);
+               pt_precision prec, cudaStream_t st, size_t nvec = 0);
 
 // ---- FMA throughput of the device (peaks.cu), TFLOP/s; synchronises st ----
 void alu_peaks(pt_ctx* ctx, double* fp32_tflops, double* fp64_tflops, cudaStream_t st);

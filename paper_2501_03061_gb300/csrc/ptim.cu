@@ -289,7 +289,9 @@ template <class T>
 struct Step {
   pt_ctx* ctx;
   int N;
-  size_t ng, n1, n2;
+  size_t ng;      // grid points
+  size_t nv;      // length of an orbital vector: ng, or npad plane-wave coefficients
+  size_t n1, n2;  // N nv orbital entries, N^2 sigma entries
   double dV;
   pt_grid g;
   pt_kernel k;
@@ -323,7 +325,24 @@ template <class T>
 pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* vloc, const pt_grid& g,
                       const pt_kernel& kern, const pt_ptim_params& P, pt_precision prec, pt_ptim_stats* stats,
                       cudaStream_t st) {
-  Step<T> S{ctx, N, ng_of(g), ng_of(g) * N, size_t(N) * N, dv_of(g), g, kern, prec, P, st, 0};
+  // Plane-wave basis (option ptim_pw): on cubic grids with compile-time FFTs the orbital blocks of
+  // the step live as their coefficients in the Ecut sphere, the basis the orbitals are expanded in
+  // (a unitary transform: every inner product and so every iterate is that of the grid form), when
+  // the input lies in the sphere to the rounding of the transform; the caller's real-space block is
+  // read at the start and written at the end
+  cx<T>* const phi_io = phi;
+  const PwBasis* pwb = nullptr;
+  if (ctx->ptim_pw && pw_applies(g)) {
+    const PwBasis& b = pw_basis(ctx, g, P.ecut, st);
+    cx<T>* c = static_cast<cx<T>*>(ctx->get("ptim_phipw", size_t(N) * b.npad * sizeof(cx<T>)));
+    const double outside = pw_from_grid<T>(ctx, b, phi, N, c, st, true);
+    if (outside <= (prec == PT_FP64 ? 1e-24 : 1e-10)) {  // fraction of sum |phi|^2 outside the sphere
+      pwb = &b;
+      phi = c;
+    }
+  }
+  const size_t nv = pwb ? pwb->npad : ng_of(g);
+  Step<T> S{ctx, N, ng_of(g), nv, nv * N, size_t(N) * N, dv_of(g), g, kern, prec, P, st, 0};
   // a step that fails part-way (non-finite input, a failed factorisation) may leave a basis that is
   // not unitary in "ptim_Q": the context's next step must not warm-start its eigensolves from it
   struct WarmStartGuard {
@@ -360,6 +379,9 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
   c128* Lc = Mx("ptim_L");
   c128* Li = Mx("ptim_Linv");
   c128* T1 = Mx("ptim_T1");
+  // real-space blocks of the plane-wave form (the exchange's input and output, the density's)
+  cx<T>* R0 = pwb ? static_cast<cx<T>*>(S.buf("ptim_real0", S.ng * N * sizeof(cx<T>))) : nullptr;
+  cx<T>* R1 = pwb ? static_cast<cx<T>*>(S.buf("ptim_real1", S.ng * N * sizeof(cx<T>))) : nullptr;
   c128* Tc = Mx("ptim_Tcomm");  // the sigma commutator, computed on a side stream
   c128* Tcm = Mx("ptim_Tcomm_half");  // A sigma_h, its half
   c128* SinvA = Mx("ptim_SinvA");
@@ -417,7 +439,7 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
       cudaStreamSynchronize(st);
     }
   } restore{phi, sig, phin, sign, fb, mb, st, true};
-  gram<T>(ctx, phin, phin, N, N, S.ng, S.dV, Sn, st);
+  gram<T>(ctx, phin, phin, N, N, S.nv, S.dV, Sn, st);
   // Pure state (sigma_n = c I, Eq. pure_vx): sigma_h stays c I, its eigenbasis is any basis, the
   // commutator [A, c I] vanishes, so the eigensolve, the rotations into and out of the eigenbasis
   // and the commutator are skipped; Algorithm 1's final step then orthonormalises Phi and keeps
@@ -439,12 +461,13 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
   // of paying an exchange application; the operators this step builds, the anchors they define and
   // the stopping test are unchanged, so the fixed point is the same.
   char warm_key[256];
-  snprintf(warm_key, sizeof(warm_key), "%d:%d:%d:%d:%.17g:%.17g:%.17g:%d:%.17g:%.17g:%d", N, g.nx, g.ny, g.nz,
-           g.L[0], g.L[1], g.L[2], kern.type, kern.mu, kern.g0, int(prec));
+  snprintf(warm_key, sizeof(warm_key), "%d:%d:%d:%d:%.17g:%.17g:%.17g:%d:%.17g:%.17g:%d:%zu", N, g.nx, g.ny, g.nz,
+           g.L[0], g.L[1], g.L[2], kern.type, kern.mu, kern.g0, int(prec), pwb ? pwb->npad : size_t(0));
   auto* fpd = static_cast<unsigned long long*>(
       S.buf("ptim_fingerprint", (2 * FP_BLOCKS + 2) * sizeof(unsigned long long)));
+  // of the caller's real-space blocks (a round trip through the plane-wave coefficients is not exact)
   auto fingerprint = [&](const cx<T>* ph, const c128* sg, unsigned long long out[2]) {
-    PT_LAUNCH(k_fingerprint<T>, FP_BLOCKS, 256, 0, st, ph, S.n1, fpd);
+    PT_LAUNCH(k_fingerprint<T>, FP_BLOCKS, 256, 0, st, ph, S.ng * N, fpd);
     PT_LAUNCH(k_fingerprint_sum, 1, 32, 0, st, fpd, fpd + 2 * FP_BLOCKS);
     PT_LAUNCH(k_fingerprint<double>, FP_BLOCKS, 256, 0, st, sg, S.n2, fpd + FP_BLOCKS);
     PT_LAUNCH(k_fingerprint_sum, 1, 32, 0, st, fpd + FP_BLOCKS, fpd + 2 * FP_BLOCKS + 1);
@@ -454,7 +477,7 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
   bool ace_warm = false;
   if (ctx->ptim_ace_warm && P.use_ace && ctx->ptim_warm_valid && ctx->ptim_warm_key == warm_key) {
     unsigned long long f[2];
-    fingerprint(phin, sign, f);
+    fingerprint(phi_io, sign, f);
     ace_warm = f[0] == ctx->ptim_warm_fp[0] && f[1] == ctx->ptim_warm_fp[1];
   }
   ctx->ptim_warm_valid = false;  // "ptim_xi" is about to change; valid again only after a finished step
@@ -506,13 +529,19 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
       PT_CUDA_CHECK(cudaEventCreate(&e.first));
       PT_CUDA_CHECK(cudaEventCreate(&e.second));
       ev.push_back(e);
+      const cx<T>* src = phih;
+      if (pwb) {  // the exchange works on real-space fields
+        pw_to_grid<T>(ctx, *pwb, phih, N, R0, st);
+        src = R0;
+      }
       PT_CUDA_CHECK(cudaEventRecord(e.first, st));
-      stv.pair_ffts += exchange(ctx, phih, d, N, nullptr, N, out, g, kern, prec, st);
+      stv.pair_ffts += exchange(ctx, src, d, N, nullptr, N, pwb ? R1 : out, g, kern, prec, st);
       PT_CUDA_CHECK(cudaEventRecord(e.second, st));
+      if (pwb) pw_from_grid<T>(ctx, *pwb, R1, N, out, st);
       tm.end();
       stv.exchange_calls++;
       if (energy) {
-        PT_LAUNCH(k_weighted_diag<T>, N, 256, 0, st, phih, out, d, S.ng, S.dV, dsc);
+        PT_LAUNCH(k_weighted_diag<T>, N, 256, 0, st, phih, out, d, S.nv, S.dV, dsc);
         std::vector<double> h(N);
         PT_CUDA_CHECK(cudaMemcpyAsync(h.data(), dsc, N * sizeof(double), cudaMemcpyDeviceToHost, st));
         PT_CUDA_CHECK(cudaStreamSynchronize(st));
@@ -531,20 +560,26 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
     ctx->ptim_q_n = N;
     tm.end();
     tm.begin(PH_ROT);
-    rotate<T>(ctx, phih, Q, N, N, N, S.ng, c128{1, 0}, nullptr, 0, phit, st);
+    rotate<T>(ctx, phih, Q, N, N, N, S.nv, c128{1, 0}, nullptr, 0, phit, st);
     tm.end();
     tm.begin(PH_EXCH);
     std::pair<cudaEvent_t, cudaEvent_t> e;
     PT_CUDA_CHECK(cudaEventCreate(&e.first));
     PT_CUDA_CHECK(cudaEventCreate(&e.second));
     ev.push_back(e);
+    const cx<T>* src = phit;
+    if (pwb) {  // the exchange works on real-space fields
+      pw_to_grid<T>(ctx, *pwb, phit, N, R0, st);
+      src = R0;
+    }
     PT_CUDA_CHECK(cudaEventRecord(e.first, st));
-    stv.pair_ffts += exchange(ctx, phit, d, N, nullptr, N, vphit, g, kern, prec, st);
+    stv.pair_ffts += exchange(ctx, src, d, N, nullptr, N, pwb ? R1 : vphit, g, kern, prec, st);
     PT_CUDA_CHECK(cudaEventRecord(e.second, st));
+    if (pwb) pw_from_grid<T>(ctx, *pwb, R1, N, vphit, st);
     tm.end();
     stv.exchange_calls++;
     if (energy) {
-      PT_LAUNCH(k_weighted_diag<T>, N, 256, 0, st, phit, vphit, d, S.ng, S.dV, dsc);
+      PT_LAUNCH(k_weighted_diag<T>, N, 256, 0, st, phit, vphit, d, S.nv, S.dV, dsc);
       std::vector<double> h(N);
       PT_CUDA_CHECK(cudaMemcpyAsync(h.data(), dsc, N * sizeof(double), cudaMemcpyDeviceToHost, st));
       PT_CUDA_CHECK(cudaStreamSynchronize(st));
@@ -554,7 +589,7 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
     }
     tm.begin(PH_ROT);
     conj_transpose(Q, N, QH, st);
-    rotate<T>(ctx, vphit, QH, N, N, N, S.ng, c128{1, 0}, nullptr, 0, out, st);
+    rotate<T>(ctx, vphit, QH, N, N, N, S.nv, c128{1, 0}, nullptr, 0, out, st);
     tm.end();
   };
 
@@ -608,7 +643,7 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
         stv.outer = ++aces;
         exchange_on_midpoint(W, true);
         tm.begin(PH_ACE_BUILD);
-        ace_from_w(ctx, W, phih, N, g, prec, xi, st);
+        ace_from_w(ctx, W, phih, N, g, prec, xi, st, pwb ? S.nv : 0);
         tm.end();
       }
     } else {
@@ -631,25 +666,33 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
         // H_{n+1/2} = H[P_{n+1/2}] (Eq. p_tilde): rho_h = spin P_h(r, r); X is free until the
         // exchange term below, so it holds chi = Phi_h sigma_h
         tm.begin(PH_HXC);
-        density<T>(ctx, phih, sigh, N, S.ng, P.spin, X, rho, st);
+        if (pwb) {
+          pw_to_grid<T>(ctx, *pwb, phih, N, R0, st);
+          density<T>(ctx, R0, sigh, N, S.ng, P.spin, R1, rho, st);
+        } else {
+          density<T>(ctx, phih, sigh, N, S.ng, P.spin, X, rho, st);
+        }
         hxc_potential(ctx, rho, vloc, g, vtot, first ? hxc_part : nullptr, st);
         tm.end();
         vh = vtot;
       }
       if (P.use_ace) {
         tm.begin(PH_ACE_APPLY);
-        ace_apply(ctx, xi, N, phih, N, X, g, prec, st);
+        ace_apply(ctx, xi, N, phih, N, X, g, prec, st, pwb ? S.nv : 0);
         tm.end();
       } else {
         exchange_on_midpoint(X, inner == 0);
       }
       if (first) ex0 = stv.exch_energy;
       tm.begin(PH_H);
-      apply_h(ctx, phih, N, Hphi, vh, X, P.alpha, P.ecut, g, prec, st, P.A);
+      if (pwb)
+        pw_apply_h<T>(ctx, *pwb, phih, N, Hphi, vh, X, P.alpha, P.A, st);
+      else
+        apply_h(ctx, phih, N, Hphi, vh, X, P.alpha, P.ecut, g, prec, st, P.A);
       tm.end();
       tm.begin(PH_SUB);
       // A = <Phi_h|H Phi_h> and S = <Phi_h|Phi_h> are Hermitian: upper tiles only, mirrored
-      gram2<T>(ctx, phih, Hphi, A, phih, Sm, N, N, S.ng, S.dV, st, true);
+      gram2<T>(ctx, phih, Hphi, A, phih, Sm, N, N, S.nv, S.dV, st, true);
       if (first) {
         e_A.resize(S.n2);
         e_sig.resize(S.n2);
@@ -732,7 +775,7 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
       tm.begin(PH_SUB);
       // r_Phi = Phi_n - i dt (H Phi_h - Phi_h S^{-1}A) - Phi
       Term tr[3] = {{Hphi, c128{0, -P.dt}}, {phin, c128{1, 0}}, {phi, c128{-1, 0}}};
-      rotate<T>(ctx, phih, SinvA, N, N, N, S.ng, c128{0, P.dt}, tr, 3, rphi, st);
+      rotate<T>(ctx, phih, SinvA, N, N, N, S.nv, c128{0, P.dt}, tr, 3, rphi, st);
       tm.end();
       tm.begin(PH_COMM);
       // r_sigma = sigma_n - i dt (A sigma_h - sigma_h A) - sigma  (the commutator is 0 in a pure state)
@@ -787,7 +830,12 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
         }
       }
       // kinetic preconditioning: Anderson then solves x = x + M (T(x) - x), same fixed point
-      if (ctx->ptim_precond) precondition_residual(ctx, rphi, N, A, P.dt, P.ecut, g, prec, st, P.A);
+      if (ctx->ptim_precond) {
+        if (pwb)
+          pw_precondition<T>(ctx, *pwb, rphi, N, A, P.dt, P.A, st);
+        else
+          precondition_residual(ctx, rphi, N, A, P.dt, P.ecut, g, prec, st, P.A);
+      }
       // ---- Anderson (type II, real coefficients) ----
       int m = 0;
       if (inner > 0) {
@@ -838,7 +886,7 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
   }
   // ---- final orthonormalisation and conjugate symmetrisation ----
   tm.begin(PH_LOEW);
-  gram<T>(ctx, phi, phi, N, N, S.ng, S.dV, Sm, st);
+  gram<T>(ctx, phi, phi, N, N, S.nv, S.dV, Sm, st);
   PT_LAUNCH(k_maxabs_diff, 1, 1024, 0, st, Sm, Sn, int(S.n2), dsc);
   set_identity(T1, N, st);
   PT_LAUNCH(k_maxabs_diff, 1, 1024, 0, st, Sm, T1, int(S.n2), dsc + 1);
@@ -881,8 +929,9 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
     PT_CUDA_CHECK(cudaStreamSynchronize(st));
     if (s_info) fail(PT_NOT_PD, "PT-IM: final overlap matrix is not positive definite");
   }
-  rotate<T>(ctx, phi, A, N, N, N, S.ng, c128{1, 0}, nullptr, 0, rphi_buf[0], st);
+  rotate<T>(ctx, phi, A, N, N, N, S.nv, c128{1, 0}, nullptr, 0, rphi_buf[0], st);
   PT_CUDA_CHECK(cudaMemcpyAsync(phi, rphi_buf[0], fb, cudaMemcpyDeviceToDevice, st));
+  if (pwb) pw_to_grid<T>(ctx, *pwb, phi, N, phi_io, st);
   if (pure) {
     PT_CUDA_CHECK(cudaMemcpyAsync(sig, sign, mb, cudaMemcpyDeviceToDevice, st));  // sigma stays c I
   } else {
@@ -906,8 +955,9 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
   stv.converged = converged ? 1 : 0;
   stv.pure_state = pure ? 1 : 0;
   stv.ace_warm = ace_warm ? 1 : 0;
+  stv.plane_waves = pwb ? int(pwb->npw) : 0;
   if (ctx->ptim_ace_warm && P.use_ace && stv.outer > 0) {
-    fingerprint(phi, sig, ctx->ptim_warm_fp);
+    fingerprint(phi_io, sig, ctx->ptim_warm_fp);
     ctx->ptim_warm_key = warm_key;
     ctx->ptim_warm_valid = true;
   }
