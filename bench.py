@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--ace-warm", type=int, default=1, choices=[0, 1],
                     help="1 (the library's default): a chained step's first outer pass reuses the previous "
                          "step's ACE operator (context option ptim_ace_warm); 0: every step builds its own")
+    ap.add_argument("--pw", type=int, default=1, choices=[0, 1],
+                    help="PT-IM step in the plane-wave basis of the Ecut sphere (context option ptim_pw)")
     ap.add_argument("--inner-kappa", type=float, default=None,
                     help="inner tolerance factor of the PT-IM step (context option ptim_inner_kappa)")
     ap.add_argument("--inner-cap", type=float, default=None,
@@ -849,6 +851,7 @@ def run_gb300(args):
     ctx.set_option("tc_gram", args.tc_gram)
     ctx.set_option("ptim_precond", args.precond)
     ctx.set_option("ptim_ace_warm", args.ace_warm)
+    ctx.set_option("ptim_pw", args.pw)
     if args.inner_kappa is not None:
         ctx.set_option("ptim_inner_kappa", args.inner_kappa)
     if args.inner_cap is not None:
@@ -1079,6 +1082,9 @@ def run_gb300(args):
                        "contraction_engine": "tcgen05 3xTF32" if args.tc_gram else "CUDA cores",
                        "inner_iteration": ("Anderson on the kinetically preconditioned map" if args.precond
                                            else "Anderson on T(x) - x"),
+                       "orbital_basis": ("%d plane waves of the Ecut sphere (of %d grid points)"
+                                         % (stats[0]["plane_waves"], ng) if stats[0]["plane_waves"]
+                                         else "the %d-point grid" % ng),
                        "anderson_depth": args.anderson_depth,
                        "ace_operator": ("the first outer pass of a chained step reuses the previous step's ACE "
                                         "operator" if args.ace_warm else "every step builds its own"),
