@@ -156,6 +156,9 @@ struct PwBasis {
   const unsigned long long* masks;  // bit z of masks[y n + x]: (x, y, z) in the sphere
   const int* col_off;               // index of the first plane wave of column (y, x)
   const int* xyz;                   // plane wave -> x | y << 8 | z << 16 (-1 on the padding)
+  const int* yact;                  // the y rows that hold sphere points (ny_act of them)
+  int ny_act;
+  unsigned long long ymask;         // bit y: row y holds sphere points
   std::shared_ptr<void> tables;     // owner of col_off and xyz
 };
 bool pw_applies(const pt_grid& g);

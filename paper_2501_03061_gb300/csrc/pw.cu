@@ -18,6 +18,9 @@
 // N^3 scratch field per orbital of a batch:
 //   to coefficients  plane pass (x, y transforms of each z plane) -> column pass (z transforms of
 //                    each y slab, gather of the sphere, 1/sqrt(Ng))
+// Only the y slabs that hold sphere points (29 of 64 at 64^3, Ecut = 10 Ha) are transformed along z
+// and moved between the passes; the plane pass takes the others as zeros (the input conversion,
+// which measures the weight outside the sphere, transforms every slab).
 //   to real space    column pass (scatter into zeroed columns, inverse z) -> plane pass (inverse
 //                    y, x, 1/sqrt(Ng))
 //   H                column pass (scatter, inverse z) -> plane pass (inverse y, x; times V_loc;
@@ -39,9 +42,11 @@ constexpr int FT = 256;
 struct PwTables {
   int* col_off = nullptr;
   int* xyz = nullptr;
+  int* yact = nullptr;
   ~PwTables() {
     cudaFree(col_off);
     cudaFree(xyz);
+    cudaFree(yact);
   }
 };
 
@@ -53,7 +58,7 @@ constexpr size_t pw_tile_bytes() {
 // x, y transforms of plane z of orbital j0 + j (real space) into scratch field j
 template <int N, class T>
 __global__ void __launch_bounds__(FT) k_pw_fwd_plane(const cx<T>* __restrict__ src, int j0, cx<T>* __restrict__ scratch,
-                                                     const cx<T>* __restrict__ twg) {
+                                                     unsigned long long ykeep, const cx<T>* __restrict__ twg) {
   extern __shared__ unsigned char smem_raw[];
   cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
   cx<T>* tw = buf + N * kPitch<N>;
@@ -74,7 +79,7 @@ __global__ void __launch_bounds__(FT) k_pw_fwd_plane(const cx<T>* __restrict__ s
 #pragma unroll 8
   for (int e = threadIdx.x; e < PL; e += FT) {
     const int yy = e / N, x = e - yy * N;
-    o[e] = buf[yy * kPitch<N> + x];
+    if ((ykeep >> yy) & 1ull) o[e] = buf[yy * kPitch<N> + x];  // rows the column pass reads
   }
 }
 
@@ -89,12 +94,12 @@ __global__ void __launch_bounds__(FT) k_pw_fwd_col(const cx<T>* __restrict__ scr
                                                    double* __restrict__ part, const cx<T>* __restrict__ cin,
                                                    const cx<T>* __restrict__ X, T alpha,
                                                    const double* __restrict__ g2, KinField kf,
-                                                   const cx<T>* __restrict__ twg) {
+                                                   const int* __restrict__ ylist, const cx<T>* __restrict__ twg) {
   extern __shared__ unsigned char smem_raw[];
   cx<T>* ba = reinterpret_cast<cx<T>*>(smem_raw);
   cx<T>* tw = ba + N * kPitch<N>;
   constexpr size_t NG = size_t(N) * N * N;
-  const int yrow = blockIdx.x, j = blockIdx.y;
+  const int yrow = ylist ? ylist[blockIdx.x] : int(blockIdx.x), j = blockIdx.y;
   __shared__ unsigned long long mrow[N];
   __shared__ int coff[N];
   __shared__ float kxf[N], kzf[N];
@@ -148,7 +153,7 @@ __global__ void __launch_bounds__(FT) k_pw_fwd_col(const cx<T>* __restrict__ scr
       s_out += float(v.re) * float(v.re) + float(v.im) * float(v.im);
     }
   }
-  if (yrow == 0)
+  if (blockIdx.x == 0)
     for (size_t p = npw + threadIdx.x; p < npad; p += FT) o[p] = czero<T>();
   if constexpr (!COMB) {
     for (int off = 16; off; off >>= 1) {
@@ -161,7 +166,7 @@ __global__ void __launch_bounds__(FT) k_pw_fwd_col(const cx<T>* __restrict__ scr
       red[1][threadIdx.x >> 5] = s_out;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && part) {
       double a = 0.0, b = 0.0;
       for (int w = 0; w < FT / 32; ++w) {
         a += red[0][w];
@@ -179,12 +184,12 @@ template <int N, class T>
 __global__ void __launch_bounds__(FT) k_pw_inv_col(const cx<T>* __restrict__ c, int j0, size_t npad,
                                                    cx<T>* __restrict__ scratch, const int* __restrict__ col_off,
                                                    const unsigned long long* __restrict__ masks,
-                                                   const cx<T>* __restrict__ twg) {
+                                                   const int* __restrict__ ylist, const cx<T>* __restrict__ twg) {
   extern __shared__ unsigned char smem_raw[];
   cx<T>* ba = reinterpret_cast<cx<T>*>(smem_raw);
   cx<T>* tw = ba + N * kPitch<N>;
   constexpr size_t NG = size_t(N) * N * N;
-  const int yrow = blockIdx.x, j = blockIdx.y;
+  const int yrow = ylist[blockIdx.x], j = blockIdx.y;
   __shared__ unsigned long long mrow[N];
   __shared__ int coff[N];
   for (int t = threadIdx.x; t < N; t += FT) {
@@ -216,7 +221,7 @@ __global__ void __launch_bounds__(FT) k_pw_inv_col(const cx<T>* __restrict__ c, 
 //   VMUL = true:  result * V_loc, forward x, y transforms, back into the scratch plane.
 template <int N, class T, bool VMUL>
 __global__ void __launch_bounds__(FT) k_pw_inv_plane(cx<T>* __restrict__ scratch, int j0, cx<T>* __restrict__ out,
-                                                     const T* __restrict__ vloc, T scale,
+                                                     const T* __restrict__ vloc, T scale, unsigned long long ykeep,
                                                      const cx<T>* __restrict__ twg) {
   extern __shared__ unsigned char smem_raw[];
   cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
@@ -229,7 +234,8 @@ __global__ void __launch_bounds__(FT) k_pw_inv_plane(cx<T>* __restrict__ scratch
 #pragma unroll 8
   for (int e = threadIdx.x; e < PL; e += FT) {
     const int yy = e / N, x = e - yy * N;
-    buf[yy * kPitch<N> + x] = f[e];
+    // rows ky outside the sphere's extent are zero: not written by the column pass, not read here
+    buf[yy * kPitch<N> + x] = ((ykeep >> yy) & 1ull) ? f[e] : czero<T>();
   }
   __syncthreads();
   cfft_slow<N, true, FT>(buf, tw);
@@ -247,7 +253,7 @@ __global__ void __launch_bounds__(FT) k_pw_inv_plane(cx<T>* __restrict__ scratch
 #pragma unroll 8
     for (int e = threadIdx.x; e < PL; e += FT) {
       const int yy = e / N, x = e - yy * N;
-      f[e] = buf[yy * kPitch<N> + x];
+      if ((ykeep >> yy) & 1ull) f[e] = buf[yy * kPitch<N> + x];
     }
   } else {
     cx<T>* o = out + size_t(j0 + j) * NG + size_t(z) * PL;
@@ -363,19 +369,29 @@ void pw_run_n(pt_ctx* ctx, const PwBasis& b, PwOp op, const cx<T>* in, int M, cx
     const int nb = std::min(pb, M - j0);
     switch (op) {
       case PwOp::ToPw:
-        PT_LAUNCH((k_pw_fwd_plane<N, T>), dim3(N, nb), FT, bytes, st, in, j0, scratch, tw);
-        PT_LAUNCH((k_pw_fwd_col<N, T, false>), dim3(N, nb), FT, bytes, st, scratch, j0, out, b.npw, b.npad, b.col_off,
-                  b.masks, unit, part, nullptr, nullptr, T(0), g2d, kf, tw);
+        if (part) {  // the sphere test sums |FFT|^2 over every slab
+          PT_LAUNCH((k_pw_fwd_plane<N, T>), dim3(N, nb), FT, bytes, st, in, j0, scratch, ~0ull, tw);
+          PT_LAUNCH((k_pw_fwd_col<N, T, false>), dim3(N, nb), FT, bytes, st, scratch, j0, out, b.npw, b.npad,
+                    b.col_off, b.masks, unit, part, nullptr, nullptr, T(0), g2d, kf, nullptr, tw);
+        } else {  // the slabs that hold sphere points only
+          PT_LAUNCH((k_pw_fwd_plane<N, T>), dim3(N, nb), FT, bytes, st, in, j0, scratch, b.ymask, tw);
+          PT_LAUNCH((k_pw_fwd_col<N, T, false>), dim3(b.ny_act, nb), FT, bytes, st, scratch, j0, out, b.npw, b.npad,
+                    b.col_off, b.masks, unit, nullptr, nullptr, nullptr, T(0), g2d, kf, b.yact, tw);
+        }
         break;
       case PwOp::ToGrid:
-        PT_LAUNCH((k_pw_inv_col<N, T>), dim3(N, nb), FT, bytes, st, in, j0, b.npad, scratch, b.col_off, b.masks, tw);
-        PT_LAUNCH((k_pw_inv_plane<N, T, false>), dim3(N, nb), FT, bytes, st, scratch, j0, out, nullptr, unit, tw);
+        PT_LAUNCH((k_pw_inv_col<N, T>), dim3(b.ny_act, nb), FT, bytes, st, in, j0, b.npad, scratch, b.col_off, b.masks,
+                  b.yact, tw);
+        PT_LAUNCH((k_pw_inv_plane<N, T, false>), dim3(N, nb), FT, bytes, st, scratch, j0, out, nullptr, unit, b.ymask,
+                  tw);
         break;
       case PwOp::H:
-        PT_LAUNCH((k_pw_inv_col<N, T>), dim3(N, nb), FT, bytes, st, in, j0, b.npad, scratch, b.col_off, b.masks, tw);
-        PT_LAUNCH((k_pw_inv_plane<N, T, true>), dim3(N, nb), FT, bytes, st, scratch, j0, nullptr, vloc, T(1), tw);
-        PT_LAUNCH((k_pw_fwd_col<N, T, true>), dim3(N, nb), FT, bytes, st, scratch, j0, out, b.npw, b.npad, b.col_off,
-                  b.masks, T(1.0 / ng), nullptr, in, X, alpha, g2d, kf, tw);
+        PT_LAUNCH((k_pw_inv_col<N, T>), dim3(b.ny_act, nb), FT, bytes, st, in, j0, b.npad, scratch, b.col_off, b.masks,
+                  b.yact, tw);
+        PT_LAUNCH((k_pw_inv_plane<N, T, true>), dim3(N, nb), FT, bytes, st, scratch, j0, nullptr, vloc, T(1), b.ymask,
+                  tw);
+        PT_LAUNCH((k_pw_fwd_col<N, T, true>), dim3(b.ny_act, nb), FT, bytes, st, scratch, j0, out, b.npw, b.npad,
+                  b.col_off, b.masks, T(1.0 / ng), nullptr, in, X, alpha, g2d, kf, b.yact, tw);
         break;
     }
   }
@@ -421,6 +437,15 @@ const PwBasis& pw_basis(pt_ctx* ctx, const pt_grid& g, double ecut, cudaStream_t
       for (int z = 0; z < n; ++z)
         if ((m >> z) & 1ull) xyz.push_back(x | (y << 8) | (z << 16));
     }
+  std::vector<int> yact;
+  unsigned long long ymask = 0;
+  for (int y = 0; y < n; ++y)
+    for (int x = 0; x < n; ++x)
+      if (hm[size_t(y) * n + x]) {
+        yact.push_back(y);
+        ymask |= 1ull << y;
+        break;
+      }
   auto b = std::make_shared<PwBasis>();
   auto tables = std::make_shared<PwTables>();
   b->grid = g;
@@ -430,12 +455,18 @@ const PwBasis& pw_basis(pt_ctx* ctx, const pt_grid& g, double ecut, cudaStream_t
   xyz.resize(b->npad, -1);
   PT_CUDA_CHECK(cudaMalloc(&tables->col_off, off.size() * sizeof(int)));
   PT_CUDA_CHECK(cudaMalloc(&tables->xyz, xyz.size() * sizeof(int)));
+  PT_CUDA_CHECK(cudaMalloc(&tables->yact, std::max<size_t>(1, yact.size()) * sizeof(int)));
   PT_CUDA_CHECK(cudaMemcpyAsync(tables->col_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice, st));
   PT_CUDA_CHECK(cudaMemcpyAsync(tables->xyz, xyz.data(), xyz.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  if (!yact.empty())
+    PT_CUDA_CHECK(cudaMemcpyAsync(tables->yact, yact.data(), yact.size() * sizeof(int), cudaMemcpyHostToDevice, st));
   PT_CUDA_CHECK(cudaStreamSynchronize(st));  // the host vectors go out of scope
   b->masks = masks;
   b->col_off = tables->col_off;
   b->xyz = tables->xyz;
+  b->yact = tables->yact;
+  b->ny_act = int(yact.size());
+  b->ymask = ymask;
   b->tables = tables;
   ctx->caches[key] = b;
   return *b;
