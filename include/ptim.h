@@ -137,6 +137,12 @@ pt_status pt_trim(pt_ctx* ctx);
  *                    is cheaper; 2: the product form wherever it applies; 0: always S = L L^* and
  *                    S^{-1} A = L^{-*} (L^{-1} A).  The forms agree to FP64 rounding; the series
  *                    costs one synchronisation per inner iteration to read e.
+ *   "ptim_sinv_mixed"  1 (default): where no series form applies, S^{-1} A comes from an FP32
+ *                    Cholesky factor of S refined in FP64: X = S32^{-1} A, then twice X <- X +
+ *                    S32^{-1} (A - S X) with the residual A - S X in FP64 (each pass multiplies the
+ *                    error by ~kappa(S) eps_32); a last correction above 1e-10 of X, or an FP32
+ *                    factorisation that fails, sends the step to the FP64 Cholesky route.  0: the
+ *                    FP64 Cholesky route (S = L L^*, S^{-1} A = L^{-*} (L^{-1} A)).
  *   "scratch_bytes"  bytes of pair/orbital fields one FFT batch may hold (default 512 MiB: the
  *                    cost per pair falls with the pair tile even past L2 residency, 4-10% from
  *                    48 MiB to 512 MiB; smaller values give more, smaller batches).
@@ -364,9 +370,12 @@ typedef struct {
   int passes;               /* inner loops run: one per ACE operator built, plus the warm-started
                                first pass and any pass that kept the operator to finish at tol */
   int pass_inner[16];       /* inner iterations of each of the first 16 passes */
-  int sinv_path[3];         /* inner iterations whose S^{-1} A took [0] the Cholesky route, [1] the
+  int sinv_path[4];         /* inner iterations whose S^{-1} A took [0] the FP64 Cholesky route, [1] the
                                Neumann series in E = S - I, [2] the product form (option
-                               "ptim_sinv_series") */
+                               "ptim_sinv_series"), [3] the FP32 factor refined in FP64 (option
+                               "ptim_sinv_mixed") */
+  int sinv_mixed_fallback;  /* 1 when the refinement converged too slowly and the step went on with
+                               the FP64 Cholesky route */
   double s_dev_max;         /* largest ||S - I||_F of the midpoint overlaps met (0 with the option off) */
   int plane_waves;          /* plane waves of the Ecut sphere the step held its orbitals in (option
                                "ptim_pw"); 0 when it ran on the grid */

@@ -40,7 +40,7 @@ class pt_ptim_stats(C.Structure):
                 ("exchange_calls", C.c_int), ("exchange_ms", C.c_double), ("phase_ms", C.c_double * 12),
                 ("eig_sweeps", C.c_int), ("total_energy", C.c_double), ("pure_state", C.c_int),
                 ("ace_warm", C.c_int), ("passes", C.c_int), ("pass_inner", C.c_int * 16),
-                ("sinv_path", C.c_int * 3), ("s_dev_max", C.c_double),
+                ("sinv_path", C.c_int * 4), ("sinv_mixed_fallback", C.c_int), ("s_dev_max", C.c_double),
                 ("plane_waves", C.c_int)]
 
 PHASES = ("exchange", "ace_build", "ace_apply", "apply_H", "subspace_gemm", "subspace_nxn", "sigma_eig",

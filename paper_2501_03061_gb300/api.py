@@ -424,7 +424,8 @@ class Context:
                 "exchange_ms": float(s.exchange_ms), "eig_sweeps": int(s.eig_sweeps),
                 "total_energy": float(s.total_energy), "pure_state": bool(s.pure_state), "ace_warm": bool(s.ace_warm),
                 "pass_inner": [int(s.pass_inner[i]) for i in range(min(int(s.passes), 16))],
-                "sinv_path": [int(s.sinv_path[i]) for i in range(3)], "s_dev_max": float(s.s_dev_max),
+                "sinv_path": [int(s.sinv_path[i]) for i in range(4)], "s_dev_max": float(s.s_dev_max),
+                "sinv_mixed_fallback": bool(s.sinv_mixed_fallback),
                 "plane_waves": int(s.plane_waves),
                 "phase_ms": {n: float(s.phase_ms[i]) for i, n in enumerate(L.PHASES)}}
 

@@ -192,6 +192,10 @@ pt_status pt_set_option(pt_ctx* ctx, const char* key, double value) {
       ctx->ptim_precond = value != 0.0 ? 1 : 0;
       return PT_OK;
     }
+    if (std::string(key) == "ptim_sinv_mixed") {
+      ctx->ptim_sinv_mixed = value != 0.0 ? 1 : 0;
+      return PT_OK;
+    }
     if (std::string(key) == "ptim_pw") {
       ctx->ptim_pw = value != 0.0 ? 1 : 0;
       return PT_OK;

@@ -160,6 +160,7 @@ struct pt_ctx {
   int ptim_precond = 1;        // option: Anderson on the kinetically preconditioned inner map when 1
   int ptim_ace_warm = 1;       // option: a chained step's first outer pass uses the previous step's ACE
   int ptim_pw = 1;             // option: the step's orbital blocks as plane-wave coefficients when 1
+  int ptim_sinv_mixed = 1;      // option: S^{-1} A from an FP32 factor refined in FP64 when 1
   int ptim_sinv_series = 1;    // option: S^{-1} A of the PT-IM inner iteration by a series in S - I when
                                // S is near the identity (1 cheapest form, 2 product form, 0 Cholesky only)
   bool ptim_warm_valid = false;  // "ptim_xi" holds the last ACE of the step whose output is fingerprinted

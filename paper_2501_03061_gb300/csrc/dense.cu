@@ -20,10 +20,11 @@ namespace pt {
 
 namespace {
 
-__device__ __forceinline__ c128 opval(const c128* A, int lda, char op, int i, int k) {
+template <class T>
+__device__ __forceinline__ cx<T> opval(const cx<T>* A, int lda, char op, int i, int k) {
   // element (i, k) of op(A)
   if (op == 'N') return A[size_t(i) * lda + k];
-  c128 v = A[size_t(k) * lda + i];
+  cx<T> v = A[size_t(k) * lda + i];
   if (op == 'C') v.im = -v.im;
   return v;
 }
@@ -31,26 +32,27 @@ __device__ __forceinline__ c128 opval(const c128* A, int lda, char op, int i, in
 constexpr int ZT = 16;
 
 // C = alpha op(A) op(B) + beta D  (D may be C itself, or another matrix with leading dimension ldd)
-__global__ void __launch_bounds__(ZT* ZT) k_zgemm(char opA, char opB, int m, int n, int k, c128 alpha,
-                                                  const c128* __restrict__ A, int lda, const c128* __restrict__ B,
-                                                  int ldb, c128 beta, const c128* D, int ldd, c128* C, int ldc) {
-  __shared__ c128 As[ZT][ZT + 1];
-  __shared__ c128 Bs[ZT][ZT + 1];
+template <class T>
+__global__ void __launch_bounds__(ZT* ZT) k_gemm(char opA, char opB, int m, int n, int k, cx<T> alpha,
+                                                 const cx<T>* __restrict__ A, int lda, const cx<T>* __restrict__ B,
+                                                 int ldb, cx<T> beta, const cx<T>* D, int ldd, cx<T>* C, int ldc) {
+  __shared__ cx<T> As[ZT][ZT + 1];
+  __shared__ cx<T> Bs[ZT][ZT + 1];
   const int tx = threadIdx.x % ZT, ty = threadIdx.x / ZT;
   const int i = blockIdx.y * ZT + ty, j = blockIdx.x * ZT + tx;
-  c128 acc = czero<double>();
+  cx<T> acc = czero<T>();
   for (int k0 = 0; k0 < k; k0 += ZT) {
     const int ka = k0 + tx, kb = k0 + ty;
-    As[ty][tx] = (i < m && ka < k) ? opval(A, lda, opA, i, ka) : czero<double>();
-    Bs[ty][tx] = (kb < k && j < n) ? opval(B, ldb, opB, kb, j) : czero<double>();
+    As[ty][tx] = (i < m && ka < k) ? opval(A, lda, opA, i, ka) : czero<T>();
+    Bs[ty][tx] = (kb < k && j < n) ? opval(B, ldb, opB, kb, j) : czero<T>();
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < ZT; ++kk) cfma(acc, As[ty][kk], Bs[kk][tx]);
     __syncthreads();
   }
   if (i < m && j < n) {
-    c128 v = cmul(alpha, acc);
-    if (beta.re != 0.0 || beta.im != 0.0) v = v + cmul(beta, D[size_t(i) * ldd + j]);
+    cx<T> v = cmul(alpha, acc);
+    if (beta.re != T(0) || beta.im != T(0)) v = v + cmul(beta, D[size_t(i) * ldd + j]);
     C[size_t(i) * ldc + j] = v;
   }
 }
@@ -243,10 +245,14 @@ __global__ void k_sort_eig(const c128* __restrict__ A, const c128* __restrict__ 
 // inverse of the diagonal block, and the trailing lower triangle gets a rank-CB update.
 constexpr int CB = 32;
 
-__global__ void __launch_bounds__(256) k_chol_diag(c128* __restrict__ A, int N, int kb, int bs,
-                                                   c128* __restrict__ Winv, int* __restrict__ info) {
-  __shared__ c128 a[CB][CB + 1];
-  __shared__ c128 x[CB][CB + 1];
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+
+template <class T>
+__global__ void __launch_bounds__(256) k_chol_diag(cx<T>* __restrict__ A, int N, int kb, int bs,
+                                                   cx<T>* __restrict__ Winv, int* __restrict__ info) {
+  __shared__ cx<T> a[CB][CB + 1];
+  __shared__ cx<T> x[CB][CB + 1];
   // lower triangle (i >= j) listed column by column: entry (j, i) at j*bs - j(j-1)/2 + (i - j), so
   // the trailing triangle of step k (j > k) is one contiguous range and no thread idles on the
   // upper half
@@ -264,10 +270,10 @@ __global__ void __launch_bounds__(256) k_chol_diag(c128* __restrict__ A, int N, 
   const int tri_end = bs * (bs + 1) / 2;
   // FP64 square roots and divisions are long instruction sequences on the FP64 pipe: one thread
   // takes them and broadcasts the results
-  __shared__ double rdiag[CB];
-  __shared__ double s_rk;
+  __shared__ T rdiag[CB];
+  __shared__ T s_rk;
   for (int k = 0; k < bs; ++k) {
-    const double piv = a[k][k].re;
+    const T piv = a[k][k].re;
     if (!(piv > 0.0) || !isfinite(piv)) {
       if (tid == 0) *info = kb + k + 1;
       return;  // uniform: every thread read the same pivot
@@ -276,13 +282,13 @@ __global__ void __launch_bounds__(256) k_chol_diag(c128* __restrict__ A, int N, 
     if (tid == 0) {
       // one reciprocal square root instead of a square root and a division (each a long FP64
       // sequence on the pivot's critical path)
-      const double rk0 = rsqrt(piv);
-      a[k][k] = c128{piv * rk0, 0.0};
+      const T rk0 = rsq(piv);
+      a[k][k] = cx<T>{piv * rk0, T(0)};
       s_rk = rk0;
       rdiag[k] = rk0;
     }
     __syncthreads();
-    const double rk = s_rk;
+    const T rk = s_rk;
     for (int i = k + 1 + tid; i < bs; i += blockDim.x) a[i][k] = a[i][k] * rk;
     __syncthreads();
     for (int e = (k + 1) * bs - (k + 1) * k / 2 + tid; e < tri_end; e += blockDim.x) {
@@ -294,20 +300,20 @@ __global__ void __launch_bounds__(256) k_chol_diag(c128* __restrict__ A, int N, 
   // inverse X of the lower-triangular factor, one row at a time with all threads:
   //   X[i][i] = 1 / L[i][i],  X[i][j] = -(sum_{p=j}^{i-1} L[i][p] X[p][j]) / L[i][i]  (j < i);
   // thread (part, j) sums every 8th p, the 8 parts meet in shared memory
-  __shared__ c128 red[8][CB];
+  __shared__ cx<T> red[8][CB];
   {
     const int j = tid & (CB - 1), part = tid >> 5;
     for (int i = 0; i < bs; ++i) {
-      c128 acc = czero<double>();
+      cx<T> acc = czero<T>();
       if (j < i)
         for (int p = j + part; p < i; p += 8) acc = acc + cmul(a[i][p], x[p][j]);
       red[part][j] = acc;
       __syncthreads();
       if (part == 0) {
-        c128 t = czero<double>();
+        cx<T> t = czero<T>();
         for (int q = 0; q < 8; ++q) t = t + red[q][j];
-        const double inv = rdiag[i];
-        x[i][j] = j < i ? t * (-inv) : (j == i ? c128{inv, 0.0} : czero<double>());
+        const T inv = rdiag[i];
+        x[i][j] = j < i ? t * (-inv) : (j == i ? cx<T>{inv, T(0)} : czero<T>());
       }
       __syncthreads();
     }
@@ -320,10 +326,11 @@ __global__ void __launch_bounds__(256) k_chol_diag(c128* __restrict__ A, int N, 
 }
 
 // L_ik = A_ik L_kk^{-*} for the rows below the diagonal block (8 rows per CTA)
-__global__ void __launch_bounds__(256) k_chol_panel(c128* __restrict__ A, int N, int kb, int bs,
-                                                    const c128* __restrict__ Winv, const int* __restrict__ info) {
-  __shared__ c128 w[CB][CB + 1];
-  __shared__ c128 r[8][CB + 1];
+template <class T>
+__global__ void __launch_bounds__(256) k_chol_panel(cx<T>* __restrict__ A, int N, int kb, int bs,
+                                                    const cx<T>* __restrict__ Winv, const int* __restrict__ info) {
+  __shared__ cx<T> w[CB][CB + 1];
+  __shared__ cx<T> r[8][CB + 1];
   pdl_wait();  // the diagonal block and its inverse
   pdl_launch_dependents();
   if (*info) return;
@@ -332,12 +339,12 @@ __global__ void __launch_bounds__(256) k_chol_panel(c128* __restrict__ A, int N,
   for (int e = tid; e < bs * bs; e += blockDim.x) w[e / bs][e % bs] = Winv[(e / bs) * CB + (e % bs)];
   for (int e = tid; e < 8 * bs; e += blockDim.x) {
     const int ii = e / bs, p = e % bs;
-    r[ii][p] = (i0 + ii < N) ? A[size_t(i0 + ii) * N + kb + p] : czero<double>();
+    r[ii][p] = (i0 + ii < N) ? A[size_t(i0 + ii) * N + kb + p] : czero<T>();
   }
   __syncthreads();
   const int ii = tid / CB, j = tid % CB;
   if (i0 + ii < N && j < bs) {
-    c128 acc = czero<double>();
+    cx<T> acc = czero<T>();
     // (L_kk^{-*})[p][j] = conj(Winv[j][p]), nonzero for p <= j
     for (int p = 0; p <= j; ++p) acc = acc + cmul(r[ii][p], conjc(w[j][p]));
     A[size_t(i0 + ii) * N + kb + j] = acc;
@@ -345,7 +352,8 @@ __global__ void __launch_bounds__(256) k_chol_panel(c128* __restrict__ A, int N,
 }
 
 // trailing update A[i][j] -= sum_p L[i][kb+p] conj(L[j][kb+p]) for kb+bs <= j <= i < N
-__global__ void __launch_bounds__(256) k_chol_update(c128* __restrict__ A, int N, int kb, int bs,
+template <class T>
+__global__ void __launch_bounds__(256) k_chol_update(cx<T>* __restrict__ A, int N, int kb, int bs,
                                                      const int* __restrict__ info) {
   pdl_wait();  // the panel below the diagonal block
   pdl_launch_dependents();
@@ -353,28 +361,29 @@ __global__ void __launch_bounds__(256) k_chol_update(c128* __restrict__ A, int N
   const int t0 = kb + bs;
   const int bi = blockIdx.y, bj = blockIdx.x;
   if (bj > bi) return;
-  __shared__ c128 li[16][CB + 1], lj[16][CB + 1];
+  __shared__ cx<T> li[16][CB + 1], lj[16][CB + 1];
   const int tid = threadIdx.x;
   const int ib = t0 + bi * 16, jb = t0 + bj * 16;
   for (int e = tid; e < 16 * bs; e += blockDim.x) {
     const int q = e / bs, p = e % bs;
-    li[q][p] = (ib + q < N) ? A[size_t(ib + q) * N + kb + p] : czero<double>();
-    lj[q][p] = (jb + q < N) ? A[size_t(jb + q) * N + kb + p] : czero<double>();
+    li[q][p] = (ib + q < N) ? A[size_t(ib + q) * N + kb + p] : czero<T>();
+    lj[q][p] = (jb + q < N) ? A[size_t(jb + q) * N + kb + p] : czero<T>();
   }
   __syncthreads();
   const int i = ib + tid / 16, j = jb + tid % 16;
   if (i < N && j < N && j <= i) {
-    c128 acc = czero<double>();
+    cx<T> acc = czero<T>();
     for (int p = 0; p < bs; ++p) acc = acc + cmulc(lj[tid % 16][p], li[tid / 16][p]);
     A[size_t(i) * N + j] = A[size_t(i) * N + j] - acc;
   }
 }
 
-__global__ void k_chol_finish(const c128* __restrict__ A, int N, c128* __restrict__ L, const int* __restrict__ info) {
+template <class T>
+__global__ void k_chol_finish(const cx<T>* __restrict__ A, int N, cx<T>* __restrict__ L, const int* __restrict__ info) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= N * N || *info) return;
   const int i = e / N, j = e % N;
-  L[e] = (j > i) ? czero<double>() : A[e];
+  L[e] = (j > i) ? czero<T>() : A[e];
 }
 
 // out = U diag(f(lam)) (scale columns), f = lam^power
@@ -430,16 +439,25 @@ __global__ void k_small_solve(const double* __restrict__ G, const double* __rest
 }  // namespace
 
 // ------------------------------------------------------------------------------------------
+template <class T>
+void gemm(char opA, char opB, int m, int n, int k, cx<T> alpha, const cx<T>* A, int lda, const cx<T>* B, int ldb,
+          cx<T> beta, const cx<T>* D, int ldd, cx<T>* C, int ldc, cudaStream_t st) {
+  dim3 grid((n + ZT - 1) / ZT, (m + ZT - 1) / ZT);
+  PT_LAUNCH(k_gemm<T>, grid, ZT * ZT, 0, st, opA, opB, m, n, k, alpha, A, lda, B, ldb, beta, D, ldd, C, ldc);
+}
+template void gemm<float>(char, char, int, int, int, c64, const c64*, int, const c64*, int, c64, const c64*, int, c64*,
+                          int, cudaStream_t);
+template void gemm<double>(char, char, int, int, int, c128, const c128*, int, const c128*, int, c128, const c128*, int,
+                           c128*, int, cudaStream_t);
+
 void zgemm(char opA, char opB, int m, int n, int k, c128 alpha, const c128* A, int lda, const c128* B, int ldb,
            c128 beta, c128* C, int ldc, cudaStream_t st) {
-  dim3 grid((n + ZT - 1) / ZT, (m + ZT - 1) / ZT);
-  PT_LAUNCH(k_zgemm, grid, ZT * ZT, 0, st, opA, opB, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, C, ldc);
+  gemm<double>(opA, opB, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, C, ldc, st);
 }
 
 void zgemm_add(char opA, char opB, int m, int n, int k, c128 alpha, const c128* A, int lda, const c128* B, int ldb,
                c128 beta, const c128* D, int ldd, c128* C, int ldc, cudaStream_t st) {
-  dim3 grid((n + ZT - 1) / ZT, (m + ZT - 1) / ZT);
-  PT_LAUNCH(k_zgemm, grid, ZT * ZT, 0, st, opA, opB, m, n, k, alpha, A, lda, B, ldb, beta, D, ldd, C, ldc);
+  gemm<double>(opA, opB, m, n, k, alpha, A, lda, B, ldb, beta, D, ldd, C, ldc, st);
 }
 
 int heev(pt_ctx* ctx, const c128* S, int N, c128* Q, double* d, cudaStream_t st, int max_sweeps, const c128* Q0,
@@ -492,50 +510,60 @@ int heev(pt_ctx* ctx, const c128* S, int N, c128* Q, double* d, cudaStream_t st,
   return sweeps;
 }
 
-void cholesky(pt_ctx* ctx, c128* A, int N, c128* L, int* info, cudaStream_t st) {
+template <class T>
+void cholesky(pt_ctx* ctx, cx<T>* A, int N, cx<T>* L, int* info, cudaStream_t st) {
   // the inverses of all diagonal blocks are kept (rows kb..kb+bs of an N x CB array) for tri_inv_lower
-  c128* winv_all = static_cast<c128*>(ctx->get("chol_winv_all", size_t(N) * CB * sizeof(c128)));
+  cx<T>* winv_all = static_cast<cx<T>*>(
+      ctx->get(sizeof(T) == 8 ? "chol_winv_all" : "chol_winv_all32", size_t(N) * CB * sizeof(cx<T>)));
   PT_CUDA_CHECK(cudaMemsetAsync(info, 0, sizeof(int), st));
   for (int kb = 0; kb < N; kb += CB) {
     const int bs = std::min(CB, N - kb);
-    c128* winv = winv_all + size_t(kb) * CB;
-    PT_LAUNCH_PDL(k_chol_diag, 1, 256, 0, st, A, N, kb, bs, winv, info);
+    cx<T>* winv = winv_all + size_t(kb) * CB;
+    PT_LAUNCH_PDL(k_chol_diag<T>, 1, 256, 0, st, A, N, kb, bs, winv, info);
     const int rest = N - kb - bs;
     if (rest <= 0) break;
-    PT_LAUNCH_PDL(k_chol_panel, (rest + 7) / 8, 256, 0, st, A, N, kb, bs, winv, info);
+    PT_LAUNCH_PDL(k_chol_panel<T>, (rest + 7) / 8, 256, 0, st, A, N, kb, bs, winv, info);
     const int nt = (rest + 15) / 16;
-    PT_LAUNCH_PDL(k_chol_update, dim3(nt, nt), 256, 0, st, A, N, kb, bs, info);
+    PT_LAUNCH_PDL(k_chol_update<T>, dim3(nt, nt), 256, 0, st, A, N, kb, bs, info);
   }
-  PT_LAUNCH(k_chol_finish, (N * N + 255) / 256, 256, 0, st, A, N, L, info);
+  PT_LAUNCH(k_chol_finish<T>, (N * N + 255) / 256, 256, 0, st, A, N, L, info);
 }
+template void cholesky<float>(pt_ctx*, c64*, int, c64*, int*, cudaStream_t);
+template void cholesky<double>(pt_ctx*, c128*, int, c128*, int*, cudaStream_t);
 
 // X = 0 except the diagonal CB-blocks, which take the inverses cholesky() kept
-__global__ void k_tri_inv_leaves(const c128* __restrict__ winv_all, int N, c128* __restrict__ X) {
+template <class T>
+__global__ void k_tri_inv_leaves(const cx<T>* __restrict__ winv_all, int N, cx<T>* __restrict__ X) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= N * N) return;
   const int i = e / N, j = e % N;
   const int bi = i / CB, bj = j / CB;
-  X[e] = (bi == bj) ? winv_all[size_t(i) * CB + (j - bj * CB)] : czero<double>();
+  X[e] = (bi == bj) ? winv_all[size_t(i) * CB + (j - bj * CB)] : czero<T>();
 }
 
-void tri_inv_lower(pt_ctx* ctx, const c128* L, int N, c128* X, cudaStream_t st) {
+template <class T>
+void tri_inv_lower(pt_ctx* ctx, const cx<T>* L, int N, cx<T>* X, cudaStream_t st) {
   // Bottom-up block inversion: for [L11 0; L21 L22] with X11 = L11^{-1}, X22 = L22^{-1} known,
   // X21 = -X22 (L21 X11).  Leaves are the CB x CB inverses from the preceding cholesky().
-  const c128* winv_all = static_cast<const c128*>(ctx->get("chol_winv_all", size_t(N) * CB * sizeof(c128)));
-  c128* T = static_cast<c128*>(ctx->get("tri_inv_T", size_t(N) * N * sizeof(c128)));
-  PT_LAUNCH(k_tri_inv_leaves, (N * N + 255) / 256, 256, 0, st, winv_all, N, X);
+  const cx<T>* winv_all = static_cast<const cx<T>*>(
+      ctx->get(sizeof(T) == 8 ? "chol_winv_all" : "chol_winv_all32", size_t(N) * CB * sizeof(cx<T>)));
+  cx<T>* Tm = static_cast<cx<T>*>(ctx->get(sizeof(T) == 8 ? "tri_inv_T" : "tri_inv_T32", size_t(N) * N * sizeof(cx<T>)));
+  PT_LAUNCH(k_tri_inv_leaves<T>, (N * N + 255) / 256, 256, 0, st, winv_all, N, X);
+  const cx<T> one{T(1), T(0)}, mone{T(-1), T(0)}, zero{T(0), T(0)};
   for (int s = CB; s < N; s *= 2) {
     for (int i0 = 0; i0 + s < N; i0 += 2 * s) {
       const int n1 = s, n2 = std::min(s, N - i0 - s);
-      const c128* X11 = X + size_t(i0) * N + i0;
-      const c128* X22 = X + size_t(i0 + s) * N + (i0 + s);
-      const c128* L21 = L + size_t(i0 + s) * N + i0;
-      c128* X21 = X + size_t(i0 + s) * N + i0;
-      zgemm('N', 'N', n2, n1, n1, c128{1, 0}, L21, N, X11, N, c128{0, 0}, T, n1, st);
-      zgemm('N', 'N', n2, n1, n2, c128{-1, 0}, X22, N, T, n1, c128{0, 0}, X21, N, st);
+      const cx<T>* X11 = X + size_t(i0) * N + i0;
+      const cx<T>* X22 = X + size_t(i0 + s) * N + (i0 + s);
+      const cx<T>* L21 = L + size_t(i0 + s) * N + i0;
+      cx<T>* X21 = X + size_t(i0 + s) * N + i0;
+      gemm<T>('N', 'N', n2, n1, n1, one, L21, N, X11, N, zero, Tm, n1, Tm, n1, st);
+      gemm<T>('N', 'N', n2, n1, n2, mone, X22, N, Tm, n1, zero, X21, N, X21, N, st);
     }
   }
 }
+template void tri_inv_lower<float>(pt_ctx*, const c64*, int, c64*, cudaStream_t);
+template void tri_inv_lower<double>(pt_ctx*, const c128*, int, c128*, cudaStream_t);
 
 void scale_cols_pow(const c128* U, const double* lam, int N, double power, c128* out, int* info, cudaStream_t st) {
   PT_LAUNCH(k_scale_cols_pow, (N * N + 255) / 256, 256, 0, st, U, lam, N, power, out, info);

@@ -94,9 +94,16 @@ void zgemm_add(char opA, char opB, int m, int n, int k, c128 alpha, const c128* 
 int heev(pt_ctx* ctx, const c128* S, int N, c128* Q, double* d, cudaStream_t st, int max_sweeps = 30,
          const c128* Q0 = nullptr, double rel_tol = 0.0);
 // A (overwritten) = L L^* ; L written to a separate buffer; *info = k+1 on a bad pivot k.
-void cholesky(pt_ctx* ctx, c128* A, int N, c128* L, int* info, cudaStream_t st);
-// X = L^{-1} for the factor of the preceding cholesky(ctx, ...) (uses its diagonal-block inverses)
-void tri_inv_lower(pt_ctx* ctx, const c128* L, int N, c128* X, cudaStream_t st);
+template <class T>
+void cholesky(pt_ctx* ctx, cx<T>* A, int N, cx<T>* L, int* info, cudaStream_t st);
+// X = L^{-1} for the factor of the preceding cholesky(ctx, ...) of the same precision (uses its
+// diagonal-block inverses)
+template <class T>
+void tri_inv_lower(pt_ctx* ctx, const cx<T>* L, int N, cx<T>* X, cudaStream_t st);
+// C = alpha op(A) op(B) + beta D in the precision of T (op in {N, C, T}; D may be C)
+template <class T>
+void gemm(char opA, char opB, int m, int n, int k, cx<T> alpha, const cx<T>* A, int lda, const cx<T>* B, int ldb,
+          cx<T> beta, const cx<T>* D, int ldd, cx<T>* C, int ldc, cudaStream_t st);
 void scale_cols_pow(const c128* U, const double* lam, int N, double power, c128* out, int* info, cudaStream_t st);
 void small_solve(const double* G, const double* rhs, int m, double reg, double* x, cudaStream_t st);
 void set_identity(c128* A, int N, cudaStream_t st);

@@ -197,6 +197,48 @@ __global__ void k_minus_adjoint(const c128* __restrict__ M, int N, c128* __restr
   out[e] = c128{a.re - b.re, a.im + b.im};
 }
 
+// N x N conversions of the mixed-precision S^{-1} A
+__global__ void k_to_c64(const c128* __restrict__ a, int n, c64* __restrict__ b) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) b[e] = c64{float(a[e].re), float(a[e].im)};
+}
+__global__ void k_to_c128(const c64* __restrict__ a, int n, c128* __restrict__ b) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) b[e] = c128{double(a[e].re), double(a[e].im)};
+}
+__global__ void k_add_c64(c128* __restrict__ x, const c64* __restrict__ c, int n) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) x[e] = c128{x[e].re + double(c[e].re), x[e].im + double(c[e].im)};
+}
+// flag = 1 when ||c||_F > tol ||x||_F (the last refinement correction against the solution)
+__global__ void k_corr_check(const c64* __restrict__ c, const c128* __restrict__ x, int n, double tol,
+                             int* __restrict__ flag) {
+  float sc = 0.f, sx = 0.f;
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    sc += c[e].re * c[e].re + c[e].im * c[e].im;
+    const float xr = float(x[e].re), xi = float(x[e].im);
+    sx += xr * xr + xi * xi;
+  }
+  for (int o = 16; o; o >>= 1) {
+    sc += __shfl_down_sync(0xffffffffu, sc, o);
+    sx += __shfl_down_sync(0xffffffffu, sx, o);
+  }
+  __shared__ float red[2][32];
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = sc;
+    red[1][threadIdx.x >> 5] = sx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) {
+      a += red[0][w];
+      b += red[1][w];
+    }
+    flag[0] = (a > tol * tol * b || !(a == a)) ? 1 : 0;
+  }
+}
+
 __global__ void k_fill(double* __restrict__ d, int n, const double* __restrict__ v) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) d[e] = v[0];
 }
@@ -250,12 +292,14 @@ __global__ void k_diff(cx<T>* out, const cx<T>* a, const cx<T>* b, size_t n) {
 // inverse, two products) costs about as much as kSinvCholCost products on this part, whose FP64
 // pipe runs the serial pivot chain slowly.  mode 1 takes the cheapest usable form, mode 2 the product
 // form whenever usable, mode 0 always the Cholesky route.
-enum SinvKind { kSinvChol = 0, kSinvHorner = 1, kSinvProduct = 2 };
+enum SinvKind { kSinvChol = 0, kSinvHorner = 1, kSinvProduct = 2, kSinvMixed = 3 };
 struct SinvPlan {
   SinvKind kind;
   int terms;  // K (Horner) or J (product)
 };
 constexpr double kSinvTol = 1e-17;
+constexpr int kMixedPasses = 2;      // FP64 refinement passes of the mixed-precision route
+constexpr double kMixedCheck = 1e-10;  // largest last correction, relative, that the route accepts
 constexpr int kSinvCholCost = 10;
 SinvPlan sinv_plan(double e, int mode) {
   if (mode == 0 || !(e < 0.25)) return {kSinvChol, 0};
@@ -391,6 +435,13 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
   double* dsc = static_cast<double*>(S.buf("ptim_dscratch", (2 * N + 64) * sizeof(double)));
   int* info = static_cast<int*>(S.buf("ptim_info", sizeof(int)));
   double* sdp = static_cast<double*>(S.buf("ptim_sdev", (SD_BLOCKS + 1) * sizeof(double)));
+  // FP32 N x N work matrices and flags of the mixed-precision S^{-1} A
+  auto M32 = [&](const char* n) { return static_cast<c64*>(S.buf(n, S.n2 * sizeof(c64))); };
+  c64 *s32 = M32("ptim_s32"), *l32 = M32("ptim_l32"), *li32 = M32("ptim_li32"), *si32 = M32("ptim_si32");
+  c64 *r32 = M32("ptim_r32"), *c32 = M32("ptim_c32");
+  int* info32 = static_cast<int*>(S.buf("ptim_info32", 2 * sizeof(int)));
+  int* mixflag = info32 + 1;
+  bool mixed_ok = true;
   // Anderson history ring: dR and Z = dX + beta dR per slot, for both segments
   std::vector<cx<T>*> Zp(depth), dRp(depth);
   std::vector<c128*> Zs(depth), dRs(depth);
@@ -721,18 +772,49 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
       }
       tm.begin(PH_SUBNN);
       SinvPlan plan{kSinvChol, 0};
-      if (ctx->ptim_sinv_series) {
-        PT_LAUNCH(k_sdev_part, SD_BLOCKS, 256, 0, st, Sm, N, sdp);
-        PT_LAUNCH(k_sdev_sum, 1, 32, 0, st, sdp, sdp + SD_BLOCKS);
+      const bool mixed = ctx->ptim_sinv_mixed && mixed_ok;
+      if (mixed) {  // FP32 factor of S for the mixed-precision route, before the synchronisation
+        PT_LAUNCH(k_to_c64, (N * N + 255) / 256, 256, 0, st, Sm, N * N, s32);
+        cholesky<float>(ctx, s32, N, l32, info32, st);
+      }
+      if (ctx->ptim_sinv_series || mixed) {
         double e2 = NAN;
-        PT_CUDA_CHECK(cudaMemcpyAsync(&e2, sdp + SD_BLOCKS, sizeof(double), cudaMemcpyDeviceToHost, st));
+        int h_info32 = 1;
+        if (ctx->ptim_sinv_series) {
+          PT_LAUNCH(k_sdev_part, SD_BLOCKS, 256, 0, st, Sm, N, sdp);
+          PT_LAUNCH(k_sdev_sum, 1, 32, 0, st, sdp, sdp + SD_BLOCKS);
+          PT_CUDA_CHECK(cudaMemcpyAsync(&e2, sdp + SD_BLOCKS, sizeof(double), cudaMemcpyDeviceToHost, st));
+        }
+        if (mixed) PT_CUDA_CHECK(cudaMemcpyAsync(&h_info32, info32, sizeof(int), cudaMemcpyDeviceToHost, st));
         PT_CUDA_CHECK(cudaStreamSynchronize(st));
-        const double e = std::sqrt(e2);
-        if (!(e <= stv.s_dev_max)) stv.s_dev_max = e;
-        plan = sinv_plan(e, ctx->ptim_sinv_series);
+        if (ctx->ptim_sinv_series) {
+          const double e = std::sqrt(e2);
+          if (!(e <= stv.s_dev_max)) stv.s_dev_max = e;
+          plan = sinv_plan(e, ctx->ptim_sinv_series);
+        }
+        if (plan.kind == kSinvChol && mixed && h_info32 == 0) plan = SinvPlan{kSinvMixed, kMixedPasses};
       }
       stv.sinv_path[plan.kind]++;
-      if (plan.kind == kSinvChol) {
+      if (plan.kind == kSinvMixed) {
+        // S^{-1} A from the FP32 factor S32 = L32 L32^*, refined in FP64 (iterative refinement):
+        // X = S32^{-1} A, then X <- X + S32^{-1} (A - S X) with the residual in FP64; each pass
+        // multiplies the error by ~kappa(S) eps_32, the last correction is checked against X
+        const int nn = N * N, nb = (N * N + 255) / 256;
+        const c64 one32{1.f, 0.f}, zero32{0.f, 0.f};
+        tri_inv_lower<float>(ctx, l32, N, li32, st);
+        gemm<float>('C', 'N', N, N, N, one32, li32, N, li32, N, zero32, si32, N, si32, N, st);  // S32^{-1}
+        PT_LAUNCH(k_to_c64, nb, 256, 0, st, A, nn, r32);
+        gemm<float>('N', 'N', N, N, N, one32, si32, N, r32, N, zero32, c32, N, c32, N, st);
+        PT_LAUNCH(k_to_c128, nb, 256, 0, st, c32, nn, SinvA);
+        for (int pass = 0; pass < plan.terms; ++pass) {
+          zgemm_add('N', 'N', N, N, N, c128{-1, 0}, Sm, N, SinvA, N, c128{1, 0}, A, N, T1, N, st);  // A - S X
+          PT_LAUNCH(k_to_c64, nb, 256, 0, st, T1, nn, r32);
+          gemm<float>('N', 'N', N, N, N, one32, si32, N, r32, N, zero32, c32, N, c32, N, st);
+          PT_LAUNCH(k_add_c64, nb, 256, 0, st, SinvA, c32, nn);
+        }
+        PT_LAUNCH(k_corr_check, 1, 1024, 0, st, c32, SinvA, nn, kMixedCheck, mixflag);
+        PT_CUDA_CHECK(cudaMemsetAsync(info, 0, sizeof(int), st));
+      } else if (plan.kind == kSinvChol) {
         // S^{-1} A = L^{-*} (L^{-1} A)
         cholesky(ctx, Sm, N, Lc, info, st);
         tri_inv_lower(ctx, Lc, N, Li, st);
@@ -788,10 +870,15 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
       lincomb<double>(ctx, rsig, S.n2, ts, 3, st);
       tm.end();
       tm.begin(PH_AND);
-      int h_info = 0;
+      int h_info = 0, h_mix = 0;
       PT_CUDA_CHECK(cudaMemcpyAsync(&h_info, info, sizeof(int), cudaMemcpyDeviceToHost, st));
+      if (plan.kind == kSinvMixed) PT_CUDA_CHECK(cudaMemcpyAsync(&h_mix, mixflag, sizeof(int), cudaMemcpyDeviceToHost, st));
       double rr = 0, xx = 0;
       S.norm2_pair(rphi, rsig, phi, sig, &rr, &xx);  // synchronises st
+      if (h_mix) {  // refinement too slow for this S (kappa(S) eps_32 not small): FP64 Cholesky from now on
+        mixed_ok = false;
+        stv.sinv_mixed_fallback = 1;
+      }
       if (first) {
         double tr = 0.0;  // Re Tr[sigma_n A_0] = Re sum_ij sigma_ij A_ji
         for (int i = 0; i < N; ++i)
