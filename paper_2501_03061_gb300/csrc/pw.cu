@@ -347,8 +347,9 @@ template <class T>
 int pw_batch(pt_ctx* ctx, const pt_grid& g, int M, cx<T>** scratch) {
   const size_t field = ng_of(g) * sizeof(cx<T>);
   const int mb = int(std::max<size_t>(1, exchange_scratch_budget(ctx) / (2 * field)));
-  *scratch = static_cast<cx<T>*>(ctx->get("h_scratch", 2 * size_t(mb) * field));
-  return std::min(M, 2 * mb);
+  const int pb = std::min(M, 2 * mb);
+  *scratch = static_cast<cx<T>*>(ctx->get("h_scratch", size_t(pb) * field));  // no more than M fields
+  return pb;
 }
 
 enum class PwOp { ToPw, ToGrid, H };
