@@ -326,7 +326,7 @@ pt_status pt_diag_occupations(pt_ctx* ctx, const void* sigma, int N, void* Q, do
 typedef struct {
   double dt;             /* time step (au) */
   double alpha;          /* exchange mixing fraction (0.25 for HSE-like functionals) */
-  double ecut;           /* plane-wave cutoff (Ha) of the projection P_sph */
+  double ecut;           /* plane-wave cutoff (Ha) of the projection P_sph and of the orbital basis, > 0 */
   double tol;            /* relative residual of x = T(x), and of the ACE anchor change */
   int max_outer;         /* outer (ACE rebuild) iterations */
   int max_inner;         /* inner Anderson iterations per outer iteration */

@@ -584,7 +584,7 @@ pt_status pt_ptim_step(pt_ctx* ctx, void* phi, void* sigma, int N, const double*
     pt::require_aligned(sigma, "sigma");
     if (!vloc) pt::fail(PT_INVALID_ARG, "vloc is NULL");
     const pt_ptim_params& P = *params;
-    if (!(P.dt > 0) || !(P.tol > 0) || P.max_inner <= 0 || P.max_outer <= 0 || P.anderson_depth <= 0 ||
+    if (!(P.dt > 0) || !(P.tol > 0) || !(P.ecut > 0) || P.max_inner <= 0 || P.max_outer <= 0 || P.anderson_depth <= 0 ||
         P.anderson_depth > 20 || (P.hxc != 0 && P.hxc != 1) || (P.hxc && !(P.spin > 0)))
       pt::fail(PT_INVALID_ARG, "invalid PT-IM parameters");
     set_device(ctx);

@@ -210,11 +210,12 @@ __global__ void k_add_c64(c128* __restrict__ x, const c64* __restrict__ c, int n
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e < n) x[e] = c128{x[e].re + double(c[e].re), x[e].im + double(c[e].im)};
 }
-// flag = 1 when ||c||_F > tol ||x||_F (the last refinement correction against the solution)
-__global__ void k_corr_check(const c64* __restrict__ c, const c128* __restrict__ x, int n, double tol,
-                             int* __restrict__ flag) {
+// flag = 1 when ||c||_F > tol ||x||_F (the last refinement correction against the solution): one
+// partial pair per block, then one thread adds them in order
+__global__ void __launch_bounds__(256) k_corr_part(const c64* __restrict__ c, const c128* __restrict__ x, int n,
+                                                   double* __restrict__ part) {
   float sc = 0.f, sx = 0.f;
-  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+  for (int e = blockIdx.x * 256 + threadIdx.x; e < n; e += SD_BLOCKS * 256) {
     sc += c[e].re * c[e].re + c[e].im * c[e].im;
     const float xr = float(x[e].re), xi = float(x[e].im);
     sx += xr * xr + xi * xi;
@@ -223,7 +224,7 @@ __global__ void k_corr_check(const c64* __restrict__ c, const c128* __restrict__
     sc += __shfl_down_sync(0xffffffffu, sc, o);
     sx += __shfl_down_sync(0xffffffffu, sx, o);
   }
-  __shared__ float red[2][32];
+  __shared__ float red[2][8];
   if ((threadIdx.x & 31) == 0) {
     red[0][threadIdx.x >> 5] = sc;
     red[1][threadIdx.x >> 5] = sx;
@@ -231,9 +232,20 @@ __global__ void k_corr_check(const c64* __restrict__ c, const c128* __restrict__
   __syncthreads();
   if (threadIdx.x == 0) {
     double a = 0.0, b = 0.0;
-    for (int w = 0; w < int(blockDim.x >> 5); ++w) {
+    for (int w = 0; w < 8; ++w) {
       a += red[0][w];
       b += red[1][w];
+    }
+    part[2 * blockIdx.x] = a;
+    part[2 * blockIdx.x + 1] = b;
+  }
+}
+__global__ void k_corr_flag(const double* __restrict__ part, double tol, int* __restrict__ flag) {
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < SD_BLOCKS; ++k) {
+      a += part[2 * k];
+      b += part[2 * k + 1];
     }
     flag[0] = (a > tol * tol * b || !(a == a)) ? 1 : 0;
   }
@@ -434,7 +446,8 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
   double* d = static_cast<double*>(S.buf("ptim_d", N * sizeof(double)));
   double* dsc = static_cast<double*>(S.buf("ptim_dscratch", (2 * N + 64) * sizeof(double)));
   int* info = static_cast<int*>(S.buf("ptim_info", sizeof(int)));
-  double* sdp = static_cast<double*>(S.buf("ptim_sdev", (SD_BLOCKS + 1) * sizeof(double)));
+  // partial sums of the N x N checks: ||S - I||_F (SD_BLOCKS + 1), the refinement check (2 SD_BLOCKS)
+  double* sdp = static_cast<double*>(S.buf("ptim_sdev", (2 * SD_BLOCKS + 2) * sizeof(double)));
   // FP32 N x N work matrices and flags of the mixed-precision S^{-1} A
   auto M32 = [&](const char* n) { return static_cast<c64*>(S.buf(n, S.n2 * sizeof(c64))); };
   c64 *s32 = M32("ptim_s32"), *l32 = M32("ptim_l32"), *li32 = M32("ptim_li32"), *si32 = M32("ptim_si32");
@@ -812,7 +825,8 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
           gemm<float>('N', 'N', N, N, N, one32, si32, N, r32, N, zero32, c32, N, c32, N, st);
           PT_LAUNCH(k_add_c64, nb, 256, 0, st, SinvA, c32, nn);
         }
-        PT_LAUNCH(k_corr_check, 1, 1024, 0, st, c32, SinvA, nn, kMixedCheck, mixflag);
+        PT_LAUNCH(k_corr_part, SD_BLOCKS, 256, 0, st, c32, SinvA, nn, sdp);
+        PT_LAUNCH(k_corr_flag, 1, 32, 0, st, sdp, kMixedCheck, mixflag);
         PT_CUDA_CHECK(cudaMemsetAsync(info, 0, sizeof(int), st));
       } else if (plan.kind == kSinvChol) {
         // S^{-1} A = L^{-*} (L^{-1} A)
