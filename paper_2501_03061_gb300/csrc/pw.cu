@@ -5,7 +5,7 @@
 // unitary, so every inner product over the grid (with its volume element dV) is the same sum over
 // the coefficients, and a field inside the sphere is represented exactly by them.  The PT-IM step
 // holds its orbital blocks (iterates, Anderson history, ACE operator, residuals) as coefficient
-// vectors: at 64^3 with Ecut = 10 Ha, 12,995 plane waves against 262,144 grid points.  Real space
+// vectors: at 64^3 with Ecut = 10 Ha, 13,037 plane waves against 262,144 grid points.  Real space
 // is entered only where the method needs it: the local potential of H, the exchange and the
 // density.
 //
