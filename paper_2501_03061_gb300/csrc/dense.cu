@@ -194,16 +194,18 @@ __global__ void k_herm_part_and_basis(const c128* __restrict__ S, c128* __restri
   V[e] = V0 ? V0[e] : c128{i == j ? 1.0 : 0.0, 0.0};
 }
 
-// sums of |offdiag|^2 and |all|^2 (one block)
-__global__ void k_offnorm(const c128* __restrict__ A, int N, double* __restrict__ out) {
+// sums of |offdiag|^2 and |all|^2: one partial pair per block (OFF_BLOCKS blocks), then one thread
+// adds the partials in order
+constexpr int OFF_BLOCKS = 64;
+__global__ void __launch_bounds__(256) k_offnorm_part(const c128* __restrict__ A, int N, double* __restrict__ part) {
   pdl_wait();  // the last Jacobi round
   double off = 0, all = 0;
-  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+  for (int e = blockIdx.x * 256 + threadIdx.x; e < N * N; e += OFF_BLOCKS * 256) {
     const double v = A[e].re * A[e].re + A[e].im * A[e].im;
     all += v;
     if (e / N != e % N) off += v;
   }
-  __shared__ double so[32], sa[32];
+  __shared__ double so[8], sa[8];
   for (int o = 16; o; o >>= 1) {
     off += __shfl_down_sync(0xffffffffu, off, o);
     all += __shfl_down_sync(0xffffffffu, all, o);
@@ -215,28 +217,55 @@ __global__ void k_offnorm(const c128* __restrict__ A, int N, double* __restrict_
   __syncthreads();
   if (threadIdx.x == 0) {
     double a = 0, b = 0;
-    for (int w = 0; w < int(blockDim.x >> 5); ++w) {
+    for (int w = 0; w < 8; ++w) {
       a += so[w];
       b += sa[w];
+    }
+    part[2 * blockIdx.x] = a;
+    part[2 * blockIdx.x + 1] = b;
+  }
+}
+__global__ void k_offnorm_sum(const double* __restrict__ part, double* __restrict__ out) {
+  if (threadIdx.x == 0) {
+    double a = 0, b = 0;
+    for (int k = 0; k < OFF_BLOCKS; ++k) {
+      a += part[2 * k];
+      b += part[2 * k + 1];
     }
     out[0] = a;
     out[1] = b;
   }
 }
 
-// ascending sort of the diagonal with the matching columns of V (one block, rank sort)
-__global__ void k_sort_eig(const c128* __restrict__ A, const c128* __restrict__ V, int N, c128* __restrict__ Q,
-                           double* __restrict__ d) {
-  for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    const double di = A[size_t(i) * N + i].re;
-    int rank = 0;
-    for (int j = 0; j < N; ++j) {
-      const double dj = A[size_t(j) * N + j].re;
-      rank += (dj < di) || (dj == di && j < i);
-    }
-    d[rank] = di;
-    for (int row = 0; row < N; ++row) Q[size_t(row) * N + rank] = V[size_t(row) * N + i];
+// ascending sort of the diagonal with the matching columns of V: a rank sort on order-preserving
+// integer keys of the doubles (an FP64 comparison issues at the FP64 rate here), then the column
+// permutation over the whole grid
+__device__ __forceinline__ unsigned long long order_key(double v) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v));
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__global__ void k_eig_keys(const c128* __restrict__ A, int N, unsigned long long* __restrict__ key) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) key[i] = order_key(A[size_t(i) * N + i].re);
+}
+__global__ void k_eig_rank(const c128* __restrict__ A, const unsigned long long* __restrict__ key, int N,
+                           int* __restrict__ rank, double* __restrict__ d) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const unsigned long long ki = key[i];
+  int r = 0;
+  for (int j = 0; j < N; ++j) {
+    const unsigned long long kj = key[j];  // the same j across the warp: one broadcast load
+    r += (kj < ki) || (kj == ki && j < i);
   }
+  rank[i] = r;
+  d[r] = A[size_t(i) * N + i].re;
+}
+__global__ void k_eig_permute(const c128* __restrict__ V, const int* __restrict__ rank, int N, c128* __restrict__ Q) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= N * N) return;
+  const int row = e / N, i = e - row * N;
+  Q[size_t(row) * N + rank[i]] = V[e];
 }
 
 // ---------------------------------------------------------------- Cholesky ----
@@ -466,7 +495,7 @@ int heev(pt_ctx* ctx, const c128* S, int N, c128* Q, double* d, cudaStream_t st,
   c128* A0 = static_cast<c128*>(ctx->get("heev_A0", size_t(N) * N * sizeof(c128)));
   c128* A1 = static_cast<c128*>(ctx->get("heev_A1", size_t(N) * N * sizeof(c128)));
   c128* V = static_cast<c128*>(ctx->get("heev_V", size_t(N) * N * sizeof(c128)));
-  double* nrm = static_cast<double*>(ctx->get("heev_norm", 2 * sizeof(double)));
+  double* nrm = static_cast<double*>(ctx->get("heev_norm", (2 * OFF_BLOCKS + 2) * sizeof(double)));
   if (Q0) {
     // warm start: rotate into the basis Q0 (Jacobi then starts from a nearly diagonal matrix when
     // Q0 diagonalises a nearby matrix) and accumulate the rotations onto Q0
@@ -483,7 +512,8 @@ int heev(pt_ctx* ctx, const c128* S, int N, c128* Q, double* d, cudaStream_t st,
   double prev_off = INFINITY;
   int sweeps = 0;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    PT_LAUNCH_PDL(k_offnorm, 1, 1024, 0, st, A0, N, nrm);
+    PT_LAUNCH_PDL(k_offnorm_part, OFF_BLOCKS, 256, 0, st, A0, N, nrm + 2);
+    PT_LAUNCH(k_offnorm_sum, 1, 32, 0, st, nrm + 2, nrm);
     PT_CUDA_CHECK(cudaMemcpyAsync(h, nrm, sizeof(h), cudaMemcpyDeviceToHost, st));
     PT_CUDA_CHECK(cudaStreamSynchronize(st));
     if (!std::isfinite(h[1])) fail(PT_NONFINITE, "non-finite entry in the matrix to diagonalise");
@@ -506,7 +536,11 @@ int heev(pt_ctx* ctx, const c128* S, int N, c128* Q, double* d, cudaStream_t st,
     }
     ++sweeps;
   }
-  PT_LAUNCH(k_sort_eig, 1, 256, 0, st, A0, V, N, Q, d);
+  auto* key = static_cast<unsigned long long*>(ctx->get("heev_key", size_t(N) * sizeof(unsigned long long)));
+  int* rank = static_cast<int*>(ctx->get("heev_rank", size_t(N) * sizeof(int)));
+  PT_LAUNCH(k_eig_keys, (N + 255) / 256, 256, 0, st, A0, N, key);
+  PT_LAUNCH(k_eig_rank, (N + 127) / 128, 128, 0, st, A0, key, N, rank, d);
+  PT_LAUNCH(k_eig_permute, (N * N + 255) / 256, 256, 0, st, V, rank, N, Q);
   return sweeps;
 }
 

@@ -74,20 +74,24 @@ class PhaseTimer {
 };
 enum { PH_EXCH = 0, PH_ACE_BUILD, PH_ACE_APPLY, PH_H, PH_SUB, PH_SUBNN, PH_EIG, PH_ROT, PH_COMM, PH_AND, PH_LOEW, PH_HXC };
 
-__global__ void k_maxabs_diff(const c128* __restrict__ A, const c128* __restrict__ B, int n, double* __restrict__ out) {
+// out[0] = max |A_e - B_e|^2 over the entries (squared: no FP64 square root per entry), as the
+// bit pattern of a non-negative double, whose integer order is its numeric order (out zeroed first)
+__global__ void __launch_bounds__(256) k_maxabs2_diff(const c128* __restrict__ A, const c128* __restrict__ B, int n,
+                                                      unsigned long long* __restrict__ out) {
   double m = 0;
-  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+  for (int e = blockIdx.x * 256 + threadIdx.x; e < n; e += gridDim.x * 256) {
     const double dr = A[e].re - B[e].re, di = A[e].im - B[e].im;
-    m = fmax(m, sqrt(dr * dr + di * di));
+    m = fmax(m, dr * dr + di * di);
   }
   for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
-  __shared__ double s[32];
+  __shared__ double s[8];
   if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = m;
   __syncthreads();
   if (threadIdx.x == 0) {
     double r = 0;
-    for (int w = 0; w < int(blockDim.x >> 5); ++w) r = fmax(r, s[w]);
-    out[0] = r;
+    for (int w = 0; w < 8; ++w) r = fmax(r, s[w]);
+    if (!(r == r)) r = __longlong_as_double(0x7ff0000000000000ll);  // NaN counts as +inf
+    atomicMax(out, static_cast<unsigned long long>(__double_as_longlong(r)));
   }
 }
 
@@ -988,12 +992,17 @@ pt_status ptim_step_t(pt_ctx* ctx, cx<T>* phi, c128* sig, int N, const double* v
   // ---- final orthonormalisation and conjugate symmetrisation ----
   tm.begin(PH_LOEW);
   gram<T>(ctx, phi, phi, N, N, S.nv, S.dV, Sm, st);
-  PT_LAUNCH(k_maxabs_diff, 1, 1024, 0, st, Sm, Sn, int(S.n2), dsc);
+  auto* dmax = reinterpret_cast<unsigned long long*>(dsc);
+  PT_CUDA_CHECK(cudaMemsetAsync(dmax, 0, 2 * sizeof(unsigned long long), st));
+  const int mblocks = std::max(1, std::min(SD_BLOCKS, int((S.n2 + 255) / 256)));
+  PT_LAUNCH(k_maxabs2_diff, mblocks, 256, 0, st, Sm, Sn, int(S.n2), dmax);
   set_identity(T1, N, st);
-  PT_LAUNCH(k_maxabs_diff, 1, 1024, 0, st, Sm, T1, int(S.n2), dsc + 1);
+  PT_LAUNCH(k_maxabs2_diff, mblocks, 256, 0, st, Sm, T1, int(S.n2), dmax + 1);
   double devs[2] = {0, 0};
   PT_CUDA_CHECK(cudaMemcpyAsync(devs, dsc, sizeof(devs), cudaMemcpyDeviceToHost, st));
   PT_CUDA_CHECK(cudaStreamSynchronize(st));
+  devs[0] = std::sqrt(devs[0]);  // the kernels keep squares
+  devs[1] = std::sqrt(devs[1]);
   stv.orth_error = devs[0];
   PT_CUDA_CHECK(cudaMemsetAsync(info, 0, sizeof(int), st));
   const double sdev = devs[1];  // max |S - I|
