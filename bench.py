@@ -42,7 +42,7 @@ WORKLOAD = "ptim_ace_step_64^3_N320_128site_L20.5"
 # iteration counts of one benchmark step as the GPU step measured them (ACE builds, inner iterations
 # per step, the mean over the timed steps of the last full benchmark run): the reference arm, which
 # runs no GPU step, composes an oracle step from these; the GPU arm uses its own live counts
-REF_OUTER, REF_INNER = 4.0, 39.0
+REF_OUTER, REF_INNER = 3.0, 28.0
 
 
 def _finite(x):
