@@ -111,7 +111,8 @@ pt_status pt_trim(pt_ctx* ctx);
  *                    the residual as 1/(1 + i dt/2 (|G + A|^2/2 - Re <phi_j|H phi_j>)) in Fourier space
  *                    inside the basis sphere (identity outside, sigma untouched).  M is invertible, so
  *                    the fixed point (the step's result) is unchanged; the iteration needs fewer
- *                    steps (64^3 grid, N = 320: 39 inner iterations per step against 46-47).
+ *                    steps (64^3 grid, N = 320, orbital blocks on the grid: 39 inner iterations per
+ *                    step against 46-47).
  *                    Default 1; 0: plain Anderson on T(x) - x.
  *   "ptim_ace_warm"  1: when a step's input (phi, sigma) is exactly the output of the context's
  *                    previous step (same sizes, grid, kernel, precision; checked by a fingerprint),
